@@ -1,0 +1,171 @@
+/*
+ * imq.h -- C ABI of the GB300 library for the fast inverse-multiquadric (IMQ)
+ * matrix-vector product and the interpolation solve built on it.
+ *
+ * Method: De Marchi, Egidi, Giacomini, Maponi, Perticarini, "Computational
+ * issues by interpolating with inverse multiquadrics: a solution",
+ * arXiv 2205.04194.
+ *
+ *   Section 2, Eq. (4)-(5):  A_ij = phi(|x_i - x_j|) = 1 / sqrt(|x_i - x_j|^2 + c^2)
+ *     (the paper names the shape parameter t; it is c here, c > 0).
+ *   Section 2.2, Eq. (11)-(13) and Algorithm 1: each entry is the Laplace Green's
+ *     function 1/|X - Y| between X = (x_i, +c/2) and Y = (x_j, -c/2), expanded in
+ *     spherical harmonics about quadtree box centres to truncation order p, so
+ *     that only adjacent ("not well separated") boxes are summed directly.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are dense and row-major.  A point set is double[N][2] (x, y).  A
+ *     block of vectors is [nrhs][N] (vector r at offset r*N).
+ *   - "Host or device" pointers are classified with cudaPointerGetAttributes:
+ *     device (and managed) memory is used in place; pageable or pinned host
+ *     memory is copied to the device and results are copied back, inside the
+ *     call, on `stream`.  Results written to host memory are complete when the
+ *     call returns (the call synchronises `stream`); results written to device
+ *     memory are complete when `stream` reaches the end of the enqueued work.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All GPU
+ *     work of a call is enqueued on it.
+ *   - The caller owns every buffer it passes; no pointer is retained after the
+ *     call returns.  A plan owns its own device memory until imq_plan_destroy.
+ *   - Every call returns an imq_status; no C++ exception crosses the ABI.  On
+ *     error the output buffers hold unspecified values, and imq_last_error()
+ *     returns a message (thread-local, valid until the next call on the thread).
+ *   - The library requires a CUDA device of compute capability 10.3 (sm_103a)
+ *     and fails with IMQ_UNSUPPORTED elsewhere; there is no CPU fallback.
+ */
+#ifndef IMQ_H
+#define IMQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum imq_status {
+    IMQ_OK = 0,
+    IMQ_INVALID_ARG = 1,       /* bad size, pointer, c <= 0, NaN/Inf coordinates ...   */
+    IMQ_DUPLICATE_POINTS = 2,  /* two points are exactly equal (Section 2 needs distinct sites) */
+    IMQ_CUDA_ERROR = 3,        /* a CUDA runtime call failed                              */
+    IMQ_OOM = 4,               /* device allocation failed                                */
+    IMQ_NOT_CONVERGED = 5,     /* iteration cap reached; best iterate returned            */
+    IMQ_NUMERICAL = 6,         /* NaN/Inf met inside an iteration                         */
+    IMQ_UNSUPPORTED = 7,       /* p outside [1, IMQ_MAX_P], wrong GPU, option not built    */
+    IMQ_TIMEOUT = 8            /* a device-side bounded wait gave up                      */
+} imq_status;
+
+typedef enum imq_dtype {
+    IMQ_F32 = 0,   /* the expansion path in FP32 (P2P, P2M ... L2P; FP32 rsqrt)     */
+    IMQ_F64 = 1    /* every kernel of the product in FP64                          */
+} imq_dtype;
+
+#define IMQ_MAX_P 18
+#define IMQ_MAX_LEVEL 16
+
+/* Opaque plan: the tree, its interaction lists and the translation operators
+ * for one point set, one shape c and one truncation order p. */
+typedef struct imq_plan_s *imq_plan_t;
+
+/* Optional plan settings.  Zero-initialise, set struct_size = sizeof(imq_options). */
+typedef struct imq_options {
+    int32_t struct_size;
+    int32_t has_domain;        /* 1: use (x0, y0, side) as the square D (Section 2.2) */
+    double x0, y0, side;       /*    otherwise D is the exact bounding square          */
+    int32_t check_duplicates;  /* 1: imq_plan fails with IMQ_DUPLICATE_POINTS on equal points */
+    int32_t reserved[7];
+} imq_options;
+
+/* ------------------------------------------------------------------------- *
+ * imq_plan -- build the quadtree, its interaction lists and the operators.
+ *
+ *   Section 2.2: the square D containing the points is partitioned into
+ *   2^l x 2^l blocks; the adaptive tree here splits a block while it holds
+ *   more than `leaf` points (and its depth is below IMQ_MAX_LEVEL).  The
+ *   well-separated sets S_p become the V/W/X lists and the not-well-separated
+ *   sets NS_p the U list.
+ *
+ *   points : double[N][2], host or device; read during the call only.
+ *   N      : number of points, N >= 1.
+ *   c      : shape parameter, c > 0 (finite).
+ *   p      : truncation order of the expansions (the paper's M), 1 <= p <= IMQ_MAX_P.
+ *   leaf   : maximum points per leaf box, leaf >= 1.
+ *   opt    : may be NULL.
+ *   out    : receives the plan (NULL on failure).
+ *
+ *   Synchronises `stream` (box counts are read back once per level).
+ *   Errors: IMQ_INVALID_ARG, IMQ_DUPLICATE_POINTS, IMQ_UNSUPPORTED, IMQ_OOM,
+ *   IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+imq_status imq_plan(const double *points, int64_t N, double c, int p, int leaf,
+                    const imq_options *opt, void *stream, imq_plan_t *out);
+
+/* Release every device allocation of the plan (after synchronising its work). */
+void imq_plan_destroy(imq_plan_t plan);
+
+/* ------------------------------------------------------------------------- *
+ * imq_matvec -- b = A v by the fast method (Algorithm 1, generalised to the
+ * translations of the fast multipole method; see the paper's Section 2.2).
+ *
+ *   v   : [nrhs][N] of dtype, host or device, in the caller's point order.
+ *   out : [nrhs][N] of dtype, host or device, in the caller's point order.
+ *   dt  : IMQ_F32 -- every kernel in FP32 except the FP64 operator set-up;
+ *         IMQ_F64 -- every kernel in FP64.
+ *   Errors: IMQ_INVALID_ARG (nrhs < 1, NULL pointers), IMQ_OOM, IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs,
+                      imq_dtype dt, void *stream);
+
+/* ------------------------------------------------------------------------- *
+ * imq_dense_matvec -- the plain ("standard row-column") product of Section 3:
+ * b_i = sum_j v_j / sqrt(|x_i - x_j|^2 + c^2) over all N^2 pairs, matrix-free.
+ *
+ *   points : double[N][2]; v, out : [nrhs][N] of dtype; all host or device.
+ *   IMQ_F32: FP32 coordinates (cast from FP64), FP32 rsqrt, FP32 partial sums
+ *            over source tiles accumulated in FP64.  IMQ_F64: all FP64.
+ *   Errors: IMQ_INVALID_ARG, IMQ_OOM, IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+imq_status imq_dense_matvec(const double *points, int64_t N, double c, const void *v,
+                            void *out, int nrhs, imq_dtype dt, void *stream);
+
+/* ------------------------------------------------------------------------- *
+ * Introspection of a plan, for tests and benchmarks.
+ * ------------------------------------------------------------------------- */
+typedef struct imq_plan_info {
+    int64_t n_points;
+    int32_t n_boxes, n_leaves, max_level, p, leaf, k_real;  /* k_real: reals per expansion */
+    double x0, y0, side, c;
+    int64_t n_u, n_v, n_w, n_x;          /* total entries of each interaction list */
+    int64_t p2p_pairs;                   /* sum over leaves of n_target * n_source in U */
+    int64_t m2l_pairs;                   /* V-list entries on levels >= 2 */
+    int64_t device_bytes;                /* device memory owned by the plan */
+} imq_plan_info;
+
+imq_status imq_plan_get_info(imq_plan_t plan, imq_plan_info *info);
+
+/* Copy the tree to HOST buffers (each may be NULL to skip it):
+ *   codes[N]   uint32 Morton codes in sorted order;  perm[N] int64 sorted->input index;
+ *   level, prefix, begin, end, parent : [n_boxes];   child : [n_boxes][4] (-1 absent). */
+imq_status imq_plan_export_tree(imq_plan_t plan, uint32_t *codes, int64_t *perm,
+                                int32_t *level, uint32_t *prefix, int64_t *begin,
+                                int64_t *end, int32_t *parent, int32_t *child);
+
+/* Copy one interaction list in CSR form to HOST buffers.
+ *   which  : 'U', 'V', 'W' or 'X'.
+ *   offsets: int32[n_boxes + 1]; items: int32[offsets[n_boxes]] (box numbers, sorted
+ *            ascending within each box).  Either may be NULL. */
+imq_status imq_plan_export_list(imq_plan_t plan, char which, int32_t *offsets, int32_t *items);
+
+/* Human-readable name of a status code (static string). */
+const char *imq_status_string(imq_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *imq_last_error(void);
+
+/* Library version string. */
+const char *imq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMQ_H */

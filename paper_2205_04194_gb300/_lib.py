@@ -1,0 +1,87 @@
+"""ctypes binding of libimq.so (include/imq.h): symbol signatures and status checks.
+
+Argument marshalling only; every computation runs in the CUDA library.  There
+is no fallback: if the shared library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+INT = ctypes.c_int
+CHAR = ctypes.c_char
+
+
+class ImqError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        self.status = status
+        super().__init__(f"{func}: {status_name(status)}: {msg}")
+
+
+class ImqOptions(ctypes.Structure):
+    _fields_ = [("struct_size", I32), ("has_domain", I32), ("x0", D), ("y0", D), ("side", D),
+                ("check_duplicates", I32), ("reserved", I32 * 7)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_points", I64), ("n_boxes", I32), ("n_leaves", I32), ("max_level", I32), ("p", I32),
+                ("leaf", I32), ("k_real", I32), ("x0", D), ("y0", D), ("side", D), ("c", D),
+                ("n_u", I64), ("n_v", I64), ("n_w", I64), ("n_x", I64), ("p2p_pairs", I64),
+                ("m2l_pairs", I64), ("device_bytes", I64)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "imq_plan": (INT, [P, I64, D, INT, INT, P, P, P]),
+    "imq_plan_destroy": (None, [P]),
+    "imq_matvec": (INT, [P, P, P, INT, INT, P]),
+    "imq_dense_matvec": (INT, [P, I64, D, P, P, INT, INT, P]),
+    "imq_plan_get_info": (INT, [P, P]),
+    "imq_plan_export_tree": (INT, [P, P, P, P, P, P, P, P, P]),
+    "imq_plan_export_list": (INT, [P, CHAR, P, P]),
+    "imq_status_string": (ctypes.c_char_p, [INT]),
+    "imq_last_error": (ctypes.c_char_p, []),
+    "imq_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str | None = None):
+    """Load libimq.so (built by ``paper_2205_04194_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = path or LIB
+            if not os.path.exists(so):
+                raise RuntimeError(f"libimq.so not built ({so}); run paper_2205_04194_gb300.build.build()")
+            lib = ctypes.CDLL(so)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().imq_status_string(int(status)).decode()
+    except Exception:   # noqa: BLE001 - name lookup only
+        return str(status)
+
+
+def call(name: str, *args) -> int:
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        raise ImqError(st, name, lib.imq_last_error().decode())
+    return st

@@ -1,0 +1,310 @@
+// C ABI entry points (include/imq.h): argument checks, host/device pointer
+// handling, and translation of internal errors into imq_status codes.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "imq_internal.h"
+#include "util.cuh"
+
+struct imq_plan_s {
+    imq::Plan P;
+};
+
+namespace imq {
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+imq_status guard(F &&f) {
+    try {
+        f();
+        g_last_error.clear();
+        return IMQ_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return IMQ_OOM;
+    } catch (...) {
+        g_last_error = "unexpected internal error";
+        return IMQ_CUDA_ERROR;
+    }
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller buffer: in place for device memory, a stream-ordered
+// copy for host memory.
+struct DevIn {
+    const void *ptr = nullptr;
+    AsyncMem *tmp = nullptr;
+    DevIn(const void *p, size_t bytes, cudaStream_t s) {
+        if (is_device_ptr(p)) {
+            ptr = p;
+        } else {
+            tmp = new AsyncMem(bytes, s);
+            IMQ_CUDA(cudaMemcpyAsync(tmp->ptr, p, bytes, cudaMemcpyHostToDevice, s));
+            ptr = tmp->ptr;
+        }
+    }
+    DevIn(const DevIn &) = delete;
+    ~DevIn() { delete tmp; }
+};
+
+struct DevOut {
+    void *user = nullptr;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    AsyncMem *tmp = nullptr;
+    DevOut(void *p, size_t b, cudaStream_t s) : user(p), bytes(b), stream(s) {
+        if (is_device_ptr(p)) {
+            ptr = p;
+        } else {
+            tmp = new AsyncMem(b, s);
+            ptr = tmp->ptr;
+        }
+    }
+    DevOut(const DevOut &) = delete;
+    void finish() {   // copy a host-destined result back and wait for it
+        if (tmp) {
+            IMQ_CUDA(cudaMemcpyAsync(user, ptr, bytes, cudaMemcpyDeviceToHost, stream));
+            IMQ_CUDA(cudaStreamSynchronize(stream));
+        }
+    }
+    ~DevOut() { delete tmp; }
+};
+
+std::mutex g_dev_mu;
+int g_dev_ok[64] = {0};   // 0 unknown, 1 ok, -1 unsupported
+
+}  // namespace
+
+void check_device() {
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (dev >= 0 && dev < 64 && g_dev_ok[dev] == 1) return;
+    cudaDeviceProp prop;
+    IMQ_CUDA(cudaGetDeviceProperties(&prop, dev));
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        if (dev >= 0 && dev < 64) g_dev_ok[dev] = -1;
+        fail(IMQ_UNSUPPORTED, std::string("this library is built for sm_103a; device is ") + prop.name +
+                                  " (sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + ")");
+    }
+    if (dev >= 0 && dev < 64) g_dev_ok[dev] = 1;
+}
+
+}  // namespace imq
+
+using namespace imq;
+
+extern "C" {
+
+const char *imq_status_string(imq_status s) {
+    switch (s) {
+        case IMQ_OK: return "IMQ_OK";
+        case IMQ_INVALID_ARG: return "IMQ_INVALID_ARG";
+        case IMQ_DUPLICATE_POINTS: return "IMQ_DUPLICATE_POINTS";
+        case IMQ_CUDA_ERROR: return "IMQ_CUDA_ERROR";
+        case IMQ_OOM: return "IMQ_OOM";
+        case IMQ_NOT_CONVERGED: return "IMQ_NOT_CONVERGED";
+        case IMQ_NUMERICAL: return "IMQ_NUMERICAL";
+        case IMQ_UNSUPPORTED: return "IMQ_UNSUPPORTED";
+        case IMQ_TIMEOUT: return "IMQ_TIMEOUT";
+    }
+    return "IMQ_UNKNOWN";
+}
+
+const char *imq_last_error(void) { return g_last_error.c_str(); }
+
+const char *imq_version(void) { return "imq-gb300 0.1 (sm_103a)"; }
+
+imq_status imq_plan(const double *points, int64_t N, double c, int p, int leaf, const imq_options *opt,
+                    void *stream, imq_plan_t *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out || !points) fail(IMQ_INVALID_ARG, "imq_plan: NULL pointer");
+        if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
+        if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
+        if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
+        if (leaf < 1) fail(IMQ_INVALID_ARG, "imq_plan: leaf must be >= 1");
+        bool dups = false;
+        double x0 = 0, y0 = 0, side = -1;
+        if (opt) {
+            if (opt->struct_size < (int)offsetof(imq_options, reserved))
+                fail(IMQ_INVALID_ARG, "imq_plan: imq_options.struct_size too small");
+            if (opt->has_domain) {
+                if (!std::isfinite(opt->x0) || !std::isfinite(opt->y0) || !std::isfinite(opt->side) ||
+                    opt->side <= 0)
+                    fail(IMQ_INVALID_ARG, "imq_plan: domain must be finite with side > 0");
+                x0 = opt->x0;
+                y0 = opt->y0;
+                side = opt->side;
+            }
+            dups = opt->check_duplicates != 0;
+        }
+        check_device();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto *h = new imq_plan_s;
+        try {
+            Plan &P = h->P;
+            IMQ_CUDA(cudaGetDevice(&P.device));
+            P.N = N;
+            P.c = c;
+            P.p = p;
+            P.leaf = leaf;
+            P.x0 = x0;
+            P.y0 = y0;
+            P.side = side;
+            P.layout.build(p);
+            DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
+            build_tree(P, static_cast<const double *>(pts.ptr), s, dups);
+            ensure_ops(P, false, s);
+            IMQ_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+void imq_plan_destroy(imq_plan_t plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    delete plan;
+}
+
+imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] {
+        if (!plan || !v || !out) fail(IMQ_INVALID_ARG, "imq_matvec: NULL pointer");
+        if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_matvec: nrhs must be >= 1");
+        if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_matvec: unknown dtype");
+        Plan &P = plan->P;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t es = dt == IMQ_F32 ? 4 : 8;
+        const size_t bytes = es * (size_t)nrhs * P.N;
+        DevIn dv(v, bytes, s);
+        DevOut dout(out, bytes, s);
+        AsyncMem us(bytes, s), bs(bytes, s);
+        if (dt == IMQ_F32) {
+            gather_sorted<float, float>(P, static_cast<const float *>(dv.ptr), us.as<float>(), nrhs, s);
+            fmm_apply<float>(P, us.as<float>(), bs.as<float>(), nrhs, s);
+            scatter_sorted<float, float>(P, bs.as<float>(), static_cast<float *>(dout.ptr), nrhs, s);
+        } else {
+            gather_sorted<double, double>(P, static_cast<const double *>(dv.ptr), us.as<double>(), nrhs, s);
+            fmm_apply<double>(P, us.as<double>(), bs.as<double>(), nrhs, s);
+            scatter_sorted<double, double>(P, bs.as<double>(), static_cast<double *>(dout.ptr), nrhs, s);
+        }
+        dout.finish();
+    });
+}
+
+imq_status imq_dense_matvec(const double *points, int64_t N, double c, const void *v, void *out, int nrhs,
+                            imq_dtype dt, void *stream) {
+    return guard([&] {
+        if (!points || !v || !out) fail(IMQ_INVALID_ARG, "imq_dense_matvec: NULL pointer");
+        if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_dense_matvec: N must be in [1, 2^31-1]");
+        if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_dense_matvec: c must be finite and > 0");
+        if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_dense_matvec: nrhs must be >= 1");
+        if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_dense_matvec: unknown dtype");
+        check_device();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t es = dt == IMQ_F32 ? 4 : 8;
+        DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
+        DevIn dv(v, es * (size_t)nrhs * N, s);
+        DevOut dout(out, es * (size_t)nrhs * N, s);
+        dense_matvec_dev(static_cast<const double *>(pts.ptr), N, c, dv.ptr, dout.ptr, nrhs, dt, s);
+        dout.finish();
+    });
+}
+
+imq_status imq_plan_get_info(imq_plan_t plan, imq_plan_info *info) {
+    return guard([&] {
+        if (!plan || !info) fail(IMQ_INVALID_ARG, "imq_plan_get_info: NULL pointer");
+        const Plan &P = plan->P;
+        std::memset(info, 0, sizeof(*info));
+        info->n_points = P.N;
+        info->n_boxes = P.nbox;
+        info->n_leaves = P.nleaf;
+        info->max_level = P.max_level;
+        info->p = P.p;
+        info->leaf = P.leaf;
+        info->k_real = P.layout.K;
+        info->x0 = P.x0;
+        info->y0 = P.y0;
+        info->side = P.side;
+        info->c = P.c;
+        info->n_u = P.U.total;
+        info->n_v = P.V.total;
+        info->n_w = P.W.total;
+        info->n_x = P.X.total;
+        info->p2p_pairs = P.p2p_pairs;
+        info->m2l_pairs = P.m2l_pairs;
+        info->device_bytes = P.device_bytes();
+    });
+}
+
+imq_status imq_plan_export_tree(imq_plan_t plan, uint32_t *codes, int64_t *perm, int32_t *level, uint32_t *prefix,
+                                int64_t *begin, int64_t *end, int32_t *parent, int32_t *child) {
+    return guard([&] {
+        if (!plan) fail(IMQ_INVALID_ARG, "imq_plan_export_tree: NULL plan");
+        const Plan &P = plan->P;
+        auto d2h = [](void *dst, const DevMem &src, size_t bytes) {
+            if (dst) IMQ_CUDA(cudaMemcpy(dst, src.ptr, bytes, cudaMemcpyDeviceToHost));
+        };
+        d2h(codes, P.codes, sizeof(uint32_t) * P.N);
+        d2h(level, P.level, sizeof(int32_t) * P.nbox);
+        d2h(prefix, P.prefix, sizeof(uint32_t) * P.nbox);
+        d2h(parent, P.parent, sizeof(int32_t) * P.nbox);
+        d2h(child, P.child, sizeof(int32_t) * 4 * P.nbox);
+        if (perm) {
+            std::vector<int32_t> t(P.N);
+            d2h(t.data(), P.perm, sizeof(int32_t) * P.N);
+            for (int64_t i = 0; i < P.N; ++i) perm[i] = t[i];
+        }
+        if (begin || end) {
+            std::vector<int32_t> b(P.nbox), e(P.nbox);
+            d2h(b.data(), P.begin, sizeof(int32_t) * P.nbox);
+            d2h(e.data(), P.end, sizeof(int32_t) * P.nbox);
+            for (int i = 0; i < P.nbox; ++i) {
+                if (begin) begin[i] = b[i];
+                if (end) end[i] = e[i];
+            }
+        }
+    });
+}
+
+imq_status imq_plan_export_list(imq_plan_t plan, char which, int32_t *offsets, int32_t *items) {
+    return guard([&] {
+        if (!plan) fail(IMQ_INVALID_ARG, "imq_plan_export_list: NULL plan");
+        const Plan &P = plan->P;
+        const ListCSR *L = nullptr;
+        switch (which) {
+            case 'U': L = &P.U; break;
+            case 'V': L = &P.V; break;
+            case 'W': L = &P.W; break;
+            case 'X': L = &P.X; break;
+            default: fail(IMQ_INVALID_ARG, "imq_plan_export_list: which must be U, V, W or X");
+        }
+        if (offsets) IMQ_CUDA(cudaMemcpy(offsets, L->off.ptr, sizeof(int32_t) * (P.nbox + 1), cudaMemcpyDeviceToHost));
+        if (items && L->total > 0)
+            IMQ_CUDA(cudaMemcpy(items, L->items.ptr, sizeof(int32_t) * L->total, cudaMemcpyDeviceToHost));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,589 @@
+// FMM kernels of the fast IMQ product on the adaptive quadtree.
+//
+// Paper Section 2.2 (Eq. (11)-(13), Algorithm 1): the moments v_k, w_k of a
+// block about its centre are the multipole coefficients (P2M); the far-field
+// evaluation d h [sin v + cos w] at the points of S_p is the multipole
+// evaluated at a target (M2P); the near field on NS_p is the direct sum (P2P,
+// p2p.cu).  The fast-multipole translations (M2M, M2L, L2L, L2P, P2L) move
+// the same expansions between boxes so that each target evaluates one local
+// expansion instead of one multipole per well-separated box.
+//
+// Coefficient layout and scaling: see imq_internal.h.  Every kernel is a
+// template over the arithmetic type (float: the FP32 path, with point
+// coordinates stored as FP32 offsets from their leaf centre; double: the FP64
+// path on absolute FP64 coordinates).
+#include <algorithm>
+#include <type_traits>
+
+#include "imq_internal.h"
+#include "ptx.cuh"
+#include "util.cuh"
+
+namespace imq {
+namespace {
+
+constexpr int kMaxCol = 10;   // (IMQ_MAX_P / 2) + 1 coefficients per m-column
+
+__device__ __forceinline__ int col_base(int m, int p) {
+    // first slot of column m in the m-major parity-even layout
+    int s = 0;
+    for (int mm = 0; mm < m; ++mm) s += ((p - mm) / 2 + 1) * (mm ? 2 : 1);
+    return s;
+}
+
+template <class T>
+__device__ __forceinline__ T box_side(double S, int lev) {
+    return (T)(S / (double)(1 << lev));
+}
+
+// offset of sorted point i from the centre of the box with centre cb,
+// where leafc is the centre of the leaf that holds i.
+template <class T>
+__device__ __forceinline__ void point_offset(int i, const float2 *loc, const double2 *pos, double2 cb, double2 leafc,
+                                             T &x, T &y) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 l = loc[i];
+        x = l.x + (float)(leafc.x - cb.x);
+        y = l.y + (float)(leafc.y - cb.y);
+    } else {
+        const double2 q = pos[i];
+        x = q.x - cb.x;
+        y = q.y - cb.y;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T rsq(T v) {
+    if constexpr (std::is_same<T, float>::value) return rsqrtf(v);
+    else return 1.0 / sqrt(v);
+}
+
+// ------------------------------------------------------------------ gather / scatter
+template <class Tin, class T>
+__global__ void k_gather(const Tin *__restrict__ v, const int32_t *__restrict__ perm, int64_t n, T *__restrict__ us) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) us[i] = (T)v[perm[i]];
+}
+
+template <class T, class Tout>
+__global__ void k_scatter(const T *__restrict__ bs, const int32_t *__restrict__ perm, int64_t n, Tout *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = (Tout)bs[i];
+}
+
+// ------------------------------------------------------------------ P2M
+// Mh_n^m = Ptilde_n^m(0) sum_j u_j conj(w_j)^m |w_j|^{n-m},  w_j = (y_j - z_B)/h_B.
+template <class T>
+__global__ void k_p2m(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
+                      const int32_t *__restrict__ end, const int32_t *__restrict__ level,
+                      const double2 *__restrict__ centre, const float2 *__restrict__ loc,
+                      const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ M, int K, int p,
+                      const T *__restrict__ coef, double S) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nleaf || lane > p) return;
+    const int b = leaves[warp];
+    const int m = lane;
+    const T inv_h = (T)1 / box_side<T>(S, level[b]);
+    const double2 cb = centre[b];
+    T ar[kMaxCol], ai[kMaxCol];
+#pragma unroll
+    for (int k = 0; k < kMaxCol; ++k) ar[k] = ai[k] = 0;
+    for (int j = begin[b]; j < end[b]; ++j) {
+        T wx, wy;
+        point_offset<T>(j, loc, pos, cb, cb, wx, wy);
+        wx *= inv_h;
+        wy *= inv_h;
+        const T uj = u[j];
+        T zr = uj, zi = 0;
+        for (int t = 0; t < m; ++t) {   // u * conj(w)^m
+            const T nr = zr * wx + zi * wy;
+            zi = zi * wx - zr * wy;
+            zr = nr;
+        }
+        const T r2 = wx * wx + wy * wy;
+#pragma unroll
+        for (int k = 0; k < kMaxCol; ++k) {
+            if (m + 2 * k <= p) {
+                ar[k] += zr;
+                ai[k] += zi;
+                zr *= r2;
+                zi *= r2;
+            }
+        }
+    }
+    int slot = col_base(m, p);
+    T *Mb = M + (int64_t)b * K;
+#pragma unroll
+    for (int k = 0; k < kMaxCol; ++k) {
+        if (m + 2 * k <= p) {
+            const T cc = coef[slot];
+            Mb[slot] = cc * ar[k];
+            if (m > 0) Mb[slot + 1] = cc * ai[k];
+            slot += m ? 2 : 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ M2M / L2L
+template <class T>
+__global__ void k_m2m(int lb, const int32_t *__restrict__ child, T *__restrict__ M, const T *__restrict__ op, int K) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Mc = reinterpret_cast<T *>(smraw);
+    const int b = lb + blockIdx.x;
+    int ch[4];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ch[q] = child[4 * b + q];
+        any |= ch[q] >= 0;
+    }
+    if (!any) return;   // a leaf keeps its P2M moments
+    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
+        const int q = e / K, i = e - q * K;
+        Mc[e] = ch[q] >= 0 ? M[(int64_t)ch[q] * K + i] : (T)0;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < K; o += blockDim.x) {
+        T acc = 0;
+        for (int q = 0; q < 4; ++q) {
+            if (ch[q] < 0) continue;
+            const T *opq = op + (int64_t)q * K * K;
+            for (int i = 0; i < K; ++i) acc += opq[(int64_t)i * K + o] * Mc[q * K + i];
+        }
+        M[(int64_t)b * K + o] = acc;
+    }
+}
+
+template <class T>
+__global__ void k_l2l(int lb, const int32_t *__restrict__ parent, const uint32_t *__restrict__ prefix,
+                      T *__restrict__ L, const T *__restrict__ op, int K) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Lp = reinterpret_cast<T *>(smraw);
+    const int b = lb + blockIdx.x;
+    const int pb = parent[b];
+    const int q = (int)(prefix[b] & 3u);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) Lp[i] = L[(int64_t)pb * K + i];
+    __syncthreads();
+    const T *opq = op + (int64_t)q * K * K;
+    for (int o = threadIdx.x; o < K; o += blockDim.x) {
+        T acc = 0;
+        for (int i = 0; i < K; ++i) acc += opq[(int64_t)i * K + o] * Lp[i];
+        L[(int64_t)b * K + o] += acc;
+    }
+}
+
+// ------------------------------------------------------------------ M2L (SIMT, batched by offset class)
+// For a tile of TB target boxes of one level and each of the 40 offset
+// classes, the class operator (K x K, input-major, rows padded to Kp = 4R)
+// and the gathered source multipoles are staged in shared memory; thread
+// (ty, tx) accumulates rows [ty*R, ty*R+R) of target tx.
+template <class T, int R, int TB>
+__global__ void __launch_bounds__(256) k_m2l(int lb, int nl, const int32_t *__restrict__ vtab,
+                                             const T *__restrict__ M, T *__restrict__ L, const T *__restrict__ ops,
+                                             int K) {
+    constexpr int Kp = 4 * R;
+    constexpr int MS = TB + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Top = reinterpret_cast<T *>(smraw);                 // [K][Kp]
+    T *Ms = Top + (size_t)K * Kp;                          // [K][TB+1]
+    const int tx = threadIdx.x % TB, ty = threadIdx.x / TB;
+    const int b0 = lb + blockIdx.x * TB;
+    const int nbt = min(TB, lb + nl - b0);
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    for (int o = 0; o < kOffsetClasses; ++o) {
+        const int src = tx < nbt ? vtab[(int64_t)kOffsetClasses * (b0 + tx) + o] : -1;
+        if (!__syncthreads_or(src >= 0)) continue;
+        const T *g = ops + (size_t)o * K * Kp;
+        for (int e = threadIdx.x; e < K * Kp; e += blockDim.x) Top[e] = g[e];
+        for (int e = threadIdx.x; e < K * TB; e += blockDim.x) {
+            const int cbox = e / K, i = e - cbox * K;
+            const int s = cbox < nbt ? vtab[(int64_t)kOffsetClasses * (b0 + cbox) + o] : -1;
+            Ms[i * MS + cbox] = s >= 0 ? M[(int64_t)s * K + i] : (T)0;
+        }
+        __syncthreads();
+        if (ty * R < K) {
+            const T *trow = Top + ty * R;
+            for (int i = 0; i < K; ++i) {
+                const T mv = Ms[i * MS + tx];
+                const T *t = trow + (size_t)i * Kp;
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] += t[r] * mv;
+            }
+        }
+        __syncthreads();
+    }
+    if (tx < nbt) {
+        T *Lb = L + (int64_t)(b0 + tx) * K;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = ty * R + r;
+            if (row < K) Lb[row] = acc[r];
+        }
+    }
+}
+
+// Fallback M2L without shared-memory staging (FP64 at large p): one thread per
+// (target box, output row), operators read through the cache hierarchy.
+template <class T>
+__global__ void k_m2l_direct(int lb, int nl, const int32_t *__restrict__ vtab, const T *__restrict__ M,
+                             T *__restrict__ L, const T *__restrict__ ops, int K, int Kp) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= (int64_t)nl * K) return;
+    const int b = lb + (int)(g / K), row = (int)(g % K);
+    T acc = 0;
+    for (int o = 0; o < kOffsetClasses; ++o) {
+        const int s = vtab[(int64_t)kOffsetClasses * b + o];
+        if (s < 0) continue;
+        const T *op = ops + (size_t)o * K * Kp + row;
+        const T *Ms = M + (int64_t)s * K;
+        for (int i = 0; i < K; ++i) acc += op[(size_t)i * Kp] * Ms[i];
+    }
+    L[(int64_t)b * K + row] = acc;
+}
+
+// ------------------------------------------------------------------ irregular-harmonic evaluation
+// G_n^m(v) = Ptilde_n^m(cos th) e^{i m om} (h/rho)^n / rho for n+m even is produced
+// column by column; F(n, slot, gr, gi) consumes each term.
+template <class T, class F>
+__device__ __forceinline__ void irregular_column(int m, int p, T a, T t, T zr, T zi, T gmm_r, T gmm_i, F &&f,
+                                                 int slot) {
+    // G_m^m given; step n upward with the normalised three-term recurrence.
+    T g2r = 0, g2i = 0, g1r = gmm_r, g1i = gmm_i;
+    f(m, slot, g1r, g1i);
+    slot += m ? 2 : 1;
+    for (int n = m + 1; n <= p; ++n) {
+        const T c1 = (T)(2 * n - 1) * t * a;
+        const T c2 = sqrt((T)((n - 1) * (n - 1) - m * m)) * a * a;
+        const T inv = rsq<T>((T)(n * n - m * m));
+        const T gr = (c1 * g1r - c2 * g2r) * inv;
+        const T gi = (c1 * g1i - c2 * g2i) * inv;
+        g2r = g1r; g2i = g1i; g1r = gr; g1i = gi;
+        if (((n + m) & 1) == 0) {
+            f(n, slot, gr, gi);
+            slot += m ? 2 : 1;
+        }
+    }
+    (void)zr;
+    (void)zi;
+}
+
+// ------------------------------------------------------------------ P2L (X list)
+// Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c.
+template <class T>
+__global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff,
+                      const int32_t *__restrict__ xitems, const int32_t *__restrict__ begin,
+                      const int32_t *__restrict__ end, const int32_t *__restrict__ level,
+                      const double2 *__restrict__ centre, const float2 *__restrict__ loc,
+                      const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p,
+                      double S, T c) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nxb || lane > p) return;
+    const int b = xboxes[warp];
+    const int l = lane;
+    const T h = box_side<T>(S, level[b]);
+    const double2 cb = centre[b];
+    T ar[kMaxCol], ai[kMaxCol];
+#pragma unroll
+    for (int k = 0; k < kMaxCol; ++k) ar[k] = ai[k] = 0;
+    T dmm = 1;
+    for (int i = 1; i <= l; ++i) dmm *= sqrt((T)(2 * i - 1) / (T)(2 * i));
+    for (int e = xoff[b]; e < xoff[b + 1]; ++e) {
+        const int s = xitems[e];
+        const double2 cs = centre[s];
+        for (int j = begin[s]; j < end[s]; ++j) {
+            T vx, vy;
+            point_offset<T>(j, loc, pos, cb, cs, vx, vy);
+            const T rho2 = vx * vx + vy * vy + c * c;
+            const T inv = rsq<T>(rho2);
+            const T a = h * inv, t = -c * inv;
+            const T zr0 = vx * inv * a, zi0 = vy * inv * a;
+            T gr = dmm * inv * u[j], gi = 0;
+            for (int q = 0; q < l; ++q) {   // times (zeta a)^l
+                const T nr = gr * zr0 - gi * zi0;
+                gi = gr * zi0 + gi * zr0;
+                gr = nr;
+            }
+            int k = 0;
+            irregular_column<T>(l, p, a, t, zr0, zi0, gr, gi,
+                                [&](int, int, T xr, T xi) {
+                                    ar[k] += xr;
+                                    ai[k] += xi;
+                                    ++k;
+                                },
+                                0);
+        }
+    }
+    int slot = col_base(l, p);
+    T *Lb = L + (int64_t)b * K;
+    for (int k = 0; k < kMaxCol && l + 2 * k <= p; ++k) {
+        Lb[slot] += ar[k];
+        if (l > 0) Lb[slot + 1] += ai[k];
+        slot += l ? 2 : 1;
+    }
+}
+
+// ------------------------------------------------------------------ L2P + M2P (W list)
+template <class T>
+__global__ void k_far(int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin,
+                      const int32_t *__restrict__ end, const int32_t *__restrict__ level,
+                      const double2 *__restrict__ centre, const float2 *__restrict__ loc,
+                      const double2 *__restrict__ pos, const int32_t *__restrict__ woff,
+                      const int32_t *__restrict__ witems, const T *__restrict__ M, const T *__restrict__ L,
+                      const T *__restrict__ coef, int K, int p, double S, T c, T *__restrict__ bs) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nleaf) return;
+    const int b = leaves[warp];
+    const double2 cb = centre[b];
+    const T inv_h = (T)1 / box_side<T>(S, level[b]);
+    const T *Lb = L + (int64_t)b * K;
+    for (int i = begin[b] + lane; i < end[b]; i += 32) {
+        T wx, wy;
+        point_offset<T>(i, loc, pos, cb, cb, wx, wy);
+        T phi = 0;
+        // L2P: sum eps_m Ptilde_n^m(0) Re(Lh_n^m conj(w)^m |w|^{n-m}), w = (x - c_B)/h
+        {
+            const T ux = wx * inv_h, uy = wy * inv_h;
+            const T r2 = ux * ux + uy * uy;
+            T zr = 1, zi = 0;
+            int slot = 0;
+            for (int m = 0; m <= p; ++m) {
+                T qr = zr, qi = zi;
+                const T eps = m ? (T)2 : (T)1;
+                for (int n = m; n <= p; n += 2) {
+                    const T lr = Lb[slot];
+                    const T li = m ? Lb[slot + 1] : (T)0;
+                    phi += eps * coef[slot] * (lr * qr - li * qi);
+                    qr *= r2;
+                    qi *= r2;
+                    slot += m ? 2 : 1;
+                }
+                const T nr = zr * ux + zi * uy;
+                zi = zi * ux - zr * uy;
+                zr = nr;
+            }
+        }
+        // M2P over the W list: sum eps_m Re(Mh_n^m G_n^m(X_i - Z_S)), vertical component +c
+        for (int e = woff[b]; e < woff[b + 1]; ++e) {
+            const int s = witems[e];
+            const double2 cs = centre[s];
+            T vx, vy;
+            point_offset<T>(i, loc, pos, cs, cb, vx, vy);
+            const T hs = box_side<T>(S, level[s]);
+            const T rho2 = vx * vx + vy * vy + c * c;
+            const T inv = rsq<T>(rho2);
+            const T a = hs * inv, t = c * inv;
+            const T zr0 = vx * inv * a, zi0 = vy * inv * a;
+            const T *Ms = M + (int64_t)s * K;
+            T gr = inv, gi = 0;   // G_0^0
+            int slot = 0;
+            for (int m = 0; m <= p; ++m) {
+                if (m > 0) {
+                    const T f = sqrt((T)(2 * m - 1) / (T)(2 * m));
+                    const T nr = (gr * zr0 - gi * zi0) * f;
+                    gi = (gr * zi0 + gi * zr0) * f;
+                    gr = nr;
+                }
+                const T eps = m ? (T)2 : (T)1;
+                irregular_column<T>(m, p, a, t, zr0, zi0, gr, gi,
+                                    [&](int, int sl, T xr, T xi) {
+                                        const T mr = Ms[sl];
+                                        const T mi = m ? Ms[sl + 1] : (T)0;
+                                        phi += eps * (mr * xr - mi * xi);
+                                    },
+                                    slot);
+                slot += ((p - m) / 2 + 1) * (m ? 2 : 1);
+            }
+        }
+        bs[i] = phi;
+    }
+}
+
+template <class T>
+void upload(DevMem &dst, const std::vector<double> &src, cudaStream_t s) {
+    std::vector<T> tmp(src.begin(), src.end());
+    dst.alloc(sizeof(T) * std::max<size_t>(1, tmp.size()));
+    IMQ_CUDA(cudaMemcpyAsync(dst.ptr, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+}
+
+int m2l_rows(int K) {   // R bucket: rows per thread, 4 row groups
+    const int r = (K + 3) / 4;
+    const int buckets[] = {12, 20, 24, 32, 40, 48};
+    for (int b : buckets)
+        if (r <= b) return b;
+    return -1;
+}
+
+template <class T>
+void launch_m2l(int R, int lb, int nl, const int32_t *vtab, const T *M, T *L, const T *ops, int K, cudaStream_t s) {
+    constexpr int TB = 64;
+    const size_t smem = sizeof(T) * ((size_t)K * 4 * R + (size_t)K * (TB + 1));
+    const unsigned grid = (unsigned)((nl + TB - 1) / TB);
+    if (smem > 200 * 1024) {
+        k_m2l_direct<T><<<blocks_for((int64_t)nl * K, 128), 128, 0, s>>>(lb, nl, vtab, M, L, ops, K, 4 * R);
+        IMQ_LAUNCH_CHECK();
+        return;
+    }
+#define IMQ_M2L_CASE(RR)                                                                                  \
+    case RR: {                                                                                            \
+        auto kern = k_m2l<T, RR, TB>;                                                                     \
+        IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
+        kern<<<grid, 256, smem, s>>>(lb, nl, vtab, M, L, ops, K);                                         \
+        break;                                                                                            \
+    }
+    switch (R) {
+        IMQ_M2L_CASE(12)
+        IMQ_M2L_CASE(20)
+        IMQ_M2L_CASE(24)
+        IMQ_M2L_CASE(32)
+        IMQ_M2L_CASE(40)
+        IMQ_M2L_CASE(48)
+        default: fail(IMQ_UNSUPPORTED, "M2L: expansion too large");
+    }
+#undef IMQ_M2L_CASE
+    IMQ_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+int64_t Plan::device_bytes() const {
+    int64_t t = 0;
+    const DevMem *all[] = {&codes, &perm, &level, &prefix, &begin, &end, &parent, &child, &centre, &leaves,
+                           &U.off, &U.items, &V.off, &V.items, &W.off, &W.items, &X.off, &X.items,
+                           &colleagues, &vtab, &ucum, &uoff, &pos, &loc, &leaf_of,
+                           &ops32.m2m, &ops32.l2l, &ops32.m2l, &ops32.p2mc,
+                           &ops64.m2m, &ops64.l2l, &ops64.m2l, &ops64.p2mc};
+    for (auto *d : all) t += (int64_t)d->bytes;
+    return t;
+}
+
+void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
+    TypedOps &O = fp64 ? P.ops64 : P.ops32;
+    if (O.ready) return;
+    const int K = P.layout.K;
+    if (P.h_m2m.empty()) {
+        build_m2m_ops(P.layout, P.h_m2m);
+        build_l2l_ops(P.layout, P.h_l2l);
+        p2m_coefficients(P.layout, P.h_p2mc);
+        const int R = m2l_rows(K);
+        if (R < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
+        const int Kp = 4 * R;
+        const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
+        P.h_m2l.assign((size_t)std::max(1, nlev) * kOffsetClasses * K * Kp, 0.0);
+        std::vector<double> tmp;
+        for (int li = 0; li < nlev; ++li) {
+            const double h = P.side / (double)(1 << (P.m2l_level_lo + li));
+            build_m2l_ops(P.layout, h, P.c, tmp);
+            for (int o = 0; o < kOffsetClasses; ++o)
+                for (int i = 0; i < K; ++i)
+                    for (int r = 0; r < K; ++r)
+                        P.h_m2l[(((size_t)li * kOffsetClasses + o) * K + i) * Kp + r] =
+                            tmp[((size_t)o * K + i) * K + r];
+        }
+    }
+    if (fp64) {
+        upload<double>(O.m2m, P.h_m2m, s);
+        upload<double>(O.l2l, P.h_l2l, s);
+        upload<double>(O.m2l, P.h_m2l, s);
+        upload<double>(O.p2mc, P.h_p2mc, s);
+    } else {
+        upload<float>(O.m2m, P.h_m2m, s);
+        upload<float>(O.l2l, P.h_l2l, s);
+        upload<float>(O.m2l, P.h_m2l, s);
+        upload<float>(O.p2mc, P.h_p2mc, s);
+    }
+    O.ready = true;
+}
+
+template <class T>
+void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
+
+template <class T>
+void fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s) {
+    const bool f64 = std::is_same<T, double>::value;
+    ensure_ops(P, f64, s);
+    TypedOps &O = f64 ? P.ops64 : P.ops32;
+    const int K = P.layout.K, p = P.p, nb = P.nbox;
+    AsyncMem Mbuf(sizeof(T) * (size_t)nb * K, s), Lbuf(sizeof(T) * (size_t)nb * K, s);
+    T *M = Mbuf.as<T>(), *L = Lbuf.as<T>();
+    const T *m2m = O.m2m.as<T>(), *l2l = O.l2l.as<T>(), *m2l = O.m2l.as<T>(), *coef = O.p2mc.as<T>();
+    const int R = m2l_rows(K);
+    const int Kp = 4 * R;
+    for (int r = 0; r < nrhs; ++r) {
+        const T *u = us + (size_t)r * P.N;
+        T *b = bs + (size_t)r * P.N;
+        IMQ_CUDA(cudaMemsetAsync(M, 0, sizeof(T) * (size_t)nb * K, s));
+        IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)nb * K, s));
+        // upward pass
+        k_p2m<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
+            P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
+            P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, p, coef, P.side);
+        IMQ_LAUNCH_CHECK();
+        for (int lev = P.max_level - 1; lev >= 2; --lev) {
+            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+            if (nl <= 0) continue;
+            k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
+            IMQ_LAUNCH_CHECK();
+        }
+        // interaction: M2L per level, P2L over X lists
+        for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
+            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+            const T *ops = m2l + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * K * Kp;
+            launch_m2l<T>(R, lb, nl, P.vtab.as<int32_t>(), M, L, ops, K, s);
+        }
+        if (P.X.total > 0) {
+            k_p2l<T><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
+                P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(),
+                P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
+                P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, p, P.side, (T)P.c);
+            IMQ_LAUNCH_CHECK();
+        }
+        // downward pass
+        for (int lev = 3; lev <= P.max_level; ++lev) {
+            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+            if (nl <= 0) continue;
+            k_l2l<T><<<nl, 128, sizeof(T) * K, s>>>(lb, P.parent.as<int32_t>(), P.prefix.as<uint32_t>(), L, l2l, K);
+            IMQ_LAUNCH_CHECK();
+        }
+        // evaluation: L2P + M2P writes b, P2P adds the near field
+        k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
+            P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
+            P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
+            P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, (T)P.c, b);
+        IMQ_LAUNCH_CHECK();
+        p2p_apply<T>(P, u, b, s);
+    }
+}
+
+template void fmm_apply<float>(Plan &, const float *, float *, int, cudaStream_t);
+template void fmm_apply<double>(Plan &, const double *, double *, int, cudaStream_t);
+
+template <class Tin, class T>
+void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s) {
+    for (int r = 0; r < nrhs; ++r) {
+        k_gather<Tin, T><<<blocks_for(P.N, 256), 256, 0, s>>>(v + (size_t)r * P.N, P.perm.as<int32_t>(), P.N,
+                                                              us + (size_t)r * P.N);
+        IMQ_LAUNCH_CHECK();
+    }
+}
+
+template <class T, class Tout>
+void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_t s) {
+    for (int r = 0; r < nrhs; ++r) {
+        k_scatter<T, Tout><<<blocks_for(P.N, 256), 256, 0, s>>>(bs + (size_t)r * P.N, P.perm.as<int32_t>(), P.N,
+                                                               out + (size_t)r * P.N);
+        IMQ_LAUNCH_CHECK();
+    }
+}
+
+template void gather_sorted<float, float>(const Plan &, const float *, float *, int, cudaStream_t);
+template void gather_sorted<double, double>(const Plan &, const double *, double *, int, cudaStream_t);
+template void scatter_sorted<float, float>(const Plan &, const float *, float *, int, cudaStream_t);
+template void scatter_sorted<double, double>(const Plan &, const double *, double *, int, cudaStream_t);
+
+}  // namespace imq

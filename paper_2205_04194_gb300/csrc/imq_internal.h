@@ -1,0 +1,154 @@
+// Internal declarations of the GB300 IMQ library (not part of the ABI).
+//
+// Geometry (paper Section 2.2, Eq. (11)-(13)): sources Y_j = (x_j, -c/2),
+// targets X_i = (x_i, +c/2); multipole centres Z_B = (centre_B, -c/2) lie in
+// the source plane, local centres C_B = (centre_B, +c/2) in the target plane.
+//
+// Expansion coefficients are stored in a parity-reduced real layout: because
+// every source lies in the plane of its multipole centre and every target in
+// the plane of its local centre, only the (n, m) terms with n + m even carry
+// information (P_n^m(0) = 0 otherwise).  Slots run m-major: for m = 0..p, for
+// n = m, m+2, ..., <= p: one real (m = 0) or a (Re, Im) pair (m > 0).
+//
+// Coefficients are scaled by the box side h so that FP32 stays in range:
+//   multipole  Mh_n^m = M_n^m * sqrt((n+m)!(n-m)!) / h^n
+//   local      Lh_n^m = L_n^m * h^n / sqrt((n+m)!(n-m)!)
+// with M_n^m = sum_j u_j conj(U_n^m(Y_j - Z)) and Phi(X) = sum L_n^m conj(U_n^m(X - C)),
+// U/T the regular/irregular solid harmonics U_n^m = r^n P_n^m e^{im om}/(n+m)!,
+// T_n^m = (n-m)! P_n^m e^{im om}/r^{n+1}  (P_n^m without Condon-Shortley phase).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/imq.h"
+
+namespace imq {
+
+struct Error {
+    imq_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(imq_status s, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+#define IMQ_CUDA(call) ::imq::cuda_check((call), #call, __FILE__, __LINE__)
+#define IMQ_LAUNCH_CHECK() ::imq::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// ---------------------------------------------------------------- device memory
+struct DevMem {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept : ptr(o.ptr), bytes(o.bytes) { o.ptr = nullptr; o.bytes = 0; }
+    DevMem &operator=(DevMem &&o) noexcept {
+        release();
+        ptr = o.ptr; bytes = o.bytes; o.ptr = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~DevMem() { release(); }
+    void alloc(size_t n);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Stream-ordered scratch (cudaMallocAsync) freed on the same stream.
+struct AsyncMem {
+    void *ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    AsyncMem(size_t bytes, cudaStream_t s);
+    AsyncMem(const AsyncMem &) = delete;
+    AsyncMem &operator=(const AsyncMem &) = delete;
+    ~AsyncMem();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ---------------------------------------------------------------- layout
+struct Layout {
+    int p = 0;
+    int K = 0;                     // reals per expansion
+    std::vector<int> slot_n, slot_m, slot_part;   // per real slot
+    std::vector<int> re_slot;      // [(p+1)*(p+1)] index n*(p+1)+m -> slot of Re part or -1
+    std::vector<int> im_slot;      // same for Im part (-1 for m = 0 or odd n+m)
+    void build(int p_);
+};
+
+constexpr int kOffsetClasses = 40;          // V-list offsets in [-3,3]^2 minus [-1,1]^2
+int offset_class(int dx, int dy);           // -1 for |dx|,|dy| <= 1 or out of range
+void offset_of_class(int k, int *dx, int *dy);
+
+// ---------------------------------------------------------------- operators (host, FP64)
+// Real K x K matrices stored input-major: op[i * K + o] multiplies input slot i into output o.
+void build_m2m_ops(const Layout &L, std::vector<double> &out);          // [4][K][K], quadrant q = 2*ybit + xbit
+void build_l2l_ops(const Layout &L, std::vector<double> &out);          // [4][K][K]
+void build_m2l_ops(const Layout &L, double h, double c, std::vector<double> &out);  // [40][K][K] for side h
+void p2m_coefficients(const Layout &L, std::vector<double> &coef);      // per slot: Ptilde_n^m(0)
+
+// ---------------------------------------------------------------- plan
+struct ListCSR {
+    DevMem off, items;   // int32[nbox+1], int32[total]
+    int64_t total = 0;
+};
+
+struct TypedOps {        // operator set in one precision
+    DevMem m2m, l2l, m2l, p2mc;
+    bool ready = false;
+};
+
+struct Plan {
+    int device = 0;
+    int64_t N = 0;
+    double c = 0, x0 = 0, y0 = 0, side = 1;
+    int p = 0, leaf = 0;
+    int nbox = 0, nleaf = 0, max_level = 0;
+    int m2l_level_lo = 2, m2l_level_hi = 1;   // levels holding V pairs
+    Layout layout;
+    std::vector<int> level_start;              // boxes of level l: [level_start[l], level_start[l+1])
+    // tree, device
+    DevMem codes;      // uint32[N] sorted
+    DevMem perm;       // int64[N] sorted -> input
+    DevMem level, prefix, begin, end, parent, child;   // per box (child: int32[4*nbox])
+    DevMem centre;     // double2[nbox]
+    DevMem leaves;     // int32[nleaf]
+    ListCSR U, V, W, X;
+    DevMem colleagues; // int32[9*nbox]
+    DevMem vtab;       // int32[40*nbox] V source per offset class, -1 if none
+    DevMem xboxes;     // int32[nxbox] boxes whose X list is not empty
+    int nxbox = 0;
+    DevMem utot;       // int32[nbox] total U-list source points of a leaf
+    DevMem ucum;       // int32[n_u]: per leaf list, exclusive prefix of source counts
+    DevMem uoff;       // float2[n_u]: (centre_target - centre_source)
+    // points, device, sorted order
+    DevMem pos;        // double2[N]
+    DevMem loc;        // float2[N]  offset from the leaf centre
+    DevMem leaf_of;    // int32[N]
+    // operators
+    std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies
+    TypedOps ops32, ops64;
+    // statistics
+    int64_t p2p_pairs = 0, m2l_pairs = 0;
+    int64_t device_bytes() const;
+};
+
+// tree.cu
+void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups);
+// expansions.cu
+void ensure_ops(Plan &P, bool fp64, cudaStream_t s);
+template <class T>
+void fmm_apply(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
+template <class Tin, class T>
+void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s);
+template <class T, class Tout>
+void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_t s);
+// dense.cu
+void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,
+                      int nrhs, imq_dtype dt, cudaStream_t s);
+// api.cu helpers
+void check_device();
+
+}  // namespace imq

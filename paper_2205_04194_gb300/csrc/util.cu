@@ -1,0 +1,160 @@
+// Host utilities of the library: error handling, device memory, exclusive scan.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "imq_internal.h"
+#include "util.cuh"
+
+namespace imq {
+
+void fail(imq_status s, const std::string &msg) { throw Error{s, msg}; }
+
+void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        fail(IMQ_OOM, buf);
+    }
+    fail(IMQ_CUDA_ERROR, buf);
+}
+
+void DevMem::alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        (void)cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? IMQ_OOM : IMQ_CUDA_ERROR,
+             std::string("cudaMalloc of ") + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = n;
+}
+
+void DevMem::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+AsyncMem::AsyncMem(size_t bytes, cudaStream_t s) : stream(s) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        (void)cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? IMQ_OOM : IMQ_CUDA_ERROR,
+             std::string("cudaMallocAsync failed: ") + cudaGetErrorString(e));
+    }
+}
+
+AsyncMem::~AsyncMem() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+// ------------------------------------------------------------------ device error word
+static std::mutex g_err_mu;
+static int *g_err_word[64] = {nullptr};
+
+int *device_error_word() {
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    if (!g_err_word[dev]) {
+        int *p = nullptr;
+        IMQ_CUDA(cudaMalloc(&p, sizeof(int)));
+        IMQ_CUDA(cudaMemset(p, 0, sizeof(int)));
+        g_err_word[dev] = p;
+    }
+    return g_err_word[dev];
+}
+
+// ------------------------------------------------------------------ scan
+namespace {
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+template <class T>
+__device__ T block_exclusive_scan(T v, T *sh, T *total) {
+    // Hillis-Steele over a 1024-thread block; returns the exclusive prefix of v.
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int off = 1; off < kScanBlock; off <<= 1) {
+        T a = tid >= off ? sh[tid - off] : T(0);
+        __syncthreads();
+        sh[tid] += a;
+        __syncthreads();
+    }
+    T incl = sh[tid];
+    if (total) *total = sh[kScanBlock - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kScanBlock) scan_tiles(const T *in, T *out, T *tile_sums, int64_t n) {
+    __shared__ T sh[kScanBlock];
+    __shared__ T tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T loc[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = base + k < n ? in[base + k] : T(0);
+        s += loc[k];
+    }
+    T pre = block_exclusive_scan<T>(s, sh, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = pre;
+        pre += loc[k];
+    }
+    if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void add_tile_offsets(T *out, const T *tile_off, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_off[i / kScanTile];
+}
+
+template <class T>
+__global__ void write_total(const T *in, const T *out, int64_t n, T *total) {
+    *total = n > 0 ? out[n - 1] + in[n - 1] : T(0);
+}
+}  // namespace
+
+template <class T>
+void exclusive_scan(const T *d_in, T *d_out, int64_t n, T *d_total, cudaStream_t s) {
+    if (n <= 0) {
+        if (d_total) IMQ_CUDA(cudaMemsetAsync(d_total, 0, sizeof(T), s));
+        return;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles == 1) {
+        scan_tiles<T><<<1, kScanBlock, 0, s>>>(d_in, d_out, nullptr, n);
+        IMQ_LAUNCH_CHECK();
+    } else {
+        AsyncMem sums(sizeof(T) * ntiles, s), offs(sizeof(T) * ntiles, s);
+        scan_tiles<T><<<(unsigned)ntiles, kScanBlock, 0, s>>>(d_in, d_out, sums.as<T>(), n);
+        IMQ_LAUNCH_CHECK();
+        exclusive_scan<T>(sums.as<T>(), offs.as<T>(), ntiles, nullptr, s);
+        add_tile_offsets<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_out, offs.as<T>(), n);
+        IMQ_LAUNCH_CHECK();
+    }
+    if (d_total) {
+        write_total<T><<<1, 1, 0, s>>>(d_in, d_out, n, d_total);
+        IMQ_LAUNCH_CHECK();
+    }
+}
+
+template void exclusive_scan<int32_t>(const int32_t *, int32_t *, int64_t, int32_t *, cudaStream_t);
+template void exclusive_scan<int64_t>(const int64_t *, int64_t *, int64_t, int64_t *, cudaStream_t);
+template void exclusive_scan<uint32_t>(const uint32_t *, uint32_t *, int64_t, uint32_t *, cudaStream_t);
+
+}  // namespace imq

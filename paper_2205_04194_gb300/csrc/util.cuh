@@ -1,0 +1,19 @@
+// Small device/host helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace imq {
+
+// Exclusive prefix sum of n values on `s`; if d_total is non-null the grand
+// total is written there (device memory).
+template <class T>
+void exclusive_scan(const T *d_in, T *d_out, int64_t n, T *d_total, cudaStream_t s);
+
+// Per-device error word that kernels OR their DeviceError codes into.
+int *device_error_word();
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace imq

@@ -1,0 +1,148 @@
+"""Python surface of the IMQ library: the same entry points as include/imq.h.
+
+Tensors are passed by pointer to the C ABI; CUDA tensors are used in place on
+the current torch stream, host tensors / numpy arrays are copied by the
+library inside the call.  Nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import ImqError, ImqOptions, PlanInfo, call
+
+F32 = 0
+F64 = 1
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _buf(a, dtype):
+    """(pointer, keep-alive object) of a contiguous array of the given torch dtype."""
+    if isinstance(a, torch.Tensor):
+        if a.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    npdt = {torch.float64: np.float64, torch.float32: np.float32}[dtype]
+    arr = np.ascontiguousarray(a, dtype=npdt)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _dtype_code(t) -> int:
+    dt = t.dtype if isinstance(t, torch.Tensor) else np.asarray(t).dtype
+    if dt in (torch.float32, np.float32):
+        return F32
+    if dt in (torch.float64, np.float64):
+        return F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def _like(v, n_total: int, code: int):
+    if isinstance(v, torch.Tensor):
+        return torch.empty_like(v)
+    return np.empty(np.shape(v), dtype=np.float32 if code == F32 else np.float64)
+
+
+class Plan:
+    """imq_plan: quadtree, interaction lists and operators for (points, c, p, leaf)."""
+
+    def __init__(self, points, c: float, p: int, leaf: int, domain=None,
+                 check_duplicates: bool = False, stream=None):
+        self._h = ctypes.c_void_p(0)
+        pts_ptr, keep = _buf(points, torch.float64)
+        n = int(np.shape(points)[0])
+        opt = ImqOptions()
+        opt.struct_size = ctypes.sizeof(ImqOptions)
+        if domain is not None:
+            opt.has_domain = 1
+            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+        opt.check_duplicates = 1 if check_duplicates else 0
+        call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
+             ctypes.byref(self._h))
+        del keep
+        self.n = n
+        self.c = float(c)
+        self.p = int(p)
+        self.leaf = int(leaf)
+
+    def close(self):
+        if self._h and self._h.value:
+            _lib.load().imq_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def matvec(self, v, out=None, stream=None):
+        """imq_matvec: b = A v (fast method); v is [N] or [nrhs][N], float32 or float64."""
+        code = _dtype_code(v)
+        tdt = torch.float32 if code == F32 else torch.float64
+        nrhs = 1 if len(np.shape(v)) == 1 else int(np.shape(v)[0])
+        if out is None:
+            out = _like(v, self.n * nrhs, code)
+        vp, kv = _buf(v, tdt)
+        op, ko = _buf(out, tdt)
+        call("imq_matvec", self._h, vp, op, nrhs, code, _stream(stream))
+        return out
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        call("imq_plan_get_info", self._h, ctypes.byref(inf))
+        return {name: getattr(inf, name) for name, _ in PlanInfo._fields_}
+
+    def export_tree(self) -> dict:
+        inf = self.info()
+        n, nb = inf["n_points"], inf["n_boxes"]
+        out = dict(codes=np.empty(n, np.uint32), perm=np.empty(n, np.int64), level=np.empty(nb, np.int32),
+                   prefix=np.empty(nb, np.uint32), begin=np.empty(nb, np.int64), end=np.empty(nb, np.int64),
+                   parent=np.empty(nb, np.int32), child=np.empty((nb, 4), np.int32))
+        ptr = {k: ctypes.c_void_p(v.ctypes.data) for k, v in out.items()}
+        call("imq_plan_export_tree", self._h, ptr["codes"], ptr["perm"], ptr["level"], ptr["prefix"],
+             ptr["begin"], ptr["end"], ptr["parent"], ptr["child"])
+        return out
+
+    def export_list(self, which: str):
+        inf = self.info()
+        nb = inf["n_boxes"]
+        off = np.empty(nb + 1, np.int32)
+        call("imq_plan_export_list", self._h, which.encode(), ctypes.c_void_p(off.ctypes.data), None)
+        items = np.empty(max(1, int(off[-1])), np.int32)
+        call("imq_plan_export_list", self._h, which.encode(), ctypes.c_void_p(off.ctypes.data),
+             ctypes.c_void_p(items.ctypes.data))
+        return off, items[:int(off[-1])]
+
+
+def dense_matvec(points, c: float, v, out=None, stream=None):
+    """imq_dense_matvec: b = A v over all N^2 pairs (the plain product)."""
+    code = _dtype_code(v)
+    tdt = torch.float32 if code == F32 else torch.float64
+    n = int(np.shape(points)[0])
+    nrhs = 1 if len(np.shape(v)) == 1 else int(np.shape(v)[0])
+    if out is None:
+        out = _like(v, n * nrhs, code)
+    pp, kp = _buf(points, torch.float64)
+    vp, kv = _buf(v, tdt)
+    op, ko = _buf(out, tdt)
+    call("imq_dense_matvec", pp, n, float(c), vp, op, nrhs, code, _stream(stream))
+    return out
+
+
+def version() -> str:
+    return _lib.load().imq_version().decode()
+
+
+__all__ = ["Plan", "dense_matvec", "version", "ImqError", "F32", "F64"]

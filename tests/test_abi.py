@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point include/imq.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(imq_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_04194_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("imq_plan", "imq_matvec", "imq_dense_matvec", "imq_plan_destroy", "imq_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_2205_04194_gb300 import _lib
+    assert set(_declared()) <= set(_lib.SIGNATURES)
+
+
+def test_status_strings_without_gpu(lib):
+    from paper_2205_04194_gb300 import _lib
+    L = _lib.load()
+    assert L.imq_status_string(0) == b"IMQ_OK"
+    assert L.imq_status_string(5) == b"IMQ_NOT_CONVERGED"
+    assert L.imq_version().startswith(b"imq-gb300")
+
+
+def test_invalid_arguments_rejected_before_any_gpu_work(lib):
+    from paper_2205_04194_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p(0)
+    pts = (ctypes.c_double * 4)(0.0, 0.0, 1.0, 1.0)
+    assert L.imq_plan(pts, 2, -1.0, 8, 16, None, None, ctypes.byref(h)) == 1      # c <= 0
+    assert L.imq_plan(pts, 0, 1.0, 8, 16, None, None, ctypes.byref(h)) == 1       # N < 1
+    assert L.imq_plan(pts, 2, 1.0, 99, 16, None, None, ctypes.byref(h)) == 7      # p too large
+    assert L.imq_plan(None, 2, 1.0, 8, 16, None, None, ctypes.byref(h)) == 1
+    assert L.imq_plan(pts, 2, float("nan"), 8, 16, None, None, ctypes.byref(h)) == 1
+    assert b"c must be" in L.imq_last_error()
+    assert L.imq_matvec(None, None, None, 1, 0, None) == 1
+
+
+def test_oracle_builds_and_is_not_linked_by_the_product(lib):
+    from oracle import dense
+    assert os.path.exists(dense.build())
+    # the product library references no oracle symbol
+    for name in ("oracle_dense_matvec", "oracle_evaluate"):
+        assert not hasattr(lib, name)

@@ -1,0 +1,101 @@
+"""GPU products vs the FP64 oracle.
+
+Tolerances (relative 2-norm):
+* FP32 paths vs FP64 dense (O1): 1e-6 at the chosen p -- the accuracy target of
+  the method; each term is one FP32 rsqrt (<= 2 ulp) and the sums are FP32
+  within one leaf / tile, so rounding stays near 1e-7 and the rest of the
+  budget is expansion truncation.
+* FP32 fast path vs the FP64 FMM reference on the same tree and p (O3b): 1e-6.
+* FP64 fast path vs O3b: 1e-11 (same truncation, only rounding differs).
+* FP64 dense vs O1: 1e-13.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, need_gpu, rel2
+from oracle import dense, fmm
+from paper_2205_04194_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _imq():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    return imq
+
+
+@pytest.mark.parametrize("n", [1, 1025, 3000])
+def test_dense_f32_f64(n):
+    import torch
+    imq = _imq()
+    pts = W.uniform_points(n, 7)
+    v = W.random_vector(n, 7, nrhs=2)
+    c = 0.05
+    ref = dense.matvec(pts, c, v)
+    b32 = host(imq.dense_matvec(cuda(pts), c, cuda(v, torch.float32)))
+    b64 = host(imq.dense_matvec(cuda(pts), c, cuda(v)))
+    for r in range(2):
+        assert rel2(b32[r], ref[r]) < 1e-6
+        assert rel2(b64[r], ref[r]) < 1e-13
+    # host buffers go through the same call
+    bh = imq.dense_matvec(pts, c, v.astype(np.float32))
+    assert isinstance(bh, np.ndarray) and rel2(bh[0], ref[0]) < 1e-6
+
+
+def _fast_case(pts, c, p, leaf, domain=None, nrhs=1, tol_dense=1e-6):
+    import torch
+    imq = _imq()
+    n = pts.shape[0]
+    v = W.random_vector(n, 11, nrhs=nrhs)
+    ref = dense.matvec(pts, c, v)
+    plan = imq.Plan(cuda(pts), c, p, leaf, domain=domain)
+    b32 = host(plan.matvec(cuda(v, torch.float32)))
+    b64 = host(plan.matvec(cuda(v)))
+    vv = v if nrhs > 1 else v[None]
+    b32 = b32 if nrhs > 1 else b32[None]
+    b64 = b64 if nrhs > 1 else b64[None]
+    rr = ref if nrhs > 1 else ref[None]
+    for r in range(nrhs):
+        ofmm = fmm.fmm_matvec(pts, c, vv[r], p, leaf, domain)
+        assert rel2(b64[r], ofmm) < 1e-11, "FP64 fast path vs FP64 FMM reference"
+        assert rel2(b32[r], ofmm) < 1e-6, "FP32 fast path vs FP64 FMM reference"
+        assert rel2(b32[r], rr[r]) < tol_dense, "FP32 fast path vs FP64 dense"
+    plan.close()
+
+
+def test_fast_plain_2k():
+    wl = W.plain_2k()
+    _fast_case(wl.points, wl.c, wl.p, wl.leaf, wl.domain)
+
+
+def test_fast_clustered_small_c():
+    pts = W.clustered_points(1500, 8, 6000, 0.03, 3)
+    _fast_case(pts, 0.01, 12, 64, nrhs=2)
+
+
+def test_fast_uniform_ragged_leaf():
+    pts = W.uniform_points(4321, 8)
+    _fast_case(pts, 0.02, 12, 17, (0.0, 0.0, 1.0))
+
+
+def test_fast_degenerate_single_leaf_and_single_point():
+    imq = _imq()
+    pts = W.uniform_points(90, 9)
+    v = W.random_vector(90, 9)
+    ref = dense.matvec(pts, 0.2, v)
+    plan = imq.Plan(cuda(pts), 0.2, 4, 1000)     # one leaf: pure P2P
+    assert rel2(host(plan.matvec(cuda(v))), ref) < 1e-13
+    one = imq.Plan(cuda(np.array([[0.4, 0.1]])), 0.5, 4, 8)
+    assert host(one.matvec(cuda(np.array([3.0]))))[0] == pytest.approx(6.0, rel=1e-14)
+
+
+def test_fast_full_size_clustered_1m_sampled_rows():
+    import torch
+    imq = _imq()
+    wl = W.clustered_1m(p=12)
+    plan = imq.Plan(cuda(wl.points), wl.c, wl.p, wl.leaf, domain=wl.domain)
+    b = host(plan.matvec(cuda(wl.v, torch.float32)))
+    rows = np.random.default_rng(0).choice(wl.n, 2048, replace=False)
+    ref = dense.matvec_rows(wl.points, wl.c, wl.v, rows)
+    assert rel2(b[rows], ref) < 1e-6
