@@ -1,0 +1,332 @@
+"""Benchmark of the fast IMQ product A v (arXiv 2205.04194) on one GB300 per rank.
+
+Default workload: the N = 1,000,000 clustered point set (8 Gaussians of
+87,500 points, sigma 0.03, clamped to [0,1]^2, plus 300,000 uniform points),
+shape c = 0.01, adaptive quadtree with leaf 64, expansion order p = 12.
+
+A step is one fast product b = A v through the C ABI (gather, P2M, M2M, M2L,
+P2L, L2L, L2P+M2P, P2P, scatter) on device-resident FP32 input.  The tree
+and operators (imq_plan) are built once before the timed region and timed
+separately.  Between timed steps a 512 MiB buffer is written to flush the
+129 MB L2 (untimed); each step is bracketed by CUDA events on the launching
+stream, and the per-phase kernel times come from the library's own events on
+that stream.
+
+One JSON line on rank 0.  With torchrun (N > 1) every rank runs an
+independent replica of the same problem ("replicas only": the single-problem
+product is not sharded); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IMQ A·v time & CG solve s at 1e-6 rel err, fast vs dense GPU matvec, N=1M"
+MUFU_PER_CLK_SM = 16        # rsqrt (MUFU) results per clock per SM
+FP32_FMA_PER_CLK_SM = 128   # FP32 lanes per SM
+N_SM = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rows(points, c, v, seconds: float, min_rows: int = 8):
+    """Time the FP64 dense oracle (O1) on a sample of rows sized to ~`seconds`."""
+    from oracle import dense
+    n = points.shape[0]
+    rng = np.random.default_rng(123)
+    rows = rng.choice(n, min_rows, replace=False)
+    t0 = time.perf_counter()
+    dense.matvec_rows(points, c, v, rows)
+    t1 = time.perf_counter() - t0
+    nrows = int(max(min_rows, min(n, min_rows * seconds / max(t1, 1e-3))))
+    rows = rng.choice(n, nrows, replace=False)
+    t0 = time.perf_counter()
+    vals = dense.matvec_rows(points, c, v, rows)
+    dt = time.perf_counter() - t0
+    return dt, nrows, rows, vals, dense.num_threads()
+
+
+def run_reference(args, wl):
+    """The oracle as it stands, on the host cores: FP64 dense rows, scaled to one A v."""
+    from oracle import dense
+    n = wl.n
+    rows_per_step = args.ref_rows
+    rng = np.random.default_rng(7)
+    times = []
+    for k in range(args.warmup + args.steps):
+        rows = rng.choice(n, rows_per_step, replace=False)
+        t0 = time.perf_counter()
+        dense.matvec_rows(wl.points, wl.c, wl.v, rows)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt / rows_per_step * n)
+    ms = 1e3 * statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": n, "c": wl.c, "p": args.p, "leaf": wl.leaf},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": dense.num_threads(), "kind": "oracle",
+                             "sample": f"{rows_per_step} rows of the FP64 dense product per step, "
+                                       f"scaled by N/rows to one full A v"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=12)
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the clustered workload (tests)")
+    ap.add_argument("--dense-reps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-rows", type=int, default=96)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2205_04194_gb300 import workloads as W
+    wl = W.clustered_1m(p=args.p, scale=args.scale)
+
+    if args.impl == "reference":
+        if rank == 0:
+            from oracle import dense
+            dense.build()
+            run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2205_04194_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2205_04194_gb300 import imq
+
+    stream = torch.cuda.current_stream()
+    d_pts = torch.from_numpy(wl.points).to(dev)
+    d_v = torch.from_numpy(wl.v).float().to(dev)
+    d_out = torch.empty_like(d_v)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = imq.Plan(d_pts, wl.c, wl.p, wl.leaf, domain=wl.domain)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    info = plan.info()
+
+    for _ in range(args.warmup):
+        plan.matvec(d_v, d_out)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase_tot = {k: 0.0 for k in imq.Plan.PHASES}
+    launches = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # untimed L2 flush
+            ev[k][0].record(stream)
+            _, ph, nl = plan.matvec_timed(d_v, d_out)
+            ev[k][1].record(stream)
+            for key, val in ph.items():
+                phase_tot[key] += val
+            launches += nl
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phase_ms = {k: v / args.steps for k, v in phase_tot.items()}
+
+    # dense GPU product (the plain form) on the same input
+    dense_ms = None
+    d_dense = torch.empty_like(d_v)
+    if rank == 0 or world > 1:
+        imq.dense_matvec(d_pts, wl.c, d_v, d_dense)
+        torch.cuda.synchronize()
+        dts = []
+        for _ in range(args.dense_reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            a.record(stream)
+            imq.dense_matvec(d_pts, wl.c, d_v, d_dense)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dts.append(a.elapsed_time(b))
+        dense_ms = statistics.mean(dts)
+
+    # end to end through the public API with pinned host buffers
+    h_v = torch.from_numpy(wl.v).float().pin_memory()
+    h_out = torch.empty_like(h_v).pin_memory()
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.matvec(h_v, h_out)                  # H2D of v, product, D2H of b inside the call
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            e2e.append(1e3 * dt)
+    e2e_ms = statistics.mean(e2e)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # accuracy on sampled rows against the FP64 oracle, and the CPU baseline
+    b_fast = d_out.double().cpu().numpy()
+    b_dense = d_dense.double().cpu().numpy()
+    cpu = None
+    err = {}
+    if not args.no_cpu:
+        from oracle import dense as O
+        O.build()
+        dt, nrows, rows, ref, cores = cpu_oracle_rows(wl.points, wl.c, wl.v, args.cpu_seconds)
+        cpu = {"value": 1e3 * dt / nrows * wl.n, "unit": "ms", "cores": cores, "kind": "oracle",
+               "sample": f"{nrows} random rows of the FP64 dense product (oracle O1) on the "
+                         f"{wl.n}-point workload, scaled by N/rows to one full A v"}
+        rel = lambda a: float(np.linalg.norm(a[rows] - ref) / np.linalg.norm(ref))
+        err = {"fast_rel2_sampled": rel(b_fast), "dense_gpu_rel2_sampled": rel(b_dense),
+               "rows": int(nrows)}
+
+    peaks, src = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    clocks = clk.summary()
+    p2p_gps = info["p2p_pairs"] / (phase_ms["p2p"] * 1e-3) / 1e9
+    p2p_peak = N_SM * MUFU_PER_CLK_SM * mhz * 1e6 / 1e9
+    K = info["k_real"]
+    m2l_tf = info["m2l_pairs"] * 2.0 * K * K / (phase_ms["m2l"] * 1e-3) / 1e12
+    m2l_peak = N_SM * FP32_FMA_PER_CLK_SM * 2 * mhz * 1e6 / 1e12
+    dominant = "p2p" if phase_ms["p2p"] >= phase_ms["m2l"] else "m2l"
+    if dominant == "p2p":
+        roof = {"kernel": "k_p2p<float>", "bound": "alu", "achieved": p2p_gps, "peak": p2p_peak,
+                "unit": "Gpair/s", "frac": p2p_gps / p2p_peak, "traffic": None,
+                "peak_source": f"derived: {N_SM} SMs x {MUFU_PER_CLK_SM} MUFU rsqrt/clk x {mhz:.0f} MHz "
+                               f"({src} sm_max_mhz)"}
+    else:
+        roof = {"kernel": "k_m2l<float>", "bound": "alu", "achieved": m2l_tf, "peak": m2l_peak,
+                "unit": "TFLOP/s", "frac": m2l_tf / m2l_peak, "traffic": None,
+                "peak_source": f"derived: {N_SM} SMs x {FP32_FMA_PER_CLK_SM} FP32 FMA/clk x 2 x {mhz:.0f} MHz"}
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n, "c": wl.c, "p": wl.p, "leaf": wl.leaf,
+                   "l2": "flushed between steps (512 MiB write, untimed)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * wl.n, "d2h_bytes_per_step": 4 * wl.n},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "dense_gpu_ms": dense_ms,
+        "speedup_vs_dense_gpu": (dense_ms / ms) if dense_ms else None,
+        "plan_ms": plan_ms,
+        "phase_ms": phase_ms,
+        "p2p_gpair_s": p2p_gps, "m2l_tflop_s": m2l_tf,
+        "errors": err,
+        "tree": {k: info[k] for k in ("n_boxes", "n_leaves", "max_level", "k_real", "n_u", "n_v", "n_w",
+                                      "n_x", "p2p_pairs", "m2l_pairs")},
+        "cg": None,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,19 @@ imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs,
                       imq_dtype dt, void *stream);
 
 /* ------------------------------------------------------------------------- *
+ * imq_matvec_timed -- imq_matvec with the kernels of each phase bracketed by
+ * CUDA events recorded on `stream` (for benchmarks).  Synchronises `stream`.
+ *
+ *   phase_ms[k] (k < n_phases, host) receives the summed event time of phase k:
+ *     0 gather  1 P2M  2 M2M  3 M2L  4 P2L  5 L2L  6 L2P+M2P  7 P2P  8 scatter.
+ *   launches (host, may be NULL) receives the number of kernels launched.
+ * ------------------------------------------------------------------------- */
+#define IMQ_NUM_PHASES 9
+imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
+                            imq_dtype dt, void *stream, float *phase_ms, int n_phases,
+                            int32_t *launches);
+
+/* ------------------------------------------------------------------------- *
  * imq_dense_matvec -- the plain ("standard row-column") product of Section 3:
  * b_i = sum_j v_j / sqrt(|x_i - x_j|^2 + c^2) over all N^2 pairs, matrix-free.
  *

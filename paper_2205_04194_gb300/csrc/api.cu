@@ -189,28 +189,43 @@ void imq_plan_destroy(imq_plan_t plan) {
     delete plan;
 }
 
+static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream,
+                        PhaseTimer *tm) {
+    if (!plan || !v || !out) fail(IMQ_INVALID_ARG, "imq_matvec: NULL pointer");
+    if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_matvec: nrhs must be >= 1");
+    if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_matvec: unknown dtype");
+    Plan &P = plan->P;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = dt == IMQ_F32 ? 4 : 8;
+    const size_t bytes = es * (size_t)nrhs * P.N;
+    DevIn dv(v, bytes, s);
+    DevOut dout(out, bytes, s);
+    AsyncMem us(bytes, s), bs(bytes, s);
+    if (tm) tm->start(kPhGather, s);
+    if (dt == IMQ_F32) gather_sorted<float, float>(P, static_cast<const float *>(dv.ptr), us.as<float>(), nrhs, s);
+    else gather_sorted<double, double>(P, static_cast<const double *>(dv.ptr), us.as<double>(), nrhs, s);
+    if (tm) { tm->stop(s); tm->launches += nrhs; }
+    if (dt == IMQ_F32) fmm_apply<float>(P, us.as<float>(), bs.as<float>(), nrhs, s, tm);
+    else fmm_apply<double>(P, us.as<double>(), bs.as<double>(), nrhs, s, tm);
+    if (tm) tm->start(kPhScatter, s);
+    if (dt == IMQ_F32) scatter_sorted<float, float>(P, bs.as<float>(), static_cast<float *>(dout.ptr), nrhs, s);
+    else scatter_sorted<double, double>(P, bs.as<double>(), static_cast<double *>(dout.ptr), nrhs, s);
+    if (tm) { tm->stop(s); tm->launches += nrhs; }
+    dout.finish();
+}
+
 imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] { matvec_impl(plan, v, out, nrhs, dt, stream, nullptr); });
+}
+
+imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream,
+                            float *phase_ms, int n_phases, int32_t *launches) {
     return guard([&] {
-        if (!plan || !v || !out) fail(IMQ_INVALID_ARG, "imq_matvec: NULL pointer");
-        if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_matvec: nrhs must be >= 1");
-        if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_matvec: unknown dtype");
-        Plan &P = plan->P;
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        const size_t es = dt == IMQ_F32 ? 4 : 8;
-        const size_t bytes = es * (size_t)nrhs * P.N;
-        DevIn dv(v, bytes, s);
-        DevOut dout(out, bytes, s);
-        AsyncMem us(bytes, s), bs(bytes, s);
-        if (dt == IMQ_F32) {
-            gather_sorted<float, float>(P, static_cast<const float *>(dv.ptr), us.as<float>(), nrhs, s);
-            fmm_apply<float>(P, us.as<float>(), bs.as<float>(), nrhs, s);
-            scatter_sorted<float, float>(P, bs.as<float>(), static_cast<float *>(dout.ptr), nrhs, s);
-        } else {
-            gather_sorted<double, double>(P, static_cast<const double *>(dv.ptr), us.as<double>(), nrhs, s);
-            fmm_apply<double>(P, us.as<double>(), bs.as<double>(), nrhs, s);
-            scatter_sorted<double, double>(P, bs.as<double>(), static_cast<double *>(dout.ptr), nrhs, s);
-        }
-        dout.finish();
+        if (!phase_ms || n_phases < 1) fail(IMQ_INVALID_ARG, "imq_matvec_timed: phase_ms required");
+        PhaseTimer tm;
+        matvec_impl(plan, v, out, nrhs, dt, stream, &tm);
+        tm.collect(phase_ms, n_phases);
+        if (launches) *launches = tm.launches;
     });
 }
 

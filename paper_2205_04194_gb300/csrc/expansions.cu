@@ -504,7 +504,7 @@ template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 
 template <class T>
-void fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s) {
+int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer *tm) {
     const bool f64 = std::is_same<T, double>::value;
     ensure_ops(P, f64, s);
     TypedOps &O = f64 ? P.ops64 : P.ops32;
@@ -514,54 +514,80 @@ void fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s) {
     const T *m2m = O.m2m.as<T>(), *l2l = O.l2l.as<T>(), *m2l = O.m2l.as<T>(), *coef = O.p2mc.as<T>();
     const int R = m2l_rows(K);
     const int Kp = 4 * R;
+    int launches = 0;
+    auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
+    auto t1 = [&]() { if (tm) tm->stop(s); };
     for (int r = 0; r < nrhs; ++r) {
         const T *u = us + (size_t)r * P.N;
         T *b = bs + (size_t)r * P.N;
         IMQ_CUDA(cudaMemsetAsync(M, 0, sizeof(T) * (size_t)nb * K, s));
         IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)nb * K, s));
         // upward pass
+        t0(kPhP2M);
         k_p2m<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
             P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
             P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, p, coef, P.side);
         IMQ_LAUNCH_CHECK();
+        ++launches;
+        t1();
+        t0(kPhM2M);
         for (int lev = P.max_level - 1; lev >= 2; --lev) {
             const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
             if (nl <= 0) continue;
             k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
             IMQ_LAUNCH_CHECK();
+            ++launches;
         }
+        t1();
         // interaction: M2L per level, P2L over X lists
+        t0(kPhM2L);
         for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
             const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
             const T *ops = m2l + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * K * Kp;
             launch_m2l<T>(R, lb, nl, P.vtab.as<int32_t>(), M, L, ops, K, s);
+            ++launches;
         }
+        t1();
+        t0(kPhP2L);
         if (P.X.total > 0) {
             k_p2l<T><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
                 P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(),
                 P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
                 P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, p, P.side, (T)P.c);
             IMQ_LAUNCH_CHECK();
+            ++launches;
         }
+        t1();
         // downward pass
+        t0(kPhL2L);
         for (int lev = 3; lev <= P.max_level; ++lev) {
             const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
             if (nl <= 0) continue;
             k_l2l<T><<<nl, 128, sizeof(T) * K, s>>>(lb, P.parent.as<int32_t>(), P.prefix.as<uint32_t>(), L, l2l, K);
             IMQ_LAUNCH_CHECK();
+            ++launches;
         }
+        t1();
         // evaluation: L2P + M2P writes b, P2P adds the near field
+        t0(kPhFar);
         k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
             P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
             P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
             P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, (T)P.c, b);
         IMQ_LAUNCH_CHECK();
+        ++launches;
+        t1();
+        t0(kPhP2P);
         p2p_apply<T>(P, u, b, s);
+        ++launches;
+        t1();
     }
+    if (tm) tm->launches += launches;
+    return launches;
 }
 
-template void fmm_apply<float>(Plan &, const float *, float *, int, cudaStream_t);
-template void fmm_apply<double>(Plan &, const double *, double *, int, cudaStream_t);
+template int fmm_apply<float>(Plan &, const float *, float *, int, cudaStream_t, PhaseTimer *);
+template int fmm_apply<double>(Plan &, const double *, double *, int, cudaStream_t, PhaseTimer *);
 
 template <class Tin, class T>
 void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s) {

@@ -135,12 +135,24 @@ struct Plan {
     int64_t device_bytes() const;
 };
 
+// Optional per-phase timing of a product with CUDA events on the launching stream.
+enum Phase { kPhGather = 0, kPhP2M, kPhM2M, kPhM2L, kPhP2L, kPhL2L, kPhFar, kPhP2P, kPhScatter, kNumPhases };
+struct PhaseTimer {
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    int launches = 0;
+    void start(int phase, cudaStream_t s);
+    void stop(cudaStream_t s);
+    void collect(float *ms, int n);   // synchronises on the last event
+    ~PhaseTimer();
+};
+
 // tree.cu
 void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups);
 // expansions.cu
 void ensure_ops(Plan &P, bool fp64, cudaStream_t s);
 template <class T>
-void fmm_apply(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
+int fmm_apply(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s, PhaseTimer *tm = nullptr);
 template <class Tin, class T>
 void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s);
 template <class T, class Tout>

@@ -55,6 +55,35 @@ AsyncMem::~AsyncMem() {
     if (ptr) cudaFreeAsync(ptr, stream);
 }
 
+// ------------------------------------------------------------------ phase timer
+void PhaseTimer::start(int phase, cudaStream_t s) {
+    Rec r{phase, nullptr, nullptr};
+    IMQ_CUDA(cudaEventCreate(&r.a));
+    IMQ_CUDA(cudaEventCreate(&r.b));
+    IMQ_CUDA(cudaEventRecord(r.a, s));
+    recs.push_back(r);
+}
+
+void PhaseTimer::stop(cudaStream_t s) { IMQ_CUDA(cudaEventRecord(recs.back().b, s)); }
+
+void PhaseTimer::collect(float *ms, int n) {
+    for (int k = 0; k < n; ++k) ms[k] = 0.f;
+    if (recs.empty()) return;
+    IMQ_CUDA(cudaEventSynchronize(recs.back().b));
+    for (auto &r : recs) {
+        float t = 0.f;
+        IMQ_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        if (r.phase >= 0 && r.phase < n) ms[r.phase] += t;
+    }
+}
+
+PhaseTimer::~PhaseTimer() {
+    for (auto &r : recs) {
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
+    }
+}
+
 // ------------------------------------------------------------------ device error word
 static std::mutex g_err_mu;
 static int *g_err_word[64] = {nullptr};

@@ -99,6 +99,23 @@ class Plan:
         call("imq_matvec", self._h, vp, op, nrhs, code, _stream(stream))
         return out
 
+    PHASES = ("gather", "p2m", "m2m", "m2l", "p2l", "l2l", "l2p_m2p", "p2p", "scatter")
+
+    def matvec_timed(self, v, out=None, stream=None):
+        """imq_matvec_timed: (out, {phase: ms}, kernel launches); synchronises the stream."""
+        code = _dtype_code(v)
+        tdt = torch.float32 if code == F32 else torch.float64
+        nrhs = 1 if len(np.shape(v)) == 1 else int(np.shape(v)[0])
+        if out is None:
+            out = _like(v, self.n * nrhs, code)
+        vp, kv = _buf(v, tdt)
+        op, ko = _buf(out, tdt)
+        ms = (ctypes.c_float * len(self.PHASES))()
+        nl = ctypes.c_int32(0)
+        call("imq_matvec_timed", self._h, vp, op, nrhs, code, _stream(stream), ms, len(self.PHASES),
+             ctypes.byref(nl))
+        return out, dict(zip(self.PHASES, list(ms))), int(nl.value)
+
     def info(self) -> dict:
         inf = PlanInfo()
         call("imq_plan_get_info", self._h, ctypes.byref(inf))
