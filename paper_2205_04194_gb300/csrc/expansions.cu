@@ -173,60 +173,8 @@ __global__ void k_l2l(int lb, const int32_t *__restrict__ parent, const uint32_t
     }
 }
 
-// ------------------------------------------------------------------ M2L (SIMT, batched by offset class)
-// For a tile of TB target boxes of one level and each of the 40 offset
-// classes, the class operator (K x K, input-major, rows padded to Kp = 4R)
-// and the gathered source multipoles are staged in shared memory; thread
-// (ty, tx) accumulates rows [ty*R, ty*R+R) of target tx.
-template <class T, int R, int TB>
-__global__ void __launch_bounds__(256) k_m2l(int lb, int nl, const int32_t *__restrict__ vtab,
-                                             const T *__restrict__ M, T *__restrict__ L, const T *__restrict__ ops,
-                                             int K) {
-    constexpr int Kp = 4 * R;
-    constexpr int MS = TB + 1;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *Top = reinterpret_cast<T *>(smraw);                 // [K][Kp]
-    T *Ms = Top + (size_t)K * Kp;                          // [K][TB+1]
-    const int tx = threadIdx.x % TB, ty = threadIdx.x / TB;
-    const int b0 = lb + blockIdx.x * TB;
-    const int nbt = min(TB, lb + nl - b0);
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0;
-    for (int o = 0; o < kOffsetClasses; ++o) {
-        const int src = tx < nbt ? vtab[(int64_t)kOffsetClasses * (b0 + tx) + o] : -1;
-        if (!__syncthreads_or(src >= 0)) continue;
-        const T *g = ops + (size_t)o * K * Kp;
-        for (int e = threadIdx.x; e < K * Kp; e += blockDim.x) Top[e] = g[e];
-        for (int e = threadIdx.x; e < K * TB; e += blockDim.x) {
-            const int cbox = e / K, i = e - cbox * K;
-            const int s = cbox < nbt ? vtab[(int64_t)kOffsetClasses * (b0 + cbox) + o] : -1;
-            Ms[i * MS + cbox] = s >= 0 ? M[(int64_t)s * K + i] : (T)0;
-        }
-        __syncthreads();
-        if (ty * R < K) {
-            const T *trow = Top + ty * R;
-            for (int i = 0; i < K; ++i) {
-                const T mv = Ms[i * MS + tx];
-                const T *t = trow + (size_t)i * Kp;
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += t[r] * mv;
-            }
-        }
-        __syncthreads();
-    }
-    if (tx < nbt) {
-        T *Lb = L + (int64_t)(b0 + tx) * K;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int row = ty * R + r;
-            if (row < K) Lb[row] = acc[r];
-        }
-    }
-}
-
-// Fallback M2L without shared-memory staging (FP64 at large p): one thread per
-// (target box, output row), operators read through the cache hierarchy.
+// M2L for the FP64 path: one thread per (target box, output row), operators
+// read through the cache hierarchy.
 template <class T>
 __global__ void k_m2l_direct(int lb, int nl, const int32_t *__restrict__ vtab, const T *__restrict__ M,
                              T *__restrict__ L, const T *__restrict__ ops, int K, int Kp) {
@@ -246,32 +194,43 @@ __global__ void k_m2l_direct(int lb, int nl, const int32_t *__restrict__ vtab, c
 
 // ------------------------------------------------------------------ irregular-harmonic evaluation
 // G_n^m(v) = Ptilde_n^m(cos th) e^{i m om} (h/rho)^n / rho for n+m even is produced
-// column by column; F(n, slot, gr, gi) consumes each term.
+// column by column from G_m^m with the normalised three-term recurrence; F(slot, gr, gi)
+// consumes each term.  tab2/tabi are the recurrence tables of fill_recurrence_tables.
 template <class T, class F>
-__device__ __forceinline__ void irregular_column(int m, int p, T a, T t, T zr, T zi, T gmm_r, T gmm_i, F &&f,
-                                                 int slot) {
-    // G_m^m given; step n upward with the normalised three-term recurrence.
+__device__ __forceinline__ void irregular_column(int m, int p, T a, T t, T gmm_r, T gmm_i, const T *tab2,
+                                                 const T *tabi, F &&f, int slot) {
     T g2r = 0, g2i = 0, g1r = gmm_r, g1i = gmm_i;
-    f(m, slot, g1r, g1i);
+    f(slot, g1r, g1i);
     slot += m ? 2 : 1;
+    const T ta = t * a, a2 = a * a;
     for (int n = m + 1; n <= p; ++n) {
-        const T c1 = (T)(2 * n - 1) * t * a;
-        const T c2 = sqrt((T)((n - 1) * (n - 1) - m * m)) * a * a;
-        const T inv = rsq<T>((T)(n * n - m * m));
-        const T gr = (c1 * g1r - c2 * g2r) * inv;
-        const T gi = (c1 * g1i - c2 * g2i) * inv;
+        const T c1 = (T)(2 * n - 1) * ta;
+        const T c2 = tab2[n * (p + 1) + m] * a2;
+        const T iv = tabi[n * (p + 1) + m];
+        const T gr = (c1 * g1r - c2 * g2r) * iv;
+        const T gi = (c1 * g1i - c2 * g2i) * iv;
         g2r = g1r; g2i = g1i; g1r = gr; g1i = gi;
         if (((n + m) & 1) == 0) {
-            f(n, slot, gr, gi);
+            f(slot, gr, gi);
             slot += m ? 2 : 1;
         }
     }
-    (void)zr;
-    (void)zi;
+}
+
+// ------------------------------------------------------------------ recurrence tables
+// tab2[n*(p+1)+m] = sqrt((n-1)^2 - m^2), tabi[n*(p+1)+m] = 1/sqrt(n^2 - m^2) (0 where undefined)
+template <class T>
+__device__ __forceinline__ void fill_recurrence_tables(T *tab2, T *tabi, int p) {
+    for (int idx = threadIdx.x; idx < (p + 1) * (p + 1); idx += blockDim.x) {
+        const int n = idx / (p + 1), m = idx - n * (p + 1);
+        const int a = (n - 1) * (n - 1) - m * m, b = n * n - m * m;
+        tab2[idx] = (n >= 1 && a > 0) ? sqrt((T)a) : (T)0;
+        tabi[idx] = b > 0 ? (T)1 / sqrt((T)b) : (T)0;
+    }
 }
 
 // ------------------------------------------------------------------ P2L (X list)
-// Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c.
+// Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c; lane l owns column l.
 template <class T>
 __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff,
                       const int32_t *__restrict__ xitems, const int32_t *__restrict__ begin,
@@ -279,6 +238,9 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
                       const double2 *__restrict__ centre, const float2 *__restrict__ loc,
                       const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p,
                       double S, T c) {
+    __shared__ T tab2[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)], tabi[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)];
+    fill_recurrence_tables<T>(tab2, tabi, p);
+    __syncthreads();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= nxb || lane > p) return;
@@ -297,8 +259,7 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
         for (int j = begin[s]; j < end[s]; ++j) {
             T vx, vy;
             point_offset<T>(j, loc, pos, cb, cs, vx, vy);
-            const T rho2 = vx * vx + vy * vy + c * c;
-            const T inv = rsq<T>(rho2);
+            const T inv = rsq<T>(vx * vx + vy * vy + c * c);
             const T a = h * inv, t = -c * inv;
             const T zr0 = vx * inv * a, zi0 = vy * inv * a;
             T gr = dmm * inv * u[j], gi = 0;
@@ -307,22 +268,37 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
                 gi = gr * zi0 + gi * zr0;
                 gr = nr;
             }
-            int k = 0;
-            irregular_column<T>(l, p, a, t, zr0, zi0, gr, gi,
-                                [&](int, int, T xr, T xi) {
-                                    ar[k] += xr;
-                                    ai[k] += xi;
-                                    ++k;
-                                },
-                                0);
+            ar[0] += gr;
+            ai[0] += gi;
+            T g2r = 0, g2i = 0, g1r = gr, g1i = gi;
+            const T a2 = a * a, ta = t * a;
+#pragma unroll
+            for (int st = 1; st <= IMQ_MAX_P; ++st) {
+                const int n = l + st;
+                if (n <= p) {
+                    const T c1 = (T)(2 * n - 1) * ta;
+                    const T c2 = tab2[n * (p + 1) + l] * a2;
+                    const T iv = tabi[n * (p + 1) + l];
+                    const T nr = (c1 * g1r - c2 * g2r) * iv;
+                    const T ni = (c1 * g1i - c2 * g2i) * iv;
+                    g2r = g1r; g2i = g1i; g1r = nr; g1i = ni;
+                    if ((st & 1) == 0) {
+                        ar[st / 2] += nr;
+                        ai[st / 2] += ni;
+                    }
+                }
+            }
         }
     }
     int slot = col_base(l, p);
     T *Lb = L + (int64_t)b * K;
-    for (int k = 0; k < kMaxCol && l + 2 * k <= p; ++k) {
-        Lb[slot] += ar[k];
-        if (l > 0) Lb[slot + 1] += ai[k];
-        slot += l ? 2 : 1;
+#pragma unroll
+    for (int k = 0; k < kMaxCol; ++k) {
+        if (l + 2 * k <= p) {
+            Lb[slot] += ar[k];
+            if (l > 0) Lb[slot + 1] += ai[k];
+            slot += l ? 2 : 1;
+        }
     }
 }
 
@@ -334,6 +310,9 @@ __global__ void k_far(int nleaf, const int32_t *__restrict__ leaves, const int32
                       const double2 *__restrict__ pos, const int32_t *__restrict__ woff,
                       const int32_t *__restrict__ witems, const T *__restrict__ M, const T *__restrict__ L,
                       const T *__restrict__ coef, int K, int p, double S, T c, T *__restrict__ bs) {
+    __shared__ T tab2[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)], tabi[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)];
+    fill_recurrence_tables<T>(tab2, tabi, p);
+    __syncthreads();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= nleaf) return;
@@ -389,8 +368,8 @@ __global__ void k_far(int nleaf, const int32_t *__restrict__ leaves, const int32
                     gr = nr;
                 }
                 const T eps = m ? (T)2 : (T)1;
-                irregular_column<T>(m, p, a, t, zr0, zi0, gr, gi,
-                                    [&](int, int sl, T xr, T xi) {
+                irregular_column<T>(m, p, a, t, gr, gi, tab2, tabi,
+                                    [&](int sl, T xr, T xi) {
                                         const T mr = Ms[sl];
                                         const T mi = m ? Ms[sl + 1] : (T)0;
                                         phi += eps * (mr * xr - mi * xi);
@@ -411,44 +390,6 @@ void upload(DevMem &dst, const std::vector<double> &src, cudaStream_t s) {
     IMQ_CUDA(cudaStreamSynchronize(s));
 }
 
-int m2l_rows(int K) {   // R bucket: rows per thread, 4 row groups
-    const int r = (K + 3) / 4;
-    const int buckets[] = {12, 20, 24, 32, 40, 48};
-    for (int b : buckets)
-        if (r <= b) return b;
-    return -1;
-}
-
-template <class T>
-void launch_m2l(int R, int lb, int nl, const int32_t *vtab, const T *M, T *L, const T *ops, int K, cudaStream_t s) {
-    constexpr int TB = 64;
-    const size_t smem = sizeof(T) * ((size_t)K * 4 * R + (size_t)K * (TB + 1));
-    const unsigned grid = (unsigned)((nl + TB - 1) / TB);
-    if (smem > 200 * 1024) {
-        k_m2l_direct<T><<<blocks_for((int64_t)nl * K, 128), 128, 0, s>>>(lb, nl, vtab, M, L, ops, K, 4 * R);
-        IMQ_LAUNCH_CHECK();
-        return;
-    }
-#define IMQ_M2L_CASE(RR)                                                                                  \
-    case RR: {                                                                                            \
-        auto kern = k_m2l<T, RR, TB>;                                                                     \
-        IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-        kern<<<grid, 256, smem, s>>>(lb, nl, vtab, M, L, ops, K);                                         \
-        break;                                                                                            \
-    }
-    switch (R) {
-        IMQ_M2L_CASE(12)
-        IMQ_M2L_CASE(20)
-        IMQ_M2L_CASE(24)
-        IMQ_M2L_CASE(32)
-        IMQ_M2L_CASE(40)
-        IMQ_M2L_CASE(48)
-        default: fail(IMQ_UNSUPPORTED, "M2L: expansion too large");
-    }
-#undef IMQ_M2L_CASE
-    IMQ_LAUNCH_CHECK();
-}
-
 }  // namespace
 
 int64_t Plan::device_bytes() const {
@@ -466,24 +407,17 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     TypedOps &O = fp64 ? P.ops64 : P.ops32;
     if (O.ready) return;
     const int K = P.layout.K;
+    const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
     if (P.h_m2m.empty()) {
         build_m2m_ops(P.layout, P.h_m2m);
         build_l2l_ops(P.layout, P.h_l2l);
         p2m_coefficients(P.layout, P.h_p2mc);
-        const int R = m2l_rows(K);
-        if (R < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
-        const int Kp = 4 * R;
-        const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
-        P.h_m2l.assign((size_t)std::max(1, nlev) * kOffsetClasses * K * Kp, 0.0);
+        P.h_m2l.assign((size_t)std::max(1, nlev) * kOffsetClasses * K * K, 0.0);
         std::vector<double> tmp;
         for (int li = 0; li < nlev; ++li) {
             const double h = P.side / (double)(1 << (P.m2l_level_lo + li));
             build_m2l_ops(P.layout, h, P.c, tmp);
-            for (int o = 0; o < kOffsetClasses; ++o)
-                for (int i = 0; i < K; ++i)
-                    for (int r = 0; r < K; ++r)
-                        P.h_m2l[(((size_t)li * kOffsetClasses + o) * K + i) * Kp + r] =
-                            tmp[((size_t)o * K + i) * K + r];
+            std::copy(tmp.begin(), tmp.end(), P.h_m2l.begin() + (size_t)li * kOffsetClasses * K * K);
         }
     }
     if (fp64) {
@@ -494,8 +428,15 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     } else {
         upload<float>(O.m2m, P.h_m2m, s);
         upload<float>(O.l2l, P.h_l2l, s);
-        upload<float>(O.m2l, P.h_m2l, s);
         upload<float>(O.p2mc, P.h_p2mc, s);
+        const int RR = m2l_tiled_rows(K);
+        if (RR < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
+        const int Kp = 16 * RR;
+        std::vector<double> pad((size_t)std::max(1, nlev) * kOffsetClasses * K * Kp, 0.0);
+        for (size_t blk = 0; blk < (size_t)std::max(1, nlev) * kOffsetClasses; ++blk)
+            for (int i = 0; i < K; ++i)
+                for (int r = 0; r < K; ++r) pad[(blk * K + i) * Kp + r] = P.h_m2l[(blk * K + i) * K + r];
+        upload<float>(O.m2l, pad, s);
     }
     O.ready = true;
 }
@@ -512,8 +453,6 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
     AsyncMem Mbuf(sizeof(T) * (size_t)nb * K, s), Lbuf(sizeof(T) * (size_t)nb * K, s);
     T *M = Mbuf.as<T>(), *L = Lbuf.as<T>();
     const T *m2m = O.m2m.as<T>(), *l2l = O.l2l.as<T>(), *m2l = O.m2l.as<T>(), *coef = O.p2mc.as<T>();
-    const int R = m2l_rows(K);
-    const int Kp = 4 * R;
     int launches = 0;
     auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
     auto t1 = [&]() { if (tm) tm->stop(s); };
@@ -541,11 +480,20 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t1();
         // interaction: M2L per level, P2L over X lists
         t0(kPhM2L);
-        for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
-            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-            const T *ops = m2l + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * K * Kp;
-            launch_m2l<T>(R, lb, nl, P.vtab.as<int32_t>(), M, L, ops, K, s);
-            ++launches;
+        if constexpr (std::is_same<T, float>::value) {
+            if (P.n_m2l_tiles > 0) {
+                m2l_tiled_launch(P, M, L, m2l, s);
+                ++launches;
+            }
+        } else {
+            for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
+                const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+                const T *ops = m2l + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * K * K;
+                k_m2l_direct<T><<<blocks_for((int64_t)nl * K, 128), 128, 0, s>>>(lb, nl, P.vtab.as<int32_t>(), M, L,
+                                                                                  ops, K, K);
+                IMQ_LAUNCH_CHECK();
+                ++launches;
+            }
         }
         t1();
         t0(kPhP2L);

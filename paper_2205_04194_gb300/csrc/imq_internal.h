@@ -118,6 +118,8 @@ struct Plan {
     ListCSR U, V, W, X;
     DevMem colleagues; // int32[9*nbox]
     DevMem vtab;       // int32[40*nbox] V source per offset class, -1 if none
+    DevMem m2l_tiles;  // int4[n_m2l_tiles]: (level - m2l_level_lo, first box, boxes) per M2L tile
+    int n_m2l_tiles = 0;
     DevMem xboxes;     // int32[nxbox] boxes whose X list is not empty
     int nxbox = 0;
     DevMem utot;       // int32[nbox] total U-list source points of a leaf
@@ -128,7 +130,7 @@ struct Plan {
     DevMem loc;        // float2[N]  offset from the leaf centre
     DevMem leaf_of;    // int32[N]
     // operators
-    std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies
+    std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
     TypedOps ops32, ops64;
     // statistics
     int64_t p2p_pairs = 0, m2l_pairs = 0;
@@ -157,6 +159,10 @@ template <class Tin, class T>
 void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s);
 template <class T, class Tout>
 void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_t s);
+// m2l.cu
+int m2l_tiled_rows(int K);
+void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s);
+void build_m2l_tiles(Plan &P, cudaStream_t s);
 // dense.cu
 void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,
                       int nrhs, imq_dtype dt, cudaStream_t s);

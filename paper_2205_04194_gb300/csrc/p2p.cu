@@ -8,11 +8,14 @@
 //
 // Mapping (source-parallel, one warp per target leaf): the sources of all U
 // entries form one virtual concatenated range; lane l takes positions
-// l, l+32, ... of it, so a warp's lanes stay busy whatever the leaf sizes.
-// Each lane keeps one partial sum per target of the current 32-target chunk in
-// registers (targets broadcast from a per-warp shared-memory slot), and a
+// l, l+32, ... of it, so the lanes stay busy whatever the leaf sizes.  The
+// targets of a leaf are processed in chunks of TC = 8, 16 or 32 (the smallest
+// that holds the chunk); every lane keeps the chunk's target coordinates and
+// one partial sum per target in registers, so the inner loop has no loads and
+// no guards (padding targets sit far away and their sums are discarded).  A
 // butterfly transpose-reduction over the 32 lanes leaves target t's total in
-// lane t.  Per pair: 2 FADD + 2 FFMA + 1 MUFU rsqrt + 1 FFMA.
+// lane t.  FP32 pairs of targets share one packed f32x2 instruction:
+// per two pairs 2 add.f32x2 + 2 fma.f32x2 + 2 MUFU rsqrt + 1 fma.f32x2.
 //
 // FP32 coordinates are offsets from the target leaf's centre: a source
 // x_j = loc_j + (c_s - c_t) becomes loc_j - delta with delta = c_t - c_s
@@ -28,18 +31,33 @@ namespace imq {
 namespace {
 
 constexpr int kP2PWarps = 4;
+constexpr float kFar = 1.0e18f;   // coordinate of padding targets
 
-template <class T>
-__device__ __forceinline__ T rsq_p2p(T v) {
-    if constexpr (std::is_same<T, float>::value) return rsqrtf(v);
-    else return 1.0 / sqrt(v);
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(u64 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
-// After the call, lane t holds sum over lanes of acc[t] (t < 32).
-template <class T>
-__device__ __forceinline__ T transpose_reduce32(T (&acc)[32], int lane) {
+// Sum over the 32 lanes of each acc[i], i < TC; lane L ends with the total of
+// target L % TC.
+template <class T, int TC>
+__device__ __forceinline__ T lane_reduce(T (&acc)[TC], int lane) {
 #pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
+    for (int k = TC / 2; k >= 1; k >>= 1) {
         const bool upper = (lane & k) != 0;
 #pragma unroll
         for (int i = 0; i < k; ++i) {
@@ -48,16 +66,105 @@ __device__ __forceinline__ T transpose_reduce32(T (&acc)[32], int lane) {
             acc[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, k);
         }
     }
-    return acc[0];
+    T v = acc[0];
+#pragma unroll
+    for (int k = TC; k < 32; k <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, k);
+    return v;
 }
 
-template <class T>
-__global__ void __launch_bounds__(32 * kP2PWarps) k_p2p(
+struct SrcCursor {
+    int r;
+};
+
+// Position q of the concatenated U-list source range -> sorted point index j, entry r.
+__device__ __forceinline__ int source_index(int q, int &r, int u1, const int32_t *__restrict__ ucum,
+                                            const int32_t *__restrict__ uitems, const int32_t *__restrict__ begin) {
+    while (r + 1 < u1 && ucum[r + 1] <= q) ++r;
+    return begin[uitems[r]] + (q - ucum[r]);
+}
+
+template <int TC>
+__device__ __forceinline__ float p2p_chunk_f32(int ti, int ntc, int lane, int u0, int u1, int St,
+                                               const int32_t *__restrict__ begin, const int32_t *__restrict__ uitems,
+                                               const int32_t *__restrict__ ucum, const float2 *__restrict__ udelta,
+                                               const float2 *__restrict__ loc, const float *__restrict__ u, float c2) {
+    u64 tx[TC / 2], ty[TC / 2], acc[TC / 2];
+#pragma unroll
+    for (int q = 0; q < TC / 2; ++q) {
+        const int i0 = 2 * q, i1 = 2 * q + 1;
+        const float2 a = i0 < ntc ? loc[ti + i0] : make_float2(kFar, kFar);
+        const float2 b = i1 < ntc ? loc[ti + i1] : make_float2(kFar, kFar);
+        tx[q] = pk2(a.x, b.x);
+        ty[q] = pk2(a.y, b.y);
+        acc[q] = 0ull;
+    }
+    const u64 cc = pk2(c2, c2);
+    int r = u0;
+    for (int q0 = 0; q0 < St; q0 += 32) {
+        const int q = q0 + lane;
+        float xs = 0.f, ys = 0.f, us = 0.f;
+        if (q < St) {
+            const int j = source_index(q, r, u1, ucum, uitems, begin);
+            const float2 l = loc[j];
+            const float2 d = udelta[r];
+            xs = l.x - d.x;
+            ys = l.y - d.y;
+            us = u[j];
+        }
+        const u64 nx = pk2(-xs, -xs), ny = pk2(-ys, -ys), uu = pk2(us, us);
+#pragma unroll
+        for (int k = 0; k < TC / 2; ++k) {
+            const u64 dx = add2(tx[k], nx);
+            const u64 dy = add2(ty[k], ny);
+            const u64 d2 = fma2(dx, dx, fma2(dy, dy, cc));
+            float a, b;
+            up2(d2, a, b);
+            acc[k] = fma2(pk2(rsqrtf(a), rsqrtf(b)), uu, acc[k]);
+        }
+    }
+    float s[TC];
+#pragma unroll
+    for (int k = 0; k < TC / 2; ++k) up2(acc[k], s[2 * k], s[2 * k + 1]);
+    return lane_reduce<float, TC>(s, lane);
+}
+
+__global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
     const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-    const double2 *__restrict__ pos, const T *__restrict__ u, T c2, T *__restrict__ bs) {
-    __shared__ T tgx[kP2PWarps][32], tgy[kP2PWarps][32];
+    const float *__restrict__ u, float c2, float *__restrict__ bs) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int widx = blockIdx.x * kP2PWarps + w;
+    if (widx >= nleaf) return;
+    const int b = leaves[widx];
+    const int tb = begin[b], nt = end[b] - tb;
+    const int u0 = uoffs[b], u1 = uoffs[b + 1];
+    const int St = utot[b];
+    for (int tc = 0; tc < nt; tc += 32) {
+        const int ntc = min(32, nt - tc);
+        float tot;
+        int tcap;
+        if (ntc <= 8) {
+            tot = p2p_chunk_f32<8>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tcap = 8;
+        } else if (ntc <= 16) {
+            tot = p2p_chunk_f32<16>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tcap = 16;
+        } else {
+            tot = p2p_chunk_f32<32>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tcap = 32;
+        }
+        if (lane < tcap && lane < ntc) bs[tb + tc + lane] += tot;
+    }
+}
+
+// FP64 form: same mapping, one target chunk of 32 at a time, absolute coordinates.
+__global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
+    int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+    const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
+    const int32_t *__restrict__ utot, const double2 *__restrict__ pos, const double *__restrict__ u, double c2,
+    double *__restrict__ bs) {
+    __shared__ double tgx[kP2PWarps][32], tgy[kP2PWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int widx = blockIdx.x * kP2PWarps + w;
     if (widx >= nleaf) return;
@@ -68,48 +175,32 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p(
     for (int tc = 0; tc < nt; tc += 32) {
         const int ntc = min(32, nt - tc);
         if (lane < ntc) {
-            const int i = tb + tc + lane;
-            if constexpr (std::is_same<T, float>::value) {
-                tgx[w][lane] = loc[i].x;
-                tgy[w][lane] = loc[i].y;
-            } else {
-                tgx[w][lane] = pos[i].x;
-                tgy[w][lane] = pos[i].y;
-            }
+            tgx[w][lane] = pos[tb + tc + lane].x;
+            tgy[w][lane] = pos[tb + tc + lane].y;
         }
         __syncwarp();
-        T acc[32];
+        double acc[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) acc[i] = 0;
-        int r = u0;   // U entry holding this lane's current source position
+        int r = u0;
         for (int q0 = 0; q0 < St; q0 += 32) {
             const int q = q0 + lane;
-            T xs = 0, ys = 0, us = 0;
+            double xs = 0, ys = 0, us = 0;
             if (q < St) {
-                while (r + 1 < u1 && ucum[r + 1] <= q) ++r;
-                const int j = begin[uitems[r]] + (q - ucum[r]);
-                if constexpr (std::is_same<T, float>::value) {
-                    const float2 l = loc[j];
-                    const float2 d = udelta[r];
-                    xs = l.x - d.x;
-                    ys = l.y - d.y;
-                } else {
-                    xs = pos[j].x;
-                    ys = pos[j].y;
-                }
+                const int j = source_index(q, r, u1, ucum, uitems, begin);
+                xs = pos[j].x;
+                ys = pos[j].y;
                 us = u[j];
             }
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (i < ntc) {
-                    const T dx = tgx[w][i] - xs;
-                    const T dy = tgy[w][i] - ys;
-                    const T d2 = dx * dx + (dy * dy + c2);
-                    acc[i] += rsq_p2p<T>(d2) * us;
+                    const double dx = tgx[w][i] - xs, dy = tgy[w][i] - ys;
+                    acc[i] += us / sqrt(dx * dx + (dy * dy + c2));
                 }
             }
         }
-        const T tot = transpose_reduce32<T>(acc, lane);
+        const double tot = lane_reduce<double, 32>(acc, lane);
         if (lane < ntc) bs[tb + tc + lane] += tot;
         __syncwarp();
     }
@@ -120,10 +211,17 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p(
 template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
     const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
-    k_p2p<T><<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
-                                              P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
-                                              P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
-                                              P.loc.as<float2>(), P.pos.as<double2>(), u, (T)(P.c * P.c), bs);
+    if constexpr (std::is_same<T, float>::value) {
+        k_p2p_f32<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
+                                                  P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
+                                                  P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
+                                                  P.loc.as<float2>(), u, (float)(P.c * P.c), bs);
+    } else {
+        k_p2p_f64<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
+                                                  P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
+                                                  P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.pos.as<double2>(), u,
+                                                  P.c * P.c, bs);
+    }
     IMQ_LAUNCH_CHECK();
 }
 

@@ -766,6 +766,7 @@ void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups
             }
         }
     }
+    build_m2l_tiles(P, s);
     int herr = 0;
     IMQ_CUDA(cudaMemcpyAsync(&herr, lerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaStreamSynchronize(s));
