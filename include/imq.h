@@ -141,6 +141,35 @@ imq_status imq_dense_matvec(const double *points, int64_t N, double c, const voi
                             void *out, int nrhs, imq_dtype dt, void *stream);
 
 /* ------------------------------------------------------------------------- *
+ * imq_dense_matvec_noalloc -- the FP32 dense product of imq_dense_matvec for
+ * callers that cannot allocate device memory.  (The paper has no counterpart:
+ * this is an interface for such callers.)
+ *
+ *   Some callers cannot let a library call cudaMalloc or cudaMallocAsync:
+ *   code running under a memory manager that owns all device memory and
+ *   forbids allocations behind its back, or latency-critical loops that
+ *   cannot afford an allocation's possible implicit synchronisation.  This
+ *   entry point allocates nothing: its scratch (the packed source records and
+ *   one error word) lives in a fixed device array of IMQ_NOALLOC_MAX_N + 1
+ *   16-byte records (4 MiB + 16 B) inside the library, which every GPU that
+ *   loads the library keeps until the process exits.
+ *
+ *   points : double[N][2]; v, out : float[N]; all DEVICE memory (host pointers
+ *            are rejected, since staging them would need an allocation).
+ *   N      : 1 <= N <= IMQ_NOALLOC_MAX_N; larger N fails with IMQ_INVALID_ARG.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array, which keeps the previous call's contents
+ *   (each call clears its error word and rewrites the records it uses): calls
+ *   that overlap on the GPU race and must be serialised by the caller, e.g.
+ *   on one stream.  Work is enqueued on `stream`; the call does not wait.
+ *   Errors: IMQ_INVALID_ARG, IMQ_UNSUPPORTED, IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+#define IMQ_NOALLOC_MAX_N 262144
+imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, const float *v,
+                                    float *out, void *stream);
+
+/* ------------------------------------------------------------------------- *
  * Introspection of a plan, for tests and benchmarks.
  * ------------------------------------------------------------------------- */
 typedef struct imq_plan_info {

@@ -47,6 +47,7 @@ SIGNATURES = {
     "imq_matvec": (INT, [P, P, P, INT, INT, P]),
     "imq_matvec_timed": (INT, [P, P, P, INT, INT, P, P, INT, P]),
     "imq_dense_matvec": (INT, [P, I64, D, P, P, INT, INT, P]),
+    "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
     "imq_plan_get_info": (INT, [P, P]),
     "imq_plan_export_tree": (INT, [P, P, P, P, P, P, P, P, P]),
     "imq_plan_export_list": (INT, [P, CHAR, P, P]),

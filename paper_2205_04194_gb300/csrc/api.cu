@@ -93,6 +93,8 @@ int g_dev_ok[64] = {0};   // 0 unknown, 1 ok, -1 unsupported
 
 }  // namespace
 
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
 void check_device() {
     int dev = 0;
     IMQ_CUDA(cudaGetDevice(&dev));

@@ -10,6 +10,8 @@
 // once per tile, which keeps the rounding error of a 10^6-term sum at the
 // level of one tile.
 // FP64 form: the same loop in double with 1/sqrt, plain cooperative loads.
+#include <mutex>
+
 #include "imq_internal.h"
 #include "ptx.cuh"
 
@@ -154,4 +156,78 @@ void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d
     if (h_err & kErrWaitTimeout) fail(IMQ_TIMEOUT, "dense matvec: shared-memory tile wait timed out");
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// imq_dense_matvec_noalloc: the FP32 dense product above with its scratch (the
+// packed (x, y, v, 0) source records and the wait-timeout word) held in one
+// file-scope device array instead of memory obtained from cudaMallocAsync.
+// Every GPU that loads the library keeps this array (IMQ_NOALLOC_MAX_N + 1
+// float4 records, 4 MiB + 16 B) until the process exits.  The host only ever
+// handles the array through the device address cudaGetSymbolAddress returns
+// for the current device; the array's name in host code is a host-side stand-in
+// and must never be passed to a kernel.
+namespace {
+
+static __device__ __align__(256) float4 g_noalloc_scratch[IMQ_NOALLOC_MAX_N + 1];
+
+std::mutex g_noalloc_mu;
+float4 *g_noalloc_addr[64] = {nullptr};
+
+// Device address of the scratch array on the current device, resolved once per device.
+float4 *noalloc_scratch() {
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(IMQ_UNSUPPORTED, "imq_dense_matvec_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            fail(IMQ_CUDA_ERROR, std::string("imq_dense_matvec_noalloc: cudaGetSymbolAddress failed: ") +
+                                     cudaGetErrorString(e));
+        }
+        g_noalloc_addr[dev] = static_cast<float4 *>(p);
+    }
+    return g_noalloc_addr[dev];
+}
+
+bool is_device_memory(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+void dense_matvec_noalloc(const double *points, int64_t N, double c, const float *v, float *out, cudaStream_t s) {
+    if (!points || !v || !out) fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: NULL pointer");
+    if (N < 1) fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: N must be >= 1");
+    if (N > IMQ_NOALLOC_MAX_N)
+        fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: N = " + std::to_string(N) +
+                                  " exceeds the fixed scratch capacity IMQ_NOALLOC_MAX_N = " +
+                                  std::to_string((long long)IMQ_NOALLOC_MAX_N));
+    if (!(c > 0) || !(c < INFINITY)) fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: c must be finite and > 0");
+    if (!is_device_memory(points) || !is_device_memory(v) || !is_device_memory(out))
+        fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: points, v and out must be device memory");
+    check_device();
+    float4 *src = noalloc_scratch();
+    int *err = reinterpret_cast<int *>(src + IMQ_NOALLOC_MAX_N);
+    IMQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    pack_sources<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(points, v, N, src);
+    IMQ_LAUNCH_CHECK();
+    const unsigned grid = (unsigned)((N + kThreads * kTPT - 1) / (kThreads * kTPT));
+    dense_f32<float><<<grid, kThreads, 0, s>>>(src, N, (float)(c * c), out, err);
+    IMQ_LAUNCH_CHECK();
+}
+
 }  // namespace imq
+
+extern "C" imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, const float *v,
+                                               float *out, void *stream) {
+    return imq::guarded_call([&] {
+        imq::dense_matvec_noalloc(points, N, c, v, out, static_cast<cudaStream_t>(stream));
+    });
+}

@@ -34,6 +34,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(imq_status s, const std::string &msg);
+void set_last_error(const std::string &msg);
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 #define IMQ_CUDA(call) ::imq::cuda_check((call), #call, __FILE__, __LINE__)
 #define IMQ_LAUNCH_CHECK() ::imq::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
@@ -168,5 +169,19 @@ void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d
                       int nrhs, imq_dtype dt, cudaStream_t s);
 // api.cu helpers
 void check_device();
+template <class F>
+imq_status guarded_call(F &&f) {   // run f, translate exceptions into a status and the thread's last error
+    try {
+        f();
+        set_last_error("");
+        return IMQ_OK;
+    } catch (const Error &e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (...) {
+        set_last_error("unexpected internal error");
+        return IMQ_CUDA_ERROR;
+    }
+}
 
 }  // namespace imq

@@ -158,8 +158,24 @@ def dense_matvec(points, c: float, v, out=None, stream=None):
     return out
 
 
+def dense_matvec_noalloc(points, c: float, v, out, stream=None):
+    """imq_dense_matvec_noalloc: FP32 dense product that allocates no device memory.
+
+    For callers that may not allocate (their memory manager owns the device, or
+    the call sits on a path that cannot afford an allocation): points (float64
+    [N,2]), v and out (float32 [N]) must be CUDA tensors, N <= 262144.  Calls on
+    overlapping streams race on the library's one fixed scratch array.
+    """
+    n = int(points.shape[0])
+    pp, kp = _buf(points, torch.float64)
+    vp, kv = _buf(v, torch.float32)
+    op, ko = _buf(out, torch.float32)
+    call("imq_dense_matvec_noalloc", pp, n, float(c), vp, op, _stream(stream))
+    return out
+
+
 def version() -> str:
     return _lib.load().imq_version().decode()
 
 
-__all__ = ["Plan", "dense_matvec", "version", "ImqError", "F32", "F64"]
+__all__ = ["Plan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
