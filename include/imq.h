@@ -129,6 +129,72 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
                             int32_t *launches);
 
 /* ------------------------------------------------------------------------- *
+ * imq_cg_solve -- solve A coef = f (Section 2, Eq. (3)-(4): the interpolant
+ * reproduces the data at the nodes) by preconditioned conjugate gradients on
+ * the fast product.  The paper names iterative methods as the solver whose
+ * cost is the matrix-vector product (Section 2) and leaves the solver and a
+ * preconditioner to future work (Section 4).
+ *
+ *   f    : double[nrhs][N], host or device, caller's point order.
+ *   coef : double[nrhs][N], host or device; initial guess on entry when
+ *          opt->x0_given, solution on exit (also on IMQ_NOT_CONVERGED: the
+ *          iterate with the smallest recursive residual of the last pass).
+ *   opt  : NULL for imq_cg_default_options().
+ *   info : may be NULL; receives iterations, outer steps, the true relative
+ *          residual ||f - A coef||_2 / ||f||_2 of each right-hand side
+ *          (computed with the FP64 product selected by opt->residual), time.
+ *
+ *   Inner iterations run the FP32 fast product with FP64 vectors, dots and
+ *   scalars, captured into a CUDA graph with a device-side convergence test.
+ *   With refine_steps > 0 an outer loop recomputes r = f - A coef in FP64 and
+ *   solves A d = r (iterative refinement).  Synchronises `stream`.
+ *   Errors: IMQ_INVALID_ARG, IMQ_NOT_CONVERGED (tolerance not reached within
+ *   maxit / refine_steps), IMQ_NUMERICAL (NaN/Inf or breakdown), IMQ_OOM,
+ *   IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+typedef enum imq_precond { IMQ_PRECOND_NONE = 0, IMQ_PRECOND_SCHWARZ = 1 } imq_precond;
+typedef enum imq_operator {
+    IMQ_OPERATOR_FAST_F32 = 0,   /* inner iterations on the FP32 fast product (default)   */
+    IMQ_OPERATOR_FAST_F64 = 1,   /* inner iterations on the FP64 fast product              */
+    IMQ_OPERATOR_DENSE_F64 = 2   /* inner iterations on the dense FP64 product (O(N^2))    */
+} imq_operator;
+typedef enum imq_residual {
+    IMQ_RESIDUAL_PLAN_F64 = 0,   /* the fast product in FP64 (opt->residual_plan if given, else plan) */
+    IMQ_RESIDUAL_DENSE_F64 = 1   /* the dense FP64 product (exact up to rounding, O(N^2))          */
+} imq_residual;
+#define IMQ_CG_MAX_RHS_INFO 16
+
+typedef struct imq_cg_options {
+    int32_t struct_size;
+    double rtol;             /* target of the true relative residual                         */
+    int32_t maxit;           /* cap on the total number of inner iterations                   */
+    int32_t precond;         /* imq_precond                                                    */
+    int32_t schwarz_nmax;    /* max points per Schwarz patch, 1..224 (0: 128)                  */
+    double schwarz_shift;    /* patch diagonal shift, relative to A_ii = 1/c                   */
+    int32_t refine_steps;    /* outer refinement steps (0: one pass, then the true residual)   */
+    double inner_rtol;       /* lower bound of the inner relative tolerance when refining      */
+    int32_t residual;        /* imq_residual                                                   */
+    int32_t x0_given;        /* 1: coef holds the initial guess                                */
+    imq_plan_t residual_plan;/* optional plan on the same points (e.g. larger p), or NULL      */
+    int32_t inner_operator;  /* imq_operator                                                   */
+    int32_t schwarz_fp64;    /* 1: factor and apply the Schwarz patches in FP64 (nmax <= 160)   */
+    int32_t reserved[6];
+} imq_cg_options;
+
+typedef struct imq_cg_info {
+    int32_t iterations;      /* inner iterations, summed over right-hand sides and outer steps */
+    int32_t outer_steps;
+    imq_status status;
+    double max_rel_residual; /* max over right-hand sides of the true relative residual       */
+    double seconds;          /* wall time of the solve (after preconditioner set-up)           */
+    double rel_residual[IMQ_CG_MAX_RHS_INFO];
+} imq_cg_info;
+
+void imq_cg_default_options(imq_cg_options *opt);
+imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs,
+                        const imq_cg_options *opt, imq_cg_info *info, void *stream);
+
+/* ------------------------------------------------------------------------- *
  * imq_dense_matvec -- the plain ("standard row-column") product of Section 3:
  * b_i = sum_j v_j / sqrt(|x_i - x_j|^2 + c^2) over all N^2 pairs, matrix-free.
  *

@@ -40,6 +40,18 @@ class PlanInfo(ctypes.Structure):
                 ("m2l_pairs", I64), ("device_bytes", I64)]
 
 
+class CgOptions(ctypes.Structure):
+    _fields_ = [("struct_size", I32), ("rtol", D), ("maxit", I32), ("precond", I32), ("schwarz_nmax", I32),
+                ("schwarz_shift", D), ("refine_steps", I32), ("inner_rtol", D), ("residual", I32),
+                ("x0_given", I32), ("residual_plan", P), ("inner_operator", I32), ("schwarz_fp64", I32),
+                ("reserved", I32 * 6)]
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iterations", I32), ("outer_steps", I32), ("status", INT), ("max_rel_residual", D),
+                ("seconds", D), ("rel_residual", D * 16)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "imq_plan": (INT, [P, I64, D, INT, INT, P, P, P]),
@@ -47,6 +59,8 @@ SIGNATURES = {
     "imq_matvec": (INT, [P, P, P, INT, INT, P]),
     "imq_matvec_timed": (INT, [P, P, P, INT, INT, P, P, INT, P]),
     "imq_dense_matvec": (INT, [P, I64, D, P, P, INT, INT, P]),
+    "imq_cg_default_options": (None, [P]),
+    "imq_cg_solve": (INT, [P, P, P, INT, P, P, P]),
     "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
     "imq_plan_get_info": (INT, [P, P]),
     "imq_plan_export_tree": (INT, [P, P, P, P, P, P, P, P, P]),

@@ -231,6 +231,67 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
     });
 }
 
+void imq_cg_default_options(imq_cg_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(imq_cg_options);
+    o->rtol = 1e-6;
+    o->maxit = 1000;
+    o->precond = IMQ_PRECOND_SCHWARZ;
+    o->schwarz_nmax = 128;
+    o->schwarz_shift = 0.0;
+    o->refine_steps = 0;
+    o->inner_rtol = 1e-4;
+    o->residual = IMQ_RESIDUAL_PLAN_F64;
+}
+
+imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs, const imq_cg_options *opt,
+                        imq_cg_info *info, void *stream) {
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = IMQ_CUDA_ERROR;
+    }
+    const imq_status st = guard([&] {
+        if (!plan || !f || !coef) fail(IMQ_INVALID_ARG, "imq_cg_solve: NULL pointer");
+        if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_cg_solve: nrhs must be >= 1");
+        imq_cg_options o;
+        imq_cg_default_options(&o);
+        if (opt) {
+            if (opt->struct_size < (int)offsetof(imq_cg_options, reserved))
+                fail(IMQ_INVALID_ARG, "imq_cg_solve: imq_cg_options.struct_size too small");
+            std::memcpy(&o, opt, std::min(sizeof(o), (size_t)opt->struct_size));
+        }
+        if (!(o.rtol > 0) || !std::isfinite(o.rtol)) fail(IMQ_INVALID_ARG, "imq_cg_solve: rtol must be > 0");
+        if (o.maxit < 1) fail(IMQ_INVALID_ARG, "imq_cg_solve: maxit must be >= 1");
+        if (o.precond != IMQ_PRECOND_NONE && o.precond != IMQ_PRECOND_SCHWARZ)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown preconditioner");
+        if (o.schwarz_nmax < 0 || o.schwarz_nmax > 224) fail(IMQ_INVALID_ARG, "imq_cg_solve: schwarz_nmax must be in [0, 224]");
+        if (o.inner_operator < IMQ_OPERATOR_FAST_F32 || o.inner_operator > IMQ_OPERATOR_DENSE_F64)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown inner operator");
+        if (o.schwarz_fp64 && o.schwarz_nmax > 160)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: schwarz_nmax must be <= 160 with FP64 patches");
+        if (o.residual != IMQ_RESIDUAL_PLAN_F64 && o.residual != IMQ_RESIDUAL_DENSE_F64)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown residual mode");
+        Plan &P = plan->P;
+        Plan *RP = o.residual_plan ? &o.residual_plan->P : nullptr;
+        if (RP && RP->N != P.N) fail(IMQ_INVALID_ARG, "imq_cg_solve: residual_plan has a different N");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t bytes = sizeof(double) * (size_t)nrhs * P.N;
+        DevIn df(f, bytes, s);
+        DevOut dx(coef, bytes, s);
+        if (o.x0_given && dx.tmp) IMQ_CUDA(cudaMemcpyAsync(dx.ptr, coef, bytes, cudaMemcpyHostToDevice, s));
+        try {
+            cg_solve(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o, RP, info, s);
+        } catch (const Error &e) {
+            if (e.status == IMQ_NOT_CONVERGED || e.status == IMQ_NUMERICAL) dx.finish();
+            throw;
+        }
+        dx.finish();
+    });
+    if (info) info->status = st;
+    return st;
+}
+
 imq_status imq_dense_matvec(const double *points, int64_t N, double c, const void *v, void *out, int nrhs,
                             imq_dtype dt, void *stream) {
     return guard([&] {

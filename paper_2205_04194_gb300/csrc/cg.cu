@@ -1,0 +1,667 @@
+// Iterative solve of the interpolation system A coef = f (paper Section 2,
+// Eq. (3)-(4)).  The paper names iterative methods as the practical solver
+// whose cost is dominated by the matrix-vector product (Section 2) and leaves
+// their use with the fast product, and a preconditioner, to future work
+// (Section 4).  Built here:
+//
+//  * preconditioned conjugate gradients (A is symmetric positive definite for
+//    distinct points) with the FP32 fast product as the operator and FP64
+//    vectors, dots and scalars; all vectors stay in Morton order so an
+//    iteration has no gather or scatter;
+//  * deterministic reductions: fixed grid, fixed per-block tree, fixed-order
+//    second stage, so a solve is bit-reproducible;
+//  * iterations captured into a CUDA graph (kIterPerGraph at a time) with the
+//    convergence test on the device: once the residual test passes, the
+//    remaining captured iterations skip their vector updates; the host reads
+//    the state once per graph launch;
+//  * symmetric additive Schwarz preconditioner z = sum_b R_b^T (A_b + d I)^{-1} R_b r
+//    over patches made of a leaf and its nearest adjacent leaves (whole leaves,
+//    nearest centre first, up to nmax points); each patch matrix is factored
+//    once in FP32 (Cholesky in shared memory) and applied by one warp with
+//    forward/backward substitution; overlapping patch results are summed per
+//    point in a fixed order;
+//  * outer iterative refinement: r = f - A x with an FP64 product (the plan in
+//    FP64, or the dense FP64 product), inner PCG on A d = r, x += d.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "imq_internal.h"
+#include "ptx.cuh"
+#include "util.cuh"
+
+namespace imq {
+namespace {
+
+constexpr int kRedBlocks = 608;
+constexpr int kRedThreads = 256;
+constexpr int kIterPerGraph = 8;
+
+enum CGState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3 };
+
+struct CGScalars {
+    double rz, rz_new, pq, rr, alpha, beta, rr_target, rr_best, rr0;
+    int iter, done, status, maxit, improved, pad;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__device__ __forceinline__ double final_sum(const double *part) {
+    __shared__ double sh[kRedThreads];
+    double v = 0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) v += part[i];
+    return block_sum(v, sh);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_p_to_f32(const double *__restrict__ p, float *__restrict__ u,
+                                                          int64_t n, const CGScalars *S) {
+    if (S->done) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = (float)p[i];
+}
+
+// q = (double) b and per-block partial of p.q
+__global__ void __launch_bounds__(kRedThreads) k_q_dot(const float *__restrict__ b, const double *__restrict__ p,
+                                                       double *__restrict__ q, int64_t n, double *__restrict__ part,
+                                                       const CGScalars *S) {
+    __shared__ double sh[kRedThreads];
+    if (S->done) return;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double qi = (double)b[i];
+        q[i] = qi;
+        acc += p[i] * qi;
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finish_alpha(const double *__restrict__ part, CGScalars *S) {
+    if (S->done) return;
+    const double pq = final_sum(part);
+    if (threadIdx.x == 0) {
+        S->pq = pq;
+        if (!(pq > 0) || !isfinite(pq)) {
+            S->status = kNumerical;
+            S->done = 1;
+        } else {
+            S->alpha = S->rz / pq;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(double *__restrict__ x, double *__restrict__ r,
+                                                           const double *__restrict__ p, const double *__restrict__ q,
+                                                           int64_t n, double *__restrict__ part, const CGScalars *S) {
+    __shared__ double sh[kRedThreads];
+    if (S->done) return;
+    const double a = S->alpha;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finish_rr(const double *__restrict__ part, CGScalars *S) {
+    if (S->done) return;
+    const double rr = final_sum(part);
+    if (threadIdx.x == 0) {
+        S->rr = rr;
+        S->iter += 1;
+        S->improved = 0;
+        if (!isfinite(rr)) {
+            S->status = kNumerical;
+            S->done = 1;
+        } else {
+            if (rr < S->rr_best) {
+                S->rr_best = rr;
+                S->improved = 1;
+            }
+            if (rr <= S->rr_target) {
+                S->status = kConverged;
+                S->done = 1;
+            } else if (S->iter >= S->maxit) {
+                S->status = kMaxIter;
+                S->done = 1;
+            }
+        }
+    }
+}
+
+// keep the iterate with the smallest recursive residual
+__global__ void k_copy_best(const double *__restrict__ x, double *__restrict__ xb, int64_t n, const CGScalars *S) {
+    if (!S->improved) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        xb[i] = x[i];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_dot_part(const double *__restrict__ a, const double *__restrict__ b,
+                                                          int64_t n, double *__restrict__ part, const CGScalars *S) {
+    __shared__ double sh[kRedThreads];
+    if (S && S->done) return;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i] * b[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finish_beta(const double *__restrict__ part, CGScalars *S,
+                                                             int use_rr) {
+    if (S->done) return;
+    const double rzn = use_rr ? S->rr : final_sum(part);
+    if (threadIdx.x == 0) {
+        S->rz_new = rzn;
+        if (!(S->rz > 0) || !isfinite(rzn)) {
+            S->status = kNumerical;
+            S->done = 1;
+        } else {
+            S->beta = rzn / S->rz;
+        }
+    }
+}
+
+__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ z, int64_t n, CGScalars *S) {
+    if (S->done) return;
+    const double bt = S->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + bt * p[i];
+}
+
+__global__ void k_commit(CGScalars *S) {
+    if (S->done) return;
+    S->rz = S->rz_new;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum_to(const double *__restrict__ part, double *out) {
+    const double v = final_sum(part);
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_axpby(double *__restrict__ y, const double *__restrict__ x, double a, double b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_sub(double *__restrict__ r, const double *__restrict__ f, const double *__restrict__ ax, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = f[i] - ax[i];
+}
+
+__global__ void k_gather_f64(const double *__restrict__ v, const int32_t *__restrict__ perm, int64_t n,
+                             double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v[perm[i]];
+}
+
+__global__ void k_scatter_f64(const double *__restrict__ v, const int32_t *__restrict__ perm, int64_t n,
+                              double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = v[i];
+}
+
+// ------------------------------------------------------------------ Schwarz preconditioner
+// Factor one patch: A_b + shift*I assembled in FP32 from FP64 coordinate
+// differences, right-looking Cholesky in shared memory; pivots below
+// dmin are raised to dmin (the patch matrices of flat shapes are numerically
+// singular).  Output: n x n column-major lower factor.
+template <class T>
+__global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
+                                 const int64_t *__restrict__ foff, const double2 *__restrict__ pos, T c2,
+                                 T shift, T dmin, T *__restrict__ factor, int *nclamped) {
+    extern __shared__ __align__(16) unsigned char smraw_f[];
+    T *A = reinterpret_cast<T *>(smraw_f);   // n x n, column-major
+    const int b = blockIdx.x;
+    if (b >= npatch) return;
+    const int o = poff[b], n = poff[b + 1] - o;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int j = e / n, i = e - j * n;   // column j, row i
+        const double2 pi = pos[ppts[o + i]], pj = pos[ppts[o + j]];
+        const T dx = (T)(pi.x - pj.x), dy = (T)(pi.y - pj.y);
+        T a = (T)1 / sqrt(dx * dx + dy * dy + c2);
+        if (i == j) a += shift;
+        A[e] = a;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            T d = A[k * n + k];
+            if (!(d > dmin)) {
+                d = dmin;
+                atomicAdd(nclamped, 1);
+            }
+            A[k * n + k] = sqrt(d);
+        }
+        __syncthreads();
+        const T piv = A[k * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[k * n + i] /= piv;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int jj = e / m, ii = e - jj * m;
+            const int j = k + 1 + jj, i = k + 1 + ii;
+            if (i >= j) A[j * n + i] -= A[k * n + i] * A[k * n + j];
+        }
+        __syncthreads();
+    }
+    T *F = factor + foff[b];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int j = e / n, i = e - j * n;
+        F[e] = i >= j ? A[e] : (T)0;
+    }
+}
+
+// One warp per patch: y = (L L^T)^{-1} r_patch by forward and backward substitution.
+constexpr int kSchwarzRowsPerLane = 8;   // patches up to 256 points
+template <class T>
+__global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
+                                const int64_t *__restrict__ foff, const T *__restrict__ factor,
+                                const double *__restrict__ r, double *__restrict__ ypatch, const CGScalars *S) {
+    if (S->done) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= npatch) return;
+    const int o = poff[warp], n = poff[warp + 1] - o;
+    const T *F = factor + foff[warp];
+    T v[kSchwarzRowsPerLane];
+#pragma unroll
+    for (int t = 0; t < kSchwarzRowsPerLane; ++t) {
+        const int i = lane + 32 * t;
+        v[t] = i < n ? (T)r[ppts[o + i]] : (T)0;
+    }
+    // forward: L y = r
+    for (int k = 0; k < n; ++k) {
+        const int owner = k & 31, tk = k >> 5;
+        T val = 0;
+#pragma unroll
+        for (int t = 0; t < kSchwarzRowsPerLane; ++t)
+            if (t == tk) val = v[t];
+        const T yk = __shfl_sync(0xFFFFFFFFu, val / F[(size_t)k * n + k], owner);
+#pragma unroll
+        for (int t = 0; t < kSchwarzRowsPerLane; ++t) {
+            const int i = lane + 32 * t;
+            if (i == k) v[t] = yk;
+            else if (i > k && i < n) v[t] -= F[(size_t)k * n + i] * yk;
+        }
+    }
+    // backward: L^T z = y
+    for (int k = n - 1; k >= 0; --k) {
+        T part = 0;
+#pragma unroll
+        for (int t = 0; t < kSchwarzRowsPerLane; ++t) {
+            const int i = lane + 32 * t;
+            if (i > k && i < n) part += F[(size_t)k * n + i] * v[t];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
+        const int owner = k & 31, tk = k >> 5;
+#pragma unroll
+        for (int t = 0; t < kSchwarzRowsPerLane; ++t)
+            if (t == tk && lane == owner) v[t] = (v[t] - part) / F[(size_t)k * n + k];
+    }
+#pragma unroll
+    for (int t = 0; t < kSchwarzRowsPerLane; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) ypatch[o + i] = (double)v[t];
+    }
+}
+
+// z_j = sum over the patch slots holding point j (fixed order); points in no patch get c r_j.
+__global__ void k_schwarz_gather(int64_t n, const int32_t *__restrict__ ptoff, const int32_t *__restrict__ ptslot,
+                                 const double *__restrict__ ypatch, const double *__restrict__ r, double cdiag,
+                                 double *__restrict__ z, const CGScalars *S) {
+    if (S->done) return;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int a = ptoff[j], e = ptoff[j + 1];
+        if (a == e) {
+            z[j] = cdiag * r[j];
+        } else {
+            double s = 0;
+            for (int k = a; k < e; ++k) s += ypatch[ptslot[k]];
+            z[j] = s;
+        }
+    }
+}
+
+template <class T>
+void upload_vec(DevMem &d, const std::vector<T> &h, cudaStream_t s) {
+    d.alloc(sizeof(T) * std::max<size_t>(1, h.size()));
+    if (!h.empty()) IMQ_CUDA(cudaMemcpyAsync(d.ptr, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+}
+
+void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
+    Schwarz &Z = P.schwarz;
+    if (Z.ready && Z.nmax == nmax && Z.shift == shift && Z.fp64 == fp64) return;
+    const int nb = P.nbox;
+    std::vector<int32_t> uoff(nb + 1), beg(nb), en(nb), leaves(P.nleaf);
+    std::vector<double2> cen(nb);
+    IMQ_CUDA(cudaMemcpyAsync(uoff.data(), P.U.off.ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> uit(std::max<int64_t>(1, P.U.total));
+    if (P.U.total)
+        IMQ_CUDA(cudaMemcpyAsync(uit.data(), P.U.items.ptr, sizeof(int32_t) * P.U.total, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(beg.data(), P.begin.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(en.data(), P.end.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(cen.data(), P.centre.ptr, sizeof(double2) * nb, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(leaves.data(), P.leaves.ptr, sizeof(int32_t) * P.nleaf, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> poff{0}, ppts;
+    std::vector<int64_t> foff;
+    int64_t fsz = 0;
+    int maxn = 0;
+    for (int li = 0; li < P.nleaf; ++li) {
+        const int b = leaves[li];
+        std::vector<std::pair<double, int>> cand;
+        for (int k = uoff[b]; k < uoff[b + 1]; ++k) {
+            const int q = uit[k];
+            const double dx = cen[q].x - cen[b].x, dy = cen[q].y - cen[b].y;
+            cand.push_back({q == b ? -1.0 : dx * dx + dy * dy, q});
+        }
+        std::sort(cand.begin(), cand.end());
+        int cnt = 0;
+        for (auto &cq : cand) {
+            const int q = cq.second, m = en[q] - beg[q];
+            if (q != b && cnt + m > nmax) continue;
+            for (int j = beg[q]; j < en[q] && cnt < nmax; ++j, ++cnt) ppts.push_back(j);
+        }
+        poff.push_back((int32_t)ppts.size());
+        foff.push_back(fsz);
+        fsz += (int64_t)cnt * cnt;
+        maxn = std::max(maxn, cnt);
+    }
+    Z.npatch = P.nleaf;
+    Z.total_slots = (int64_t)ppts.size();
+    // reverse map point -> slots, in increasing slot order (deterministic sums)
+    std::vector<int32_t> ptcnt(P.N + 1, 0);
+    for (auto j : ppts) ptcnt[j + 1]++;
+    for (int64_t j = 0; j < P.N; ++j) ptcnt[j + 1] += ptcnt[j];
+    std::vector<int32_t> ptslot(ppts.size()), cur(ptcnt.begin(), ptcnt.end() - 1);
+    for (size_t sl = 0; sl < ppts.size(); ++sl) ptslot[cur[ppts[sl]]++] = (int32_t)sl;
+    upload_vec(Z.patch_off, poff, s);
+    upload_vec(Z.patch_pts, ppts, s);
+    upload_vec(Z.fac_off, foff, s);
+    upload_vec(Z.pt_off, ptcnt, s);
+    upload_vec(Z.pt_slot, ptslot, s);
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    Z.factor.alloc(es * std::max<int64_t>(1, fsz));
+    Z.ypatch.alloc(sizeof(double) * std::max<int64_t>(1, Z.total_slots));
+    AsyncMem ncl(sizeof(int), s);
+    IMQ_CUDA(cudaMemsetAsync(ncl.ptr, 0, sizeof(int), s));
+    const size_t smem = es * (size_t)maxn * maxn;
+    const double diag = 1.0 / P.c;
+    if (fp64) {
+        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_schwarz_factor<double><<<Z.npatch, 256, smem, s>>>(
+            Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
+            P.pos.as<double2>(), P.c * P.c, shift * diag, 1e-14 * diag, Z.factor.as<double>(), ncl.as<int>());
+    } else {
+        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_schwarz_factor<float><<<Z.npatch, 256, smem, s>>>(
+            Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
+            P.pos.as<double2>(), (float)(P.c * P.c), (float)(shift * diag), (float)(1e-6 * diag),
+            Z.factor.as<float>(), ncl.as<int>());
+    }
+    IMQ_LAUNCH_CHECK();
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    Z.nmax = nmax;
+    Z.shift = shift;
+    Z.fp64 = fp64;
+    Z.ready = true;
+}
+
+void schwarz_apply(const Schwarz &Z, const double *r, double *z, double c, int64_t n, const CGScalars *S,
+                   cudaStream_t s) {
+    const unsigned g = blocks_for((int64_t)Z.npatch * 32, 128);
+    if (Z.fp64)
+        k_schwarz_solve<double><<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
+                                                  Z.fac_off.as<int64_t>(), Z.factor.as<double>(), r,
+                                                  Z.ypatch.as<double>(), S);
+    else
+        k_schwarz_solve<float><<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
+                                                 Z.fac_off.as<int64_t>(), Z.factor.as<float>(), r,
+                                                 Z.ypatch.as<double>(), S);
+    k_schwarz_gather<<<kRedBlocks, kRedThreads, 0, s>>>(n, Z.pt_off.as<int32_t>(), Z.pt_slot.as<int32_t>(),
+                                                        Z.ypatch.as<double>(), r, c, z, S);
+    IMQ_LAUNCH_CHECK();
+}
+
+struct Work {
+    DevMem x, xb, r, p, q, z, u32, b32, part, S, tmp;
+};
+
+double read_dot(const double *a, const double *b, int64_t n, DevMem &part, DevMem &tmp, cudaStream_t s) {
+    k_dot_part<<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, part.as<double>(), nullptr);
+    IMQ_LAUNCH_CHECK();
+    k_sum_to<<<1, kRedThreads, 0, s>>>(part.as<double>(), tmp.as<double>());
+    IMQ_LAUNCH_CHECK();
+    double h = 0;
+    IMQ_CUDA(cudaMemcpyAsync(&h, tmp.ptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// FP64 residual product in the Morton order of plan P: out = A v.  mode 1: the
+// dense FP64 product; otherwise the fast product of RP (or P) in FP64.
+void residual_product(Plan &P, Plan *RP, int mode, const double *vs, double *outs, cudaStream_t s) {
+    const unsigned g = blocks_for(P.N, 256);
+    if (mode == 1) {
+        dense_matvec_dev(P.pos.as<double>(), P.N, P.c, vs, outs, 1, IMQ_F64, s);
+        return;
+    }
+    if (RP && RP != &P) {   // another plan on the same points: go through the caller's order
+        AsyncMem orig(sizeof(double) * P.N, s), us(sizeof(double) * P.N, s), bs(sizeof(double) * P.N, s),
+            o2(sizeof(double) * P.N, s);
+        k_scatter_f64<<<g, 256, 0, s>>>(vs, P.perm.as<int32_t>(), P.N, orig.as<double>());
+        gather_sorted<double, double>(*RP, orig.as<double>(), us.as<double>(), 1, s);
+        fmm_apply<double>(*RP, us.as<double>(), bs.as<double>(), 1, s);
+        scatter_sorted<double, double>(*RP, bs.as<double>(), o2.as<double>(), 1, s);
+        k_gather_f64<<<g, 256, 0, s>>>(o2.as<double>(), P.perm.as<int32_t>(), P.N, outs);
+        IMQ_LAUNCH_CHECK();
+        return;
+    }
+    fmm_apply<double>(P, vs, outs, 1, s);
+}
+
+}  // namespace
+
+void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o, Plan *RP,
+              imq_cg_info *info, cudaStream_t s) {
+    const int64_t n = P.N;
+    ensure_ops(P, false, s);
+    if (o.residual == IMQ_RESIDUAL_PLAN_F64) ensure_ops(RP ? *RP : P, true, s);
+    if (o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);
+    if (o.precond == IMQ_PRECOND_SCHWARZ)
+        build_schwarz(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    const Schwarz &Z = P.schwarz;
+    Work w;
+    w.x.alloc(8 * n); w.xb.alloc(8 * n); w.r.alloc(8 * n); w.p.alloc(8 * n); w.q.alloc(8 * n); w.z.alloc(8 * n);
+    w.u32.alloc(4 * n); w.b32.alloc(4 * n); w.part.alloc(8 * kRedBlocks); w.S.alloc(sizeof(CGScalars));
+    w.tmp.alloc(64);
+    DevMem xs, fs, rr_out, ax;
+    xs.alloc(8 * n); fs.alloc(8 * n); ax.alloc(8 * n);
+    CGScalars *S = w.S.as<CGScalars>();
+    double *x = w.x.as<double>(), *r = w.r.as<double>(), *p = w.p.as<double>(), *q = w.q.as<double>();
+    double *z = o.precond == IMQ_PRECOND_SCHWARZ ? w.z.as<double>() : r;
+    const unsigned g = blocks_for(n, 256);
+    const unsigned gr = kRedBlocks;
+    // one product outside the capture sets kernel attributes and touches every buffer
+    const int op = o.inner_operator;
+    IMQ_CUDA(cudaMemsetAsync(w.u32.ptr, 0, 4 * n, s));
+    IMQ_CUDA(cudaMemsetAsync(p, 0, 8 * n, s));
+    if (op == IMQ_OPERATOR_FAST_F32) fmm_apply<float>(P, w.u32.as<float>(), w.b32.as<float>(), 1, s);
+    else if (op == IMQ_OPERATOR_FAST_F64) fmm_apply<double>(P, p, q, 1, s);
+    IMQ_CUDA(cudaStreamSynchronize(s));
+
+    // ---- capture kIterPerGraph PCG iterations on a private stream
+    cudaStream_t cs;
+    IMQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    IMQ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < kIterPerGraph; ++it) {
+        if (op == IMQ_OPERATOR_FAST_F32) {
+            k_p_to_f32<<<gr, kRedThreads, 0, cs>>>(p, w.u32.as<float>(), n, S);
+            fmm_apply<float>(P, w.u32.as<float>(), w.b32.as<float>(), 1, cs);
+            k_q_dot<<<gr, kRedThreads, 0, cs>>>(w.b32.as<float>(), p, q, n, w.part.as<double>(), S);
+        } else {
+            if (op == IMQ_OPERATOR_FAST_F64) fmm_apply<double>(P, p, q, 1, cs);
+            else dense_f64_async(P.pos.as<double>(), n, P.c, p, q, cs);
+            k_dot_part<<<gr, kRedThreads, 0, cs>>>(p, q, n, w.part.as<double>(), S);
+        }
+        k_finish_alpha<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S);
+        k_update_xr<<<gr, kRedThreads, 0, cs>>>(x, r, p, q, n, w.part.as<double>(), S);
+        k_finish_rr<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S);
+        k_copy_best<<<gr, kRedThreads, 0, cs>>>(x, w.xb.as<double>(), n, S);
+        if (o.precond == IMQ_PRECOND_SCHWARZ) {
+            schwarz_apply(Z, r, z, P.c, n, S, cs);
+            k_dot_part<<<gr, kRedThreads, 0, cs>>>(r, z, n, w.part.as<double>(), S);
+            k_finish_beta<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S, 0);
+        } else {
+            k_finish_beta<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S, 1);
+        }
+        k_update_p<<<gr, kRedThreads, 0, cs>>>(p, z, n, S);
+        k_commit<<<1, 1, 0, cs>>>(S);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        IMQ_CUDA(ce);
+    }
+    IMQ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+    };
+
+    const auto t0 = std::chrono::steady_clock::now();
+    int total_iter = 0, outer_done = 0, final_status = kConverged;
+    double worst_rel = 0;
+    try {
+        for (int rhs = 0; rhs < nrhs; ++rhs) {
+            const double *f = f_dev + (size_t)rhs * n;
+            double *xo = x_dev + (size_t)rhs * n;
+            k_gather_f64<<<g, 256, 0, s>>>(f, P.perm.as<int32_t>(), n, fs.as<double>());
+            if (o.x0_given) k_gather_f64<<<g, 256, 0, s>>>(xo, P.perm.as<int32_t>(), n, xs.as<double>());
+            else IMQ_CUDA(cudaMemsetAsync(xs.ptr, 0, 8 * n, s));
+            IMQ_LAUNCH_CHECK();
+            const double ff = read_dot(fs.as<double>(), fs.as<double>(), n, w.part, w.tmp, s);
+            const double fn = std::sqrt(ff);
+            double rel = 1.0;
+            int status = kMaxIter;
+            int iters = 0;
+            const int max_outer = std::max(0, o.refine_steps);
+            for (int outer = 0; outer <= max_outer; ++outer) {
+                // residual r = f - A x (FP64 product unless x = 0)
+                if (outer == 0 && !o.x0_given) {
+                    IMQ_CUDA(cudaMemcpyAsync(r, fs.ptr, 8 * n, cudaMemcpyDeviceToDevice, s));
+                } else {
+                    residual_product(P, RP, o.residual == IMQ_RESIDUAL_DENSE_F64 ? 1 : 0, xs.as<double>(),
+                                     ax.as<double>(), s);
+                    k_sub<<<g, 256, 0, s>>>(r, fs.as<double>(), ax.as<double>(), n);
+                    IMQ_LAUNCH_CHECK();
+                }
+                const double rr0 = read_dot(r, r, n, w.part, w.tmp, s);
+                rel = fn > 0 ? std::sqrt(rr0) / fn : 0.0;
+                if (!std::isfinite(rel)) {
+                    status = kNumerical;
+                    break;
+                }
+                if (rel <= o.rtol) {
+                    status = kConverged;
+                    break;
+                }
+                if (outer == max_outer && outer > 0) break;
+                if (iters >= o.maxit) break;
+                // inner PCG on A d = r from d = 0
+                // the recursive residual of the inner operator drifts from the true one by about the
+                // operator's rounding error, so a single pass aims at half the tolerance
+                const double inner_rtol =
+                    max_outer > 0 ? std::max(o.inner_rtol, std::min(0.5, 0.5 * o.rtol / rel)) : 0.5 * o.rtol / rel;
+                IMQ_CUDA(cudaMemsetAsync(x, 0, 8 * n, s));
+                IMQ_CUDA(cudaMemsetAsync(w.xb.ptr, 0, 8 * n, s));
+                CGScalars h{};
+                h.rr = rr0;
+                h.rr0 = rr0;
+                h.rr_best = rr0;
+                h.rr_target = inner_rtol * inner_rtol * rr0;
+                h.maxit = o.maxit - iters;
+                if (o.precond == IMQ_PRECOND_SCHWARZ) {
+                    CGScalars hz = h;
+                    IMQ_CUDA(cudaMemcpyAsync(S, &hz, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+                    schwarz_apply(Z, r, z, P.c, n, S, s);
+                    h.rz = read_dot(r, z, n, w.part, w.tmp, s);
+                } else {
+                    h.rz = rr0;
+                }
+                IMQ_CUDA(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, s));
+                IMQ_CUDA(cudaMemcpyAsync(S, &h, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+                CGScalars hs{};
+                for (;;) {
+                    IMQ_CUDA(cudaGraphLaunch(exec, s));
+                    IMQ_CUDA(cudaMemcpyAsync(&hs, S, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+                    IMQ_CUDA(cudaStreamSynchronize(s));
+                    if (hs.done) break;
+                }
+                iters += hs.iter;
+                // x += best inner iterate
+                k_axpby<<<g, 256, 0, s>>>(xs.as<double>(), w.xb.as<double>(), 1.0, 1.0, n);
+                IMQ_LAUNCH_CHECK();
+                outer_done = std::max(outer_done, outer + 1);
+                if (hs.status == kNumerical) {
+                    status = kNumerical;
+                    break;
+                }
+                if (max_outer == 0) {
+                    // single pass: report the true residual of the final iterate
+                    residual_product(P, RP, o.residual == IMQ_RESIDUAL_DENSE_F64 ? 1 : 0, xs.as<double>(),
+                                     ax.as<double>(), s);
+                    k_sub<<<g, 256, 0, s>>>(r, fs.as<double>(), ax.as<double>(), n);
+                    IMQ_LAUNCH_CHECK();
+                    rel = std::sqrt(read_dot(r, r, n, w.part, w.tmp, s)) / fn;
+                    status = rel <= o.rtol ? kConverged : kMaxIter;
+                    break;
+                }
+            }
+            k_scatter_f64<<<g, 256, 0, s>>>(xs.as<double>(), P.perm.as<int32_t>(), n, xo);
+            IMQ_LAUNCH_CHECK();
+            IMQ_CUDA(cudaStreamSynchronize(s));
+            total_iter += iters;
+            worst_rel = std::max(worst_rel, rel);
+            if (status != kConverged) final_status = status == kNumerical ? kNumerical : kMaxIter;
+            if (info && rhs < IMQ_CG_MAX_RHS_INFO) info->rel_residual[rhs] = rel;
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+        info->iterations = total_iter;
+        info->outer_steps = outer_done;
+        info->max_rel_residual = worst_rel;
+        info->seconds = secs;
+        info->status = final_status == kConverged ? IMQ_OK : (final_status == kNumerical ? IMQ_NUMERICAL : IMQ_NOT_CONVERGED);
+    }
+    if (final_status == kNumerical) fail(IMQ_NUMERICAL, "imq_cg_solve: non-finite value or breakdown in CG");
+    if (final_status != kConverged)
+        fail(IMQ_NOT_CONVERGED, "imq_cg_solve: tolerance not reached; coef holds the best iterate");
+}
+
+}  // namespace imq

@@ -127,6 +127,11 @@ __global__ void __launch_bounds__(256) dense_f64(const double *__restrict__ pts,
 
 }  // namespace
 
+void dense_f64_async(const double *d_points, int64_t N, double c, const double *d_v, double *d_out, cudaStream_t s) {
+    dense_f64<double, double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_points, d_v, N, c * c, d_out);
+    IMQ_LAUNCH_CHECK();
+}
+
 void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,
                       int nrhs, imq_dtype dt, cudaStream_t s) {
     AsyncMem err(sizeof(int), s);

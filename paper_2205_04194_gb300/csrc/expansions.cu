@@ -397,8 +397,10 @@ int64_t Plan::device_bytes() const {
     const DevMem *all[] = {&codes, &perm, &level, &prefix, &begin, &end, &parent, &child, &centre, &leaves,
                            &U.off, &U.items, &V.off, &V.items, &W.off, &W.items, &X.off, &X.items,
                            &colleagues, &vtab, &ucum, &uoff, &pos, &loc, &leaf_of,
-                           &ops32.m2m, &ops32.l2l, &ops32.m2l, &ops32.p2mc,
-                           &ops64.m2m, &ops64.l2l, &ops64.m2l, &ops64.p2mc};
+                           &ops32.m2m, &ops32.l2l, &ops32.m2l, &ops32.p2mc, &ops32.M, &ops32.L,
+                           &ops64.m2m, &ops64.l2l, &ops64.m2l, &ops64.p2mc, &ops64.M, &ops64.L,
+                           &schwarz.patch_off, &schwarz.patch_pts, &schwarz.fac_off, &schwarz.factor,
+                           &schwarz.pt_off, &schwarz.pt_slot, &schwarz.ypatch};
     for (auto *d : all) t += (int64_t)d->bytes;
     return t;
 }
@@ -420,6 +422,9 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
             std::copy(tmp.begin(), tmp.end(), P.h_m2l.begin() + (size_t)li * kOffsetClasses * K * K);
         }
     }
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    O.M.alloc(es * (size_t)P.nbox * K);
+    O.L.alloc(es * (size_t)P.nbox * K);
     if (fp64) {
         upload<double>(O.m2m, P.h_m2m, s);
         upload<double>(O.l2l, P.h_l2l, s);
@@ -450,8 +455,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
     ensure_ops(P, f64, s);
     TypedOps &O = f64 ? P.ops64 : P.ops32;
     const int K = P.layout.K, p = P.p, nb = P.nbox;
-    AsyncMem Mbuf(sizeof(T) * (size_t)nb * K, s), Lbuf(sizeof(T) * (size_t)nb * K, s);
-    T *M = Mbuf.as<T>(), *L = Lbuf.as<T>();
+    T *M = O.M.as<T>(), *L = O.L.as<T>();
     const T *m2m = O.m2m.as<T>(), *l2l = O.l2l.as<T>(), *m2l = O.m2l.as<T>(), *coef = O.p2mc.as<T>();
     int launches = 0;
     auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };

@@ -98,7 +98,25 @@ struct ListCSR {
 
 struct TypedOps {        // operator set in one precision
     DevMem m2m, l2l, m2l, p2mc;
+    DevMem M, L;         // expansion workspace (nbox x K), owned by the plan
     bool ready = false;
+};
+
+// Additive Schwarz preconditioner over leaf neighbourhood patches (cg.cu).
+struct Schwarz {
+    bool ready = false;
+    int nmax = 0;
+    double shift = 0;
+    int npatch = 0;
+    DevMem patch_off;    // int32[npatch+1] offsets into patch_pts
+    DevMem patch_pts;    // int32[] sorted point indices of each patch
+    DevMem fac_off;      // int64[npatch] offset of each patch's n*n factor
+    DevMem factor;       // float[] or double[] column-major Cholesky factors
+    bool fp64 = false;
+    DevMem pt_off;       // int32[N+1] reverse map: point -> patch slots
+    DevMem pt_slot;      // int32[] patch slot (patch_off[b] + local index)
+    DevMem ypatch;       // double[total slots] per-patch solutions
+    int64_t total_slots = 0;
 };
 
 struct Plan {
@@ -133,6 +151,7 @@ struct Plan {
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
     TypedOps ops32, ops64;
+    Schwarz schwarz;
     // statistics
     int64_t p2p_pairs = 0, m2l_pairs = 0;
     int64_t device_bytes() const;
@@ -160,6 +179,9 @@ template <class Tin, class T>
 void gather_sorted(const Plan &P, const Tin *v, T *us, int nrhs, cudaStream_t s);
 template <class T, class Tout>
 void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_t s);
+// cg.cu
+void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o, Plan *RP,
+              imq_cg_info *info, cudaStream_t s);
 // m2l.cu
 int m2l_tiled_rows(int K);
 void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s);
@@ -167,6 +189,8 @@ void build_m2l_tiles(Plan &P, cudaStream_t s);
 // dense.cu
 void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,
                       int nrhs, imq_dtype dt, cudaStream_t s);
+// FP64 dense product, kernel launch only (no host synchronisation; graph-capturable)
+void dense_f64_async(const double *d_points, int64_t N, double c, const double *d_v, double *d_out, cudaStream_t s);
 // api.cu helpers
 void check_device();
 template <class F>

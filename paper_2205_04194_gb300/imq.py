@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import ImqError, ImqOptions, PlanInfo, call
+from ._lib import CgInfo, CgOptions, ImqError, ImqOptions, PlanInfo, call
 
 F32 = 0
 F64 = 1
@@ -98,6 +98,43 @@ class Plan:
         op, ko = _buf(out, tdt)
         call("imq_matvec", self._h, vp, op, nrhs, code, _stream(stream))
         return out
+
+    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
+              schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan", x0=None,
+              residual_plan=None, operator="fast_f32", schwarz_fp64=False, stream=None,
+              raise_on_failure=False):
+        """imq_cg_solve: coef with A coef = f.  Returns (coef, info dict); info["status"] is the
+        imq_status name (IMQ_NOT_CONVERGED keeps the best iterate in coef)."""
+        nrhs = 1 if len(np.shape(f)) == 1 else int(np.shape(f)[0])
+        if coef is None:
+            coef = _like(f, 0, F64) if x0 is None else (x0.clone() if isinstance(x0, torch.Tensor) else np.array(x0, dtype=np.float64))
+        elif x0 is not None:
+            raise ValueError("pass either coef or x0")
+        o = CgOptions()
+        _lib.load().imq_cg_default_options(ctypes.byref(o))
+        o.rtol = float(rtol)
+        o.maxit = int(maxit)
+        o.precond = {"none": 0, None: 0, "schwarz": 1}[precond]
+        o.schwarz_nmax = int(schwarz_nmax)
+        o.schwarz_shift = float(schwarz_shift)
+        o.refine_steps = int(refine_steps)
+        o.inner_rtol = float(inner_rtol)
+        o.residual = {"plan": 0, "dense": 1}[residual]
+        o.x0_given = 1 if x0 is not None else 0
+        o.residual_plan = residual_plan._h if residual_plan is not None else None
+        o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[operator]
+        o.schwarz_fp64 = 1 if schwarz_fp64 else 0
+        info = CgInfo()
+        fp, kf = _buf(f, torch.float64)
+        cp, kc = _buf(coef, torch.float64)
+        st = _lib.load().imq_cg_solve(self._h, fp, cp, nrhs, ctypes.byref(o), ctypes.byref(info), _stream(stream))
+        msg = _lib.load().imq_last_error().decode()
+        out = {"status": _lib.status_name(st), "iterations": info.iterations, "outer_steps": info.outer_steps,
+               "max_rel_residual": info.max_rel_residual, "seconds": info.seconds,
+               "rel_residual": list(info.rel_residual)[:min(nrhs, 16)], "message": msg}
+        if st != 0 and (raise_on_failure or st not in (5,)):
+            raise ImqError(st, "imq_cg_solve", msg)
+        return coef, out
 
     PHASES = ("gather", "p2m", "m2m", "m2l", "p2l", "l2l", "l2p_m2p", "p2p", "scatter")
 
