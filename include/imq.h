@@ -99,6 +99,18 @@ typedef struct imq_options {
 imq_status imq_plan(const double *points, int64_t N, double c, int p, int leaf,
                     const imq_options *opt, void *stream, imq_plan_t *out);
 
+/* ------------------------------------------------------------------------- *
+ * imq_plan_eval -- a plan for evaluating the interpolant of Eq. (2),
+ * P(t) = sum_j coef_j phi(|t - x_j|), at off-node targets.  The tree is built
+ * over nodes and targets together (node i is point i, target k is point
+ * n_nodes + k), so the same fast product serves evaluation, its transpose and
+ * the c-derivative (imq_evaluate*).  Arguments as imq_plan; targets may
+ * coincide with nodes (check_duplicates must be 0).
+ * ------------------------------------------------------------------------- */
+imq_status imq_plan_eval(const double *nodes, int64_t n_nodes, const double *targets, int64_t n_targets,
+                         double c, int p, int leaf, const imq_options *opt, void *stream,
+                         imq_plan_t *out);
+
 /* Release every device allocation of the plan (after synchronising its work). */
 void imq_plan_destroy(imq_plan_t plan);
 
@@ -114,6 +126,29 @@ void imq_plan_destroy(imq_plan_t plan);
  * ------------------------------------------------------------------------- */
 imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs,
                       imq_dtype dt, void *stream);
+
+/* ------------------------------------------------------------------------- *
+ * imq_matvec_dc -- b = (dA/dc) v, dA_ij/dc = -c / (|x_i - x_j|^2 + c^2)^{3/2}
+ * (derivative of Eq. (5) in the shape parameter).  Under the lift of Eq. (11)
+ * this is the vertical derivative of the Green's function at the targets, so
+ * the same multipoles and tree serve (odd-parity locals, see dz.cu).
+ * Arguments, layout and errors as imq_matvec.
+ * ------------------------------------------------------------------------- */
+imq_status imq_matvec_dc(imq_plan_t plan, const void *v, void *out, int nrhs,
+                         imq_dtype dt, void *stream);
+
+/* ------------------------------------------------------------------------- *
+ * Evaluation on a plan from imq_plan_eval (Eq. (2)), E_kj = phi(|t_k - x_j|):
+ *   imq_evaluate           out[r][k] = sum_j E_kj coef[r][j]      coef: [nrhs][n_nodes], out: [nrhs][n_targets]
+ *   imq_evaluate_transpose out[r][j] = sum_k E_kj v[r][k]         v: [nrhs][n_targets],  out: [nrhs][n_nodes]
+ *   imq_evaluate_dc        out[r][k] = sum_j dE_kj/dc coef[r][j]
+ * Host or device buffers; errors as imq_matvec, and IMQ_INVALID_ARG for a plan
+ * not made by imq_plan_eval.
+ * ------------------------------------------------------------------------- */
+imq_status imq_evaluate(imq_plan_t eplan, const void *coef, void *out, int nrhs, imq_dtype dt, void *stream);
+imq_status imq_evaluate_transpose(imq_plan_t eplan, const void *v, void *out, int nrhs, imq_dtype dt,
+                                  void *stream);
+imq_status imq_evaluate_dc(imq_plan_t eplan, const void *coef, void *out, int nrhs, imq_dtype dt, void *stream);
 
 /* ------------------------------------------------------------------------- *
  * imq_matvec_timed -- imq_matvec with the kernels of each phase bracketed by
@@ -195,6 +230,24 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
                         const imq_cg_options *opt, imq_cg_info *info, void *stream);
 
 /* ------------------------------------------------------------------------- *
+ * imq_interp_loss_grad -- validation loss of the interpolant (Eq. (2)) and its
+ * gradient in the shape c and the data values f (adjoint method).
+ *   coef = A^{-1} f (CG on `train`), P = E coef on `eval` (a plan from
+ *   imq_plan_eval with the training points as nodes and the validation points
+ *   as targets, same c), L = mean (P - y)^2, g = (2/N_v)(P - y),
+ *   lambda = A^{-1} E^T g, dL/df = lambda, dL/dc = g.(dE/dc coef) - lambda.(dA/dc coef).
+ *   f: double[N]; y: double[N_v]; host or device.  loss, dloss_dc: host scalars.
+ *   dloss_df, coef_out: double[N] (host or device) or NULL.  dt selects the
+ *   precision of the evaluation and derivative products; opt configures both
+ *   solves.  info (may be NULL) sums both solves.  Errors: those of
+ *   imq_cg_solve and imq_evaluate, IMQ_INVALID_ARG for mismatched plans.
+ * ------------------------------------------------------------------------- */
+imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, const double *f, const double *y,
+                                const imq_cg_options *opt, imq_dtype dt, double *loss,
+                                double *dloss_dc, double *dloss_df, double *coef_out,
+                                imq_cg_info *info, void *stream);
+
+/* ------------------------------------------------------------------------- *
  * imq_dense_matvec -- the plain ("standard row-column") product of Section 3:
  * b_i = sum_j v_j / sqrt(|x_i - x_j|^2 + c^2) over all N^2 pairs, matrix-free.
  *
@@ -240,6 +293,7 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  * ------------------------------------------------------------------------- */
 typedef struct imq_plan_info {
     int64_t n_points;
+    int64_t n_nodes;                     /* evaluation plans: nodes among n_points (else 0) */
     int32_t n_boxes, n_leaves, max_level, p, leaf, k_real;  /* k_real: reals per expansion */
     double x0, y0, side, c;
     int64_t n_u, n_v, n_w, n_x;          /* total entries of each interaction list */

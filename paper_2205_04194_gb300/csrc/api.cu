@@ -135,53 +135,102 @@ const char *imq_last_error(void) { return g_last_error.c_str(); }
 
 const char *imq_version(void) { return "imq-gb300 0.1 (sm_103a)"; }
 
+}  // extern "C"
+
+namespace {
+
+void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
+                     double &side, bool &dups) {
+    if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
+    if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
+    if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
+    if (leaf < 1) fail(IMQ_INVALID_ARG, "imq_plan: leaf must be >= 1");
+    dups = false;
+    x0 = 0;
+    y0 = 0;
+    side = -1;
+    if (opt) {
+        if (opt->struct_size < (int)offsetof(imq_options, reserved))
+            fail(IMQ_INVALID_ARG, "imq_plan: imq_options.struct_size too small");
+        if (opt->has_domain) {
+            if (!std::isfinite(opt->x0) || !std::isfinite(opt->y0) || !std::isfinite(opt->side) || opt->side <= 0)
+                fail(IMQ_INVALID_ARG, "imq_plan: domain must be finite with side > 0");
+            x0 = opt->x0;
+            y0 = opt->y0;
+            side = opt->side;
+        }
+        dups = opt->check_duplicates != 0;
+    }
+}
+
+imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, double c, int p, int leaf,
+                        const imq_options *opt, cudaStream_t s) {
+    double x0, y0, side;
+    bool dups;
+    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups);
+    check_device();
+    auto *h = new imq_plan_s;
+    try {
+        Plan &P = h->P;
+        IMQ_CUDA(cudaGetDevice(&P.device));
+        P.N = N;
+        P.n_nodes = n_nodes;
+        P.c = c;
+        P.p = p;
+        P.leaf = leaf;
+        P.x0 = x0;
+        P.y0 = y0;
+        P.side = side;
+        P.layout.build(p, 0);
+        build_tree(P, d_points, s, dups);
+        ensure_ops(P, false, s);
+        IMQ_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
 imq_status imq_plan(const double *points, int64_t N, double c, int p, int leaf, const imq_options *opt,
                     void *stream, imq_plan_t *out) {
     if (out) *out = nullptr;
     return guard([&] {
         if (!out || !points) fail(IMQ_INVALID_ARG, "imq_plan: NULL pointer");
-        if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
-        if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
-        if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
-        if (leaf < 1) fail(IMQ_INVALID_ARG, "imq_plan: leaf must be >= 1");
-        bool dups = false;
-        double x0 = 0, y0 = 0, side = -1;
-        if (opt) {
-            if (opt->struct_size < (int)offsetof(imq_options, reserved))
-                fail(IMQ_INVALID_ARG, "imq_plan: imq_options.struct_size too small");
-            if (opt->has_domain) {
-                if (!std::isfinite(opt->x0) || !std::isfinite(opt->y0) || !std::isfinite(opt->side) ||
-                    opt->side <= 0)
-                    fail(IMQ_INVALID_ARG, "imq_plan: domain must be finite with side > 0");
-                x0 = opt->x0;
-                y0 = opt->y0;
-                side = opt->side;
-            }
-            dups = opt->check_duplicates != 0;
-        }
-        check_device();
+        double x0, y0, side;
+        bool dups;
+        parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups);   // argument errors before any GPU work
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        auto *h = new imq_plan_s;
-        try {
-            Plan &P = h->P;
-            IMQ_CUDA(cudaGetDevice(&P.device));
-            P.N = N;
-            P.c = c;
-            P.p = p;
-            P.leaf = leaf;
-            P.x0 = x0;
-            P.y0 = y0;
-            P.side = side;
-            P.layout.build(p);
-            DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
-            build_tree(P, static_cast<const double *>(pts.ptr), s, dups);
-            ensure_ops(P, false, s);
-            IMQ_CUDA(cudaStreamSynchronize(s));
-        } catch (...) {
-            delete h;
-            throw;
-        }
-        *out = h;
+        check_device();
+        DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
+        *out = plan_create(static_cast<const double *>(pts.ptr), N, 0, c, p, leaf, opt, s);
+    });
+}
+
+imq_status imq_plan_eval(const double *nodes, int64_t n_nodes, const double *targets, int64_t n_targets, double c,
+                         int p, int leaf, const imq_options *opt, void *stream, imq_plan_t *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out || !nodes || !targets) fail(IMQ_INVALID_ARG, "imq_plan_eval: NULL pointer");
+        if (n_nodes < 1 || n_targets < 1 || n_nodes + n_targets > 0x7FFFFFFF)
+            fail(IMQ_INVALID_ARG, "imq_plan_eval: need n_nodes >= 1, n_targets >= 1, total < 2^31");
+        if (opt && opt->check_duplicates) fail(IMQ_INVALID_ARG, "imq_plan_eval: targets may coincide with nodes");
+        double x0, y0, side;
+        bool dups;
+        parse_plan_args(n_nodes + n_targets, c, p, leaf, opt, x0, y0, side, dups);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        check_device();
+        const int64_t N = n_nodes + n_targets;
+        DevIn a(nodes, sizeof(double) * 2 * (size_t)n_nodes, s), b(targets, sizeof(double) * 2 * (size_t)n_targets, s);
+        AsyncMem all(sizeof(double) * 2 * (size_t)N, s);
+        IMQ_CUDA(cudaMemcpyAsync(all.ptr, a.ptr, sizeof(double) * 2 * n_nodes, cudaMemcpyDeviceToDevice, s));
+        IMQ_CUDA(cudaMemcpyAsync(all.as<double>() + 2 * n_nodes, b.ptr, sizeof(double) * 2 * n_targets,
+                                 cudaMemcpyDeviceToDevice, s));
+        *out = plan_create(all.as<double>(), N, n_nodes, c, p, leaf, opt, s);
     });
 }
 
@@ -192,7 +241,7 @@ void imq_plan_destroy(imq_plan_t plan) {
 }
 
 static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream,
-                        PhaseTimer *tm) {
+                        PhaseTimer *tm, bool dz = false) {
     if (!plan || !v || !out) fail(IMQ_INVALID_ARG, "imq_matvec: NULL pointer");
     if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_matvec: nrhs must be >= 1");
     if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_matvec: unknown dtype");
@@ -207,8 +256,13 @@ static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq
     if (dt == IMQ_F32) gather_sorted<float, float>(P, static_cast<const float *>(dv.ptr), us.as<float>(), nrhs, s);
     else gather_sorted<double, double>(P, static_cast<const double *>(dv.ptr), us.as<double>(), nrhs, s);
     if (tm) { tm->stop(s); tm->launches += nrhs; }
-    if (dt == IMQ_F32) fmm_apply<float>(P, us.as<float>(), bs.as<float>(), nrhs, s, tm);
-    else fmm_apply<double>(P, us.as<double>(), bs.as<double>(), nrhs, s, tm);
+    if (dz) {
+        if (dt == IMQ_F32) fmm_apply_dz<float>(P, us.as<float>(), bs.as<float>(), nrhs, s);
+        else fmm_apply_dz<double>(P, us.as<double>(), bs.as<double>(), nrhs, s);
+    } else {
+        if (dt == IMQ_F32) fmm_apply<float>(P, us.as<float>(), bs.as<float>(), nrhs, s, tm);
+        else fmm_apply<double>(P, us.as<double>(), bs.as<double>(), nrhs, s, tm);
+    }
     if (tm) tm->start(kPhScatter, s);
     if (dt == IMQ_F32) scatter_sorted<float, float>(P, bs.as<float>(), static_cast<float *>(dout.ptr), nrhs, s);
     else scatter_sorted<double, double>(P, bs.as<double>(), static_cast<double *>(dout.ptr), nrhs, s);
@@ -218,6 +272,51 @@ static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq
 
 imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream) {
     return guard([&] { matvec_impl(plan, v, out, nrhs, dt, stream, nullptr); });
+}
+
+imq_status imq_matvec_dc(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] { matvec_impl(plan, v, out, nrhs, dt, stream, nullptr, true); });
+}
+
+// mode 0: evaluate, 1: transpose, 2: evaluate with dphi/dc
+static void eval_impl(imq_plan_t plan, const void *in, void *out, int nrhs, imq_dtype dt, void *stream, int mode) {
+    if (!plan || !in || !out) fail(IMQ_INVALID_ARG, "imq_evaluate: NULL pointer");
+    if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_evaluate: nrhs must be >= 1");
+    if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_evaluate: unknown dtype");
+    Plan &P = plan->P;
+    if (P.n_nodes <= 0) fail(IMQ_INVALID_ARG, "imq_evaluate: the plan was not made by imq_plan_eval");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = P.N, Nn = P.n_nodes, Nt = N - Nn;
+    const int64_t in_len = mode == 1 ? Nt : Nn, out_len = mode == 1 ? Nn : Nt;
+    const int64_t in_off = mode == 1 ? Nn : 0, out_off = mode == 1 ? 0 : Nn;
+    const size_t es = dt == IMQ_F32 ? 4 : 8;
+    DevIn din(in, es * (size_t)nrhs * in_len, s);
+    DevOut dout(out, es * (size_t)nrhs * out_len, s);
+    AsyncMem fu(es * (size_t)nrhs * N, s), fb(es * (size_t)nrhs * N, s);
+    IMQ_CUDA(cudaMemsetAsync(fu.ptr, 0, es * (size_t)nrhs * N, s));
+    for (int r = 0; r < nrhs; ++r)
+        IMQ_CUDA(cudaMemcpyAsync(static_cast<char *>(fu.ptr) + es * ((size_t)r * N + in_off),
+                                 static_cast<const char *>(din.ptr) + es * (size_t)r * in_len, es * in_len,
+                                 cudaMemcpyDeviceToDevice, s));
+    imq_plan_s *hp = plan;
+    matvec_impl(hp, fu.ptr, fb.ptr, nrhs, dt, s, nullptr, mode == 2);
+    for (int r = 0; r < nrhs; ++r)
+        IMQ_CUDA(cudaMemcpyAsync(static_cast<char *>(dout.ptr) + es * (size_t)r * out_len,
+                                 static_cast<const char *>(fb.ptr) + es * ((size_t)r * N + out_off), es * out_len,
+                                 cudaMemcpyDeviceToDevice, s));
+    dout.finish();
+}
+
+imq_status imq_evaluate(imq_plan_t eplan, const void *coef, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] { eval_impl(eplan, coef, out, nrhs, dt, stream, 0); });
+}
+
+imq_status imq_evaluate_transpose(imq_plan_t eplan, const void *r, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] { eval_impl(eplan, r, out, nrhs, dt, stream, 1); });
+}
+
+imq_status imq_evaluate_dc(imq_plan_t eplan, const void *coef, void *out, int nrhs, imq_dtype dt, void *stream) {
+    return guard([&] { eval_impl(eplan, coef, out, nrhs, dt, stream, 2); });
 }
 
 imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream,
@@ -317,6 +416,7 @@ imq_status imq_plan_get_info(imq_plan_t plan, imq_plan_info *info) {
         const Plan &P = plan->P;
         std::memset(info, 0, sizeof(*info));
         info->n_points = P.N;
+        info->n_nodes = P.n_nodes;
         info->n_boxes = P.nbox;
         info->n_leaves = P.nleaf;
         info->max_level = P.max_level;

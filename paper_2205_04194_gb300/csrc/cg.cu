@@ -479,6 +479,13 @@ void residual_product(Plan &P, Plan *RP, int mode, const double *vs, double *out
 
 }  // namespace
 
+double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s) {
+    DevMem part, tmp;
+    part.alloc(8 * kRedBlocks);
+    tmp.alloc(64);
+    return read_dot(a, b, n, part, tmp, s);
+}
+
 void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o, Plan *RP,
               imq_cg_info *info, cudaStream_t s) {
     const int64_t n = P.N;

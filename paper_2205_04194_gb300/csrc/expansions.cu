@@ -15,48 +15,13 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "fmm_common.cuh"
 #include "imq_internal.h"
 #include "ptx.cuh"
 #include "util.cuh"
 
 namespace imq {
 namespace {
-
-constexpr int kMaxCol = 10;   // (IMQ_MAX_P / 2) + 1 coefficients per m-column
-
-__device__ __forceinline__ int col_base(int m, int p) {
-    // first slot of column m in the m-major parity-even layout
-    int s = 0;
-    for (int mm = 0; mm < m; ++mm) s += ((p - mm) / 2 + 1) * (mm ? 2 : 1);
-    return s;
-}
-
-template <class T>
-__device__ __forceinline__ T box_side(double S, int lev) {
-    return (T)(S / (double)(1 << lev));
-}
-
-// offset of sorted point i from the centre of the box with centre cb,
-// where leafc is the centre of the leaf that holds i.
-template <class T>
-__device__ __forceinline__ void point_offset(int i, const float2 *loc, const double2 *pos, double2 cb, double2 leafc,
-                                             T &x, T &y) {
-    if constexpr (std::is_same<T, float>::value) {
-        const float2 l = loc[i];
-        x = l.x + (float)(leafc.x - cb.x);
-        y = l.y + (float)(leafc.y - cb.y);
-    } else {
-        const double2 q = pos[i];
-        x = q.x - cb.x;
-        y = q.y - cb.y;
-    }
-}
-
-template <class T>
-__device__ __forceinline__ T rsq(T v) {
-    if constexpr (std::is_same<T, float>::value) return rsqrtf(v);
-    else return 1.0 / sqrt(v);
-}
 
 // ------------------------------------------------------------------ gather / scatter
 template <class Tin, class T>
@@ -177,19 +142,19 @@ __global__ void k_l2l(int lb, const int32_t *__restrict__ parent, const uint32_t
 // read through the cache hierarchy.
 template <class T>
 __global__ void k_m2l_direct(int lb, int nl, const int32_t *__restrict__ vtab, const T *__restrict__ M,
-                             T *__restrict__ L, const T *__restrict__ ops, int K, int Kp) {
+                             T *__restrict__ L, const T *__restrict__ ops, int Kin, int Kout) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= (int64_t)nl * K) return;
-    const int b = lb + (int)(g / K), row = (int)(g % K);
+    if (g >= (int64_t)nl * Kout) return;
+    const int b = lb + (int)(g / Kout), row = (int)(g % Kout);
     T acc = 0;
     for (int o = 0; o < kOffsetClasses; ++o) {
         const int s = vtab[(int64_t)kOffsetClasses * b + o];
         if (s < 0) continue;
-        const T *op = ops + (size_t)o * K * Kp + row;
-        const T *Ms = M + (int64_t)s * K;
-        for (int i = 0; i < K; ++i) acc += op[(size_t)i * Kp] * Ms[i];
+        const T *op = ops + (size_t)o * Kin * Kout + row;
+        const T *Ms = M + (int64_t)s * Kin;
+        for (int i = 0; i < Kin; ++i) acc += op[(size_t)i * Kout] * Ms[i];
     }
-    L[(int64_t)b * K + row] = acc;
+    L[(int64_t)b * Kout + row] = acc;
 }
 
 // ------------------------------------------------------------------ irregular-harmonic evaluation
@@ -217,21 +182,9 @@ __device__ __forceinline__ void irregular_column(int m, int p, T a, T t, T gmm_r
     }
 }
 
-// ------------------------------------------------------------------ recurrence tables
-// tab2[n*(p+1)+m] = sqrt((n-1)^2 - m^2), tabi[n*(p+1)+m] = 1/sqrt(n^2 - m^2) (0 where undefined)
-template <class T>
-__device__ __forceinline__ void fill_recurrence_tables(T *tab2, T *tabi, int p) {
-    for (int idx = threadIdx.x; idx < (p + 1) * (p + 1); idx += blockDim.x) {
-        const int n = idx / (p + 1), m = idx - n * (p + 1);
-        const int a = (n - 1) * (n - 1) - m * m, b = n * n - m * m;
-        tab2[idx] = (n >= 1 && a > 0) ? sqrt((T)a) : (T)0;
-        tabi[idx] = b > 0 ? (T)1 / sqrt((T)b) : (T)0;
-    }
-}
-
 // ------------------------------------------------------------------ P2L (X list)
 // Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c; lane l owns column l.
-template <class T>
+template <class T, int PAR>
 __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff,
                       const int32_t *__restrict__ xitems, const int32_t *__restrict__ begin,
                       const int32_t *__restrict__ end, const int32_t *__restrict__ level,
@@ -268,8 +221,10 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
                 gi = gr * zi0 + gi * zr0;
                 gr = nr;
             }
-            ar[0] += gr;
-            ai[0] += gi;
+            if (PAR == 0) {
+                ar[0] += gr;
+                ai[0] += gi;
+            }
             T g2r = 0, g2i = 0, g1r = gr, g1i = gi;
             const T a2 = a * a, ta = t * a;
 #pragma unroll
@@ -282,7 +237,7 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
                     const T nr = (c1 * g1r - c2 * g2r) * iv;
                     const T ni = (c1 * g1i - c2 * g2i) * iv;
                     g2r = g1r; g2i = g1i; g1r = nr; g1i = ni;
-                    if ((st & 1) == 0) {
+                    if ((st & 1) == PAR) {
                         ar[st / 2] += nr;
                         ai[st / 2] += ni;
                     }
@@ -290,11 +245,11 @@ __global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t
             }
         }
     }
-    int slot = col_base(l, p);
+    int slot = col_base(l, p, PAR);
     T *Lb = L + (int64_t)b * K;
 #pragma unroll
     for (int k = 0; k < kMaxCol; ++k) {
-        if (l + 2 * k <= p) {
+        if (l + PAR + 2 * k <= p) {
             Lb[slot] += ar[k];
             if (l > 0) Lb[slot + 1] += ai[k];
             slot += l ? 2 : 1;
@@ -418,7 +373,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
         std::vector<double> tmp;
         for (int li = 0; li < nlev; ++li) {
             const double h = P.side / (double)(1 << (P.m2l_level_lo + li));
-            build_m2l_ops(P.layout, h, P.c, tmp);
+            build_m2l_ops(P.layout, P.layout, h, P.c, tmp);
             std::copy(tmp.begin(), tmp.end(), P.h_m2l.begin() + (size_t)li * kOffsetClasses * K * K);
         }
     }
@@ -448,6 +403,67 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
 
 template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
+
+template <class T>
+void p2l_odd_launch(Plan &P, const T *u, T *Lodd, cudaStream_t s) {
+    if (P.X.total == 0) return;
+    k_p2l<T, 1><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
+        P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(), P.begin.as<int32_t>(),
+        P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(),
+        u, Lodd, P.layout_odd.K, P.p, P.side, (T)P.c);
+    IMQ_LAUNCH_CHECK();
+}
+template void p2l_odd_launch<float>(Plan &, const float *, float *, cudaStream_t);
+template void p2l_odd_launch<double>(Plan &, const double *, double *, cudaStream_t);
+
+template <class T>
+void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaStream_t s, int *launches) {
+    const int K = P.layout.K;
+    k_p2m<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
+        P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
+        P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, P.p, coef, P.side);
+    IMQ_LAUNCH_CHECK();
+    ++*launches;
+    for (int lev = P.max_level - 1; lev >= 2; --lev) {
+        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+        if (nl <= 0) continue;
+        k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
+        IMQ_LAUNCH_CHECK();
+        ++*launches;
+    }
+}
+template void upward_launch<float>(Plan &, const float *, float *, const float *, const float *, cudaStream_t, int *);
+template void upward_launch<double>(Plan &, const double *, double *, const double *, const double *, cudaStream_t, int *);
+
+template <class T>
+void l2l_launch(Plan &P, T *L, const T *op, int K, cudaStream_t s, int *launches) {
+    for (int lev = 3; lev <= P.max_level; ++lev) {
+        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+        if (nl <= 0) continue;
+        k_l2l<T><<<nl, 128, sizeof(T) * K, s>>>(lb, P.parent.as<int32_t>(), P.prefix.as<uint32_t>(), L, op, K);
+        IMQ_LAUNCH_CHECK();
+        ++*launches;
+    }
+}
+template void l2l_launch<float>(Plan &, float *, const float *, int, cudaStream_t, int *);
+template void l2l_launch<double>(Plan &, double *, const double *, int, cudaStream_t, int *);
+
+template <class T>
+void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kout, cudaStream_t s, int *launches);
+
+template <class T>
+void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kout, cudaStream_t s, int *launches) {
+    for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
+        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
+        const T *opl = ops + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * Kin * Kout;
+        k_m2l_direct<T><<<blocks_for((int64_t)nl * Kout, 128), 128, 0, s>>>(lb, nl, P.vtab.as<int32_t>(), M, L, opl,
+                                                                             Kin, Kout);
+        IMQ_LAUNCH_CHECK();
+        ++*launches;
+    }
+}
+template void m2l_direct_launch<float>(Plan &, const float *, float *, const float *, int, int, cudaStream_t, int *);
+template void m2l_direct_launch<double>(Plan &, const double *, double *, const double *, int, int, cudaStream_t, int *);
 
 template <class T>
 int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer *tm) {
@@ -490,19 +506,12 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
                 ++launches;
             }
         } else {
-            for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
-                const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-                const T *ops = m2l + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * K * K;
-                k_m2l_direct<T><<<blocks_for((int64_t)nl * K, 128), 128, 0, s>>>(lb, nl, P.vtab.as<int32_t>(), M, L,
-                                                                                  ops, K, K);
-                IMQ_LAUNCH_CHECK();
-                ++launches;
-            }
+            m2l_direct_launch<T>(P, M, L, m2l, K, K, s, &launches);
         }
         t1();
         t0(kPhP2L);
         if (P.X.total > 0) {
-            k_p2l<T><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
+            k_p2l<T, 0><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
                 P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(),
                 P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
                 P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, p, P.side, (T)P.c);

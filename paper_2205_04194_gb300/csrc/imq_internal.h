@@ -72,11 +72,12 @@ struct AsyncMem {
 // ---------------------------------------------------------------- layout
 struct Layout {
     int p = 0;
+    int parity = 0;                // 0: slots with n+m even, 1: n+m odd
     int K = 0;                     // reals per expansion
     std::vector<int> slot_n, slot_m, slot_part;   // per real slot
     std::vector<int> re_slot;      // [(p+1)*(p+1)] index n*(p+1)+m -> slot of Re part or -1
     std::vector<int> im_slot;      // same for Im part (-1 for m = 0 or odd n+m)
-    void build(int p_);
+    void build(int p_, int parity_ = 0);
 };
 
 constexpr int kOffsetClasses = 40;          // V-list offsets in [-3,3]^2 minus [-1,1]^2
@@ -87,8 +88,10 @@ void offset_of_class(int k, int *dx, int *dy);
 // Real K x K matrices stored input-major: op[i * K + o] multiplies input slot i into output o.
 void build_m2m_ops(const Layout &L, std::vector<double> &out);          // [4][K][K], quadrant q = 2*ybit + xbit
 void build_l2l_ops(const Layout &L, std::vector<double> &out);          // [4][K][K]
-void build_m2l_ops(const Layout &L, double h, double c, std::vector<double> &out);  // [40][K][K] for side h
+// [40][K_in][K_out] for side h; Lo the output (local) layout, L the input (multipole) layout
+void build_m2l_ops(const Layout &Lo, const Layout &L, double h, double c, std::vector<double> &out);
 void p2m_coefficients(const Layout &L, std::vector<double> &coef);      // per slot: Ptilde_n^m(0)
+void l2p_dz_coefficients(const Layout &Lo, std::vector<double> &coef);  // odd slots: d/dz of L2P
 
 // ---------------------------------------------------------------- plan
 struct ListCSR {
@@ -100,6 +103,9 @@ struct TypedOps {        // operator set in one precision
     DevMem m2m, l2l, m2l, p2mc;
     DevMem M, L;         // expansion workspace (nbox x K), owned by the plan
     bool ready = false;
+    // derivative in c (odd-parity locals): M2L even->odd, L2L odd, d/dz L2P coefficients
+    DevMem m2l_odd, l2l_odd, dzc, Lodd;
+    bool dz_ready = false;
 };
 
 // Additive Schwarz preconditioner over leaf neighbourhood patches (cg.cu).
@@ -126,7 +132,9 @@ struct Plan {
     int p = 0, leaf = 0;
     int nbox = 0, nleaf = 0, max_level = 0;
     int m2l_level_lo = 2, m2l_level_hi = 1;   // levels holding V pairs
-    Layout layout;
+    Layout layout;       // multipoles and value locals (n+m even)
+    Layout layout_odd;   // locals of the c-derivative (n+m odd)
+    int64_t n_nodes = 0; // evaluation plans: the first n_nodes points are nodes, the rest targets
     std::vector<int> level_start;              // boxes of level l: [level_start[l], level_start[l+1])
     // tree, device
     DevMem codes;      // uint32[N] sorted
@@ -150,6 +158,7 @@ struct Plan {
     DevMem leaf_of;    // int32[N]
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
+    std::vector<double> h_m2l_odd, h_l2l_odd, h_dzc;   // derivative path ([lev][40][K][Ko], [4][Ko][Ko])
     TypedOps ops32, ops64;
     Schwarz schwarz;
     // statistics
@@ -182,9 +191,24 @@ void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_
 // cg.cu
 void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o, Plan *RP,
               imq_cg_info *info, cudaStream_t s);
+double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s);   // deterministic, synchronises
 // m2l.cu
 int m2l_tiled_rows(int K);
-void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s);
+void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s, int Kout = 0);
+// expansions.cu building blocks reused by the derivative path
+template <class T>
+void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaStream_t s, int *launches);
+template <class T>
+void l2l_launch(Plan &P, T *L, const T *op, int K, cudaStream_t s, int *launches);
+template <class T>
+void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kout, cudaStream_t s, int *launches);
+template <class T>
+void p2l_odd_launch(Plan &P, const T *u, T *Lodd, cudaStream_t s);
+template <class T>
+void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
+// dz.cu: b = (dA/dc) u in Morton order
+template <class T>
+int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
 void build_m2l_tiles(Plan &P, cudaStream_t s);
 // dense.cu
 void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,

@@ -27,11 +27,12 @@ template <int RR>
 __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__ tiles,
                                                         const int32_t *__restrict__ vtab,
                                                         const float *__restrict__ M, float *__restrict__ L,
-                                                        const float *__restrict__ ops, int K, int Kpad) {
+                                                        const float *__restrict__ ops, int K, int Kout, int Kpad) {
+    // K: input (multipole) reals; Kout: output (local) reals, Kout <= 16*RR
     constexpr int Kp = 16 * RR;
     extern __shared__ __align__(16) unsigned char smraw[];
     float *Top = reinterpret_cast<float *>(smraw);        // [K][Kp]
-    float *Ms = Top + (size_t)K * Kp;                     // [kTB][Kpad]
+    float *Ms = Top + (size_t)K * Kp;                     // [kTB][Kpad]  (Top: [K][Kp])
     __shared__ int srcs[kTB];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -92,11 +93,11 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__
     for (int c = 0; c < 8; ++c) {
         const int col = tx + 16 * c;
         if (col >= nbt) continue;
-        float *Lb = L + (int64_t)(b0 + col) * K;
+        float *Lb = L + (int64_t)(b0 + col) * Kout;
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const int row = ty * RR + r;
-            if (row < K) Lb[row] = acc[r][c];
+            if (row < Kout) Lb[row] = acc[r][c];
         }
     }
 }
@@ -111,9 +112,10 @@ int m2l_tiled_rows(int K) {
     return -1;
 }
 
-void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s) {
+void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s, int Kout) {
     const int K = P.layout.K;
-    const int RR = m2l_tiled_rows(K);
+    if (Kout <= 0) Kout = K;
+    const int RR = m2l_tiled_rows(Kout);
     const int Kp = 16 * RR;
     const int Kpad = K | 1;
     const size_t smem = sizeof(float) * ((size_t)K * Kp + (size_t)kTB * Kpad);
@@ -123,7 +125,7 @@ void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops,
         auto kern = k_m2l_tiled<R>;                                                                       \
         IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
         kern<<<P.n_m2l_tiles, kThreads, smem, s>>>(P.m2l_tiles.as<int4>(), P.vtab.as<int32_t>(), M, L,    \
-                                                   ops, K, Kpad);                                         \
+                                                   ops, K, Kout, Kpad);                                   \
         break;                                                                                            \
     }
     switch (RR) {

@@ -25,13 +25,14 @@ namespace imq {
 
 using cd = std::complex<double>;
 
-void Layout::build(int p_) {
+void Layout::build(int p_, int parity_) {
     p = p_;
+    parity = parity_;
     slot_n.clear(); slot_m.clear(); slot_part.clear();
     re_slot.assign((p + 1) * (p + 1), -1);
     im_slot.assign((p + 1) * (p + 1), -1);
     for (int m = 0; m <= p; ++m) {
-        for (int n = m; n <= p; n += 2) {
+        for (int n = m + parity; n <= p; n += 2) {
             re_slot[n * (p + 1) + m] = (int)slot_n.size();
             slot_n.push_back(n); slot_m.push_back(m); slot_part.push_back(0);
             if (m > 0) {
@@ -102,19 +103,19 @@ Harm harmonics(int nmax, double x, double y, double z, bool irregular) {
 // Fold a complex coefficient function C(out_n, out_m, in_n, in_m) (signed m) into
 // the real input-major K x K matrix op[in * K + out] on the parity-even layout.
 template <class F>
-void fold(const Layout &L, F coef, double *op) {
-    const int K = L.K, p = L.p;
-    for (int i = 0; i < K * K; ++i) op[i] = 0.0;
+void fold(const Layout &Lo, const Layout &Li, F coef, double *op) {
+    const int K = Lo.K, p = Lo.p;
+    for (int i = 0; i < Li.K * K; ++i) op[i] = 0.0;
     for (int k = 0; k <= p; ++k) {
         for (int l = 0; l <= k; ++l) {
-            const int oRe = L.re_slot[k * (p + 1) + l];
+            const int oRe = Lo.re_slot[k * (p + 1) + l];
             if (oRe < 0) continue;
-            const int oIm = L.im_slot[k * (p + 1) + l];
+            const int oIm = Lo.im_slot[k * (p + 1) + l];
             for (int n = 0; n <= p; ++n) {
                 for (int m = 0; m <= n; ++m) {
-                    const int iRe = L.re_slot[n * (p + 1) + m];
+                    const int iRe = Li.re_slot[n * (p + 1) + m];
                     if (iRe < 0) continue;
-                    const int iIm = L.im_slot[n * (p + 1) + m];
+                    const int iIm = Li.im_slot[n * (p + 1) + m];
                     const cd T1 = coef(k, l, n, m);
                     if (m == 0) {
                         op[iRe * K + oRe] += T1.real();
@@ -150,6 +151,17 @@ void p2m_coefficients(const Layout &L, std::vector<double> &coef) {
     for (int s = 0; s < L.K; ++s) coef[s] = P0[L.slot_n[s] * (L.p + 1) + L.slot_m[s]];
 }
 
+void l2p_dz_coefficients(const Layout &Lo, std::vector<double> &coef) {
+    // d/dz of conj(U_k^l(X - C)) is conj(U_{k-1}^l): in scaled form each odd slot (k, l)
+    // contributes Lh_k^l sqrt((k+l)(k-l)) Ptilde_{k-1}^l(0) conj(w)^l |w|^{k-1-l} / h
+    const auto P0 = legendre_normalised(Lo.p, 0.0);
+    coef.resize(Lo.K);
+    for (int s = 0; s < Lo.K; ++s) {
+        const int k = Lo.slot_n[s], l = Lo.slot_m[s];
+        coef[s] = std::sqrt((double)(k + l) * (double)(k - l)) * P0[(k - 1) * (Lo.p + 1) + l];
+    }
+}
+
 void build_m2m_ops(const Layout &L, std::vector<double> &out) {
     // Parent side 1, child side 1/2.  Mh(P)_n^m = sum (s_nm / s_kl) 2^{-k} conj(U_{n-k}^{m-l}(t)) Mh(Q)_k^l
     const int K = L.K, p = L.p;
@@ -164,7 +176,7 @@ void build_m2m_ops(const Layout &L, std::vector<double> &out) {
             const double sc = std::exp(log_s(n, m) - log_s(k, l) - log_s(j, i)) * std::pow(0.5, k);
             return sc * std::conj(R.at(j, i));
         };
-        fold(L, coef, out.data() + (size_t)q * K * K);
+        fold(L, L, coef, out.data() + (size_t)q * K * K);
     }
 }
 
@@ -182,15 +194,15 @@ void build_l2l_ops(const Layout &L, std::vector<double> &out) {
             const double sc = std::exp(log_s(k, l) - log_s(j, i) - log_s(dn, dm)) * std::pow(0.5, j);
             return sc * std::conj(R.at(dn, dm));
         };
-        fold(L, coef, out.data() + (size_t)q * K * K);
+        fold(L, L, coef, out.data() + (size_t)q * K * K);
     }
 }
 
-void build_m2l_ops(const Layout &L, double h, double c, std::vector<double> &out) {
+void build_m2l_ops(const Layout &Lo, const Layout &L, double h, double c, std::vector<double> &out) {
     // Lh_k^l = (-1)^k h^{k+n} s_{n+k,m+l} / (s_kl s_nm) [T_{n+k}^{m+l}(d) / s_{n+k,m+l}] Mh_n^m
     // d = C_B - Z_S = (-dx h, -dy h, c) for a source at box offset (dx, dy).
-    const int K = L.K, p = L.p;
-    out.assign((size_t)kOffsetClasses * K * K, 0.0);
+    const int K = L.K, Ko = Lo.K, p = L.p;
+    out.assign((size_t)kOffsetClasses * K * Ko, 0.0);
     for (int k = 0; k < kOffsetClasses; ++k) {
         int dx, dy;
         offset_of_class(k, &dx, &dy);
@@ -202,7 +214,7 @@ void build_m2l_ops(const Layout &L, double h, double c, std::vector<double> &out
             const double sc = std::exp(log_s(j, i) - log_s(kk, l) - log_s(n, m)) * std::pow(h / r, j) / r;
             return ((kk & 1) ? -1.0 : 1.0) * sc * I.at(j, i);
         };
-        fold(L, coef, out.data() + (size_t)k * K * K);
+        fold(Lo, L, coef, out.data() + (size_t)k * K * Ko);
     }
 }
 

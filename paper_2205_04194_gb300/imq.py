@@ -136,6 +136,18 @@ class Plan:
             raise ImqError(st, "imq_cg_solve", msg)
         return coef, out
 
+    def matvec_dc(self, v, out=None, stream=None):
+        """imq_matvec_dc: b = (dA/dc) v, dA_ij/dc = -c (r^2 + c^2)^{-3/2}."""
+        code = _dtype_code(v)
+        tdt = torch.float32 if code == F32 else torch.float64
+        nrhs = 1 if len(np.shape(v)) == 1 else int(np.shape(v)[0])
+        if out is None:
+            out = _like(v, self.n * nrhs, code)
+        vp, kv = _buf(v, tdt)
+        op, ko = _buf(out, tdt)
+        call("imq_matvec_dc", self._h, vp, op, nrhs, code, _stream(stream))
+        return out
+
     PHASES = ("gather", "p2m", "m2m", "m2l", "p2l", "l2l", "l2p_m2p", "p2p", "scatter")
 
     def matvec_timed(self, v, out=None, stream=None):
@@ -180,6 +192,51 @@ class Plan:
         return off, items[:int(off[-1])]
 
 
+class EvalPlan(Plan):
+    """imq_plan_eval: one tree over nodes and evaluation targets (interpolant of Eq. (2))."""
+
+    def __init__(self, nodes, targets, c: float, p: int, leaf: int, domain=None, stream=None):
+        self._h = ctypes.c_void_p(0)
+        np_, kn = _buf(nodes, torch.float64)
+        tp_, kt = _buf(targets, torch.float64)
+        nn, nt = int(np.shape(nodes)[0]), int(np.shape(targets)[0])
+        opt = ImqOptions()
+        opt.struct_size = ctypes.sizeof(ImqOptions)
+        if domain is not None:
+            opt.has_domain = 1
+            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+        call("imq_plan_eval", np_, nn, tp_, nt, float(c), int(p), int(leaf), ctypes.byref(opt),
+             _stream(stream), ctypes.byref(self._h))
+        self.n = nn + nt
+        self.n_nodes, self.n_targets = nn, nt
+        self.c, self.p, self.leaf = float(c), int(p), int(leaf)
+
+    def _eval(self, name, x, n_in, n_out, out, stream):
+        code = _dtype_code(x)
+        tdt = torch.float32 if code == F32 else torch.float64
+        nrhs = 1 if len(np.shape(x)) == 1 else int(np.shape(x)[0])
+        if out is None:
+            shape = (n_out,) if nrhs == 1 else (nrhs, n_out)
+            out = (torch.empty(shape, dtype=tdt, device=x.device) if isinstance(x, torch.Tensor)
+                   else np.empty(shape, dtype=np.float32 if code == F32 else np.float64))
+        xp, kx = _buf(x, tdt)
+        op, ko = _buf(out, tdt)
+        call(name, self._h, xp, op, nrhs, code, _stream(stream))
+        return out
+
+    def evaluate(self, coef, out=None, stream=None):
+        """P(t_k) = sum_j coef_j phi(|t_k - x_j|)."""
+        return self._eval("imq_evaluate", coef, self.n_nodes, self.n_targets, out, stream)
+
+    def evaluate_transpose(self, v, out=None, stream=None):
+        """(E^T v)_j = sum_k phi(|t_k - x_j|) v_k."""
+        return self._eval("imq_evaluate_transpose", v, self.n_targets, self.n_nodes, out, stream)
+
+    def evaluate_dc(self, coef, out=None, stream=None):
+        """sum_j coef_j d phi(|t_k - x_j|)/dc."""
+        return self._eval("imq_evaluate_dc", coef, self.n_nodes, self.n_targets, out, stream)
+
+
 def dense_matvec(points, c: float, v, out=None, stream=None):
     """imq_dense_matvec: b = A v over all N^2 pairs (the plain product)."""
     code = _dtype_code(v)
@@ -215,4 +272,4 @@ def version() -> str:
     return _lib.load().imq_version().decode()
 
 
-__all__ = ["Plan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
+__all__ = ["Plan", "EvalPlan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
