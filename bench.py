@@ -143,6 +143,84 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_solves(args, imq, wl, d_pts, plan, dev):
+    """CG solves (metric config and the 100k config), the paper's Table 1 workload and the
+    200k gradient config.  Each is bounded so the default run stays within minutes."""
+    import torch
+    from paper_2205_04194_gb300 import workloads as W
+    out = {}
+    # CG at the metric configuration: f = Franke, 1e-6, capped iterations
+    f = torch.from_numpy(wl.f).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    coef, info = plan.solve(f, rtol=1e-6, maxit=args.cg_maxit, precond="schwarz", schwarz_nmax=128,
+                            schwarz_shift=1e-5)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out["cg"] = {"workload": wl.name, "rtol": 1e-6, "maxit": args.cg_maxit, "precond": "schwarz(128, shift 1e-5/c)",
+                 "operator": "fast_f32", "status": info["status"], "iterations": info["iterations"],
+                 "solve_s": info["seconds"], "wall_s_incl_setup": wall,
+                 "s_per_iter": info["seconds"] / max(1, info["iterations"]),
+                 "true_rel_residual": info["max_rel_residual"], "residual_product": "fast FP64, same tree"}
+    # 100k uniform, c = 2 x mean NN spacing, FP32 inner / FP64 refinement to 1e-8
+    u = W.uniform_100k()
+    pl = imq.Plan(torch.from_numpy(u.points).to(dev), u.c, u.p, u.leaf, domain=u.domain)
+    coef, info = pl.solve(torch.from_numpy(u.f).to(dev), rtol=1e-8, maxit=3000, precond="schwarz",
+                          refine_steps=8, inner_rtol=1e-5, residual="dense")
+    out["cg_uniform_100k"] = {"n": u.n, "c": u.c, "p": u.p, "leaf": u.leaf, "rtol": 1e-8,
+                              "status": info["status"], "iterations": info["iterations"],
+                              "outer_steps": info["outer_steps"], "solve_s": info["seconds"],
+                              "true_rel_residual": info["max_rel_residual"], "residual_product": "dense FP64"}
+    pl.close()
+    # the paper's Table 1 workload: Halton points, c = 1, p = 10, random vector in [-1, 1]
+    rows = []
+    for n in (20000, 40000, 60000, 80000, 100000):
+        t = W.table1_halton(n)
+        dp = torch.from_numpy(t.points).to(dev)
+        dv = torch.from_numpy(t.v).to(dev)
+        pt = imq.Plan(dp, t.c, 10, 64, domain=t.domain)
+        ref = imq.dense_matvec(dp, t.c, dv)                        # FP64 dense on the GPU
+        b64 = pt.matvec(dv)
+        for _ in range(2):
+            pt.matvec(dv.float())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b32 = pt.matvec(dv.float())
+        e1.record()
+        torch.cuda.synchronize()
+        fast_ms = e0.elapsed_time(e1)
+        e0.record()
+        imq.dense_matvec(dp, t.c, dv.float())
+        e1.record()
+        torch.cuda.synchronize()
+        dense_ms = e0.elapsed_time(e1)
+        rinf = lambda a: float((a.double() - ref).abs().max() / ref.abs().max())
+        rows.append({"n": n, "fast_f32_ms": fast_ms, "dense_f32_ms": dense_ms, "einf_fast_f32": rinf(b32),
+                     "einf_fast_f64": rinf(b64)})
+        pt.close()
+    out["table1"] = {"c": 1.0, "p": 10, "leaf": 64, "rows": rows,
+                     "note": "paper Table 1 (Xeon E5-2620 v3, FP64): dense 1.62..128 s, translation 1.58..23.3 s, "
+                             "E 2.67e-9..1.06e-8"}
+    # gradient of the validation loss at N = 200k, 20k validation points, c = 0.05
+    from paper_2205_04194_gb300 import autograd as AG
+    g = W.grad_200k()
+    ct = torch.tensor(g["c"], dtype=torch.float64, requires_grad=True)
+    ft = torch.from_numpy(g["f"]).to(dev).requires_grad_(True)
+    cg = dict(rtol=1e-6, maxit=args.grad_maxit, precond="schwarz", schwarz_nmax=128, schwarz_shift=1e-5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = AG.InterpLoss.apply(ct, ft, torch.from_numpy(g["train"]).to(dev), torch.from_numpy(g["val"]).to(dev),
+                            torch.from_numpy(g["y_val"]).to(dev), 12, 64, (0.0, 0.0, 1.0), torch.float32, cg)
+    L.backward()
+    torch.cuda.synchronize()
+    out["grad"] = {"n_train": 200000, "n_val": 20000, "c": g["c"], "p": 12, "loss": float(L.item()),
+                   "dloss_dc": float(ct.grad.item()), "dloss_df_norm": float(ft.grad.norm().item()),
+                   "wall_s": time.perf_counter() - t0, "cg_maxit_per_solve": args.grad_maxit,
+                   "note": "forward + adjoint; solves capped (c/h ~ 45 is ill-conditioned)"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -155,6 +233,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=96)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip CG, Table 1 and gradient sections")
+    ap.add_argument("--cg-maxit", type=int, default=200)
+    ap.add_argument("--grad-maxit", type=int, default=100)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -266,6 +347,10 @@ def main():
         dist.destroy_process_group()
         return
 
+    extras = {}
+    if not args.no_solve:
+        extras = run_solves(args, imq, wl, d_pts, plan, dev)
+
     # accuracy on sampled rows against the FP64 oracle, and the CPU baseline
     b_fast = d_out.double().cpu().numpy()
     b_dense = d_dense.double().cpu().numpy()
@@ -320,7 +405,10 @@ def main():
         "errors": err,
         "tree": {k: info[k] for k in ("n_boxes", "n_leaves", "max_level", "k_real", "n_u", "n_v", "n_w",
                                       "n_x", "p2p_pairs", "m2l_pairs")},
-        "cg": None,
+        "cg": extras.get("cg"),
+        "cg_uniform_100k": extras.get("cg_uniform_100k"),
+        "table1_halton": extras.get("table1"),
+        "grad_200k": extras.get("grad"),
     }
     print(json.dumps(line), flush=True)
     plan.close()

@@ -240,7 +240,8 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
  *   dloss_df, coef_out: double[N] (host or device) or NULL.  dt selects the
  *   precision of the evaluation and derivative products; opt configures both
  *   solves.  info (may be NULL) sums both solves.  Errors: those of
- *   imq_cg_solve and imq_evaluate, IMQ_INVALID_ARG for mismatched plans.
+ *   imq_cg_solve and imq_evaluate, IMQ_INVALID_ARG for mismatched plans.  On
+ *   IMQ_NOT_CONVERGED every output is still written, from the best iterates.
  * ------------------------------------------------------------------------- */
 imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, const double *f, const double *y,
                                 const imq_cg_options *opt, imq_dtype dt, double *loss,

@@ -15,17 +15,19 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CgInfo, CgOptions, call
+from ._lib import CgInfo, CgOptions
 from .imq import F32, F64, EvalPlan, Plan, _buf, _stream
 
 
 def cg_options(rtol=1e-10, maxit=2000, precond="schwarz", schwarz_nmax=128, schwarz_fp64=False,
-               refine_steps=0, inner_rtol=1e-4, residual="plan", operator="fast_f32") -> CgOptions:
+               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan",
+               operator="fast_f32") -> CgOptions:
     o = CgOptions()
     _lib.load().imq_cg_default_options(ctypes.byref(o))
     o.rtol, o.maxit = float(rtol), int(maxit)
     o.precond = {"none": 0, "schwarz": 1}[precond]
     o.schwarz_nmax, o.schwarz_fp64 = int(schwarz_nmax), 1 if schwarz_fp64 else 0
+    o.schwarz_shift = float(schwarz_shift)
     o.refine_steps, o.inner_rtol = int(refine_steps), float(inner_rtol)
     o.residual = {"plan": 0, "dense": 1}[residual]
     o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[operator]
@@ -44,10 +46,13 @@ def interp_loss_grad(train: Plan, evalp: EvalPlan, f, y, dtype=torch.float64, **
     info = CgInfo()
     opt = cg_options(**cg)
     code = F64 if dtype == torch.float64 else F32
-    call("imq_interp_loss_grad", train._h, evalp._h, fp, yp, ctypes.byref(opt), code, ctypes.byref(loss),
-         ctypes.byref(dc), ctypes.c_void_p(df.data_ptr()), ctypes.c_void_p(coef.data_ptr()),
-         ctypes.byref(info), _stream(None))
-    return loss.value, dc.value, df, coef, {"iterations": info.iterations,
+    lib = _lib.load()
+    st = lib.imq_interp_loss_grad(train._h, evalp._h, fp, yp, ctypes.byref(opt), code, ctypes.byref(loss),
+                                  ctypes.byref(dc), ctypes.c_void_p(df.data_ptr()), ctypes.c_void_p(coef.data_ptr()),
+                                  ctypes.byref(info), _stream(None))
+    if st not in (0, 5, 6):   # IMQ_NOT_CONVERGED / IMQ_NUMERICAL keep the best iterates
+        raise _lib.ImqError(st, "imq_interp_loss_grad", lib.imq_last_error().decode())
+    return loss.value, dc.value, df, coef, {"iterations": info.iterations, "status": _lib.status_name(st),
                                              "max_rel_residual": info.max_rel_residual}
 
 

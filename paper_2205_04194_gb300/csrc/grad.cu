@@ -59,6 +59,12 @@ static void ok_or_throw(imq_status st) {
     if (st != IMQ_OK) fail(st, imq_last_error());
 }
 
+// a solve that stops at the iteration cap still leaves its best iterate: carry on, report at the end
+static void solve_or_flag(imq_status st, bool &not_converged) {
+    if (st == IMQ_NOT_CONVERGED || st == IMQ_NUMERICAL) not_converged = true;
+    else ok_or_throw(st);
+}
+
 extern "C" imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, const double *f, const double *y,
                                            const imq_cg_options *opt, imq_dtype dt, double *loss,
                                            double *dloss_dc, double *dloss_df, double *coef_out,
@@ -78,7 +84,8 @@ extern "C" imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, co
         IMQ_CUDA(cudaMemcpyAsync(dy.ptr, y, 8 * nv, cudaMemcpyDefault, s));
         imq_cg_info i1{}, i2{};
         // forward: coef = A^{-1} f, P = E coef
-        ok_or_throw(imq_cg_solve(train, df.as<double>(), coef.as<double>(), 1, opt, &i1, s));
+        bool unconverged = false;
+        solve_or_flag(imq_cg_solve(train, df.as<double>(), coef.as<double>(), 1, opt, &i1, s), unconverged);
         // products in the requested precision (FP32 products take FP32 vectors)
         auto product = [&](auto fn, imq_plan_t pl, const double *in, int64_t nin, double *out, int64_t nout) {
             if (dt == IMQ_F64) {
@@ -102,7 +109,7 @@ extern "C" imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, co
         *loss = device_dot(diff.as<double>(), diff.as<double>(), nv, s) / (double)nv;
         // adjoint: lambda = A^{-1} E^T g
         product(imq_evaluate_transpose, eval, g.as<double>(), nv, etg.as<double>(), n);
-        ok_or_throw(imq_cg_solve(train, etg.as<double>(), lam.as<double>(), 1, opt, &i2, s));
+        solve_or_flag(imq_cg_solve(train, etg.as<double>(), lam.as<double>(), 1, opt, &i2, s), unconverged);
         // dL/dc = g . (dE/dc coef) - lambda . (dA/dc coef)
         product(imq_evaluate_dc, eval, coef.as<double>(), n, dec.as<double>(), nv);
         product(imq_matvec_dc, train, coef.as<double>(), n, dac.as<double>(), n);
@@ -117,5 +124,7 @@ extern "C" imq_status imq_interp_loss_grad(imq_plan_t train, imq_plan_t eval, co
             info->max_rel_residual = std::max(i1.max_rel_residual, i2.max_rel_residual);
             info->seconds = i1.seconds + i2.seconds;
         }
+        if (unconverged)
+            fail(IMQ_NOT_CONVERGED, "imq_interp_loss_grad: a CG solve stopped at its cap; outputs use its best iterate");
     });
 }

@@ -132,7 +132,8 @@ class Plan:
         out = {"status": _lib.status_name(st), "iterations": info.iterations, "outer_steps": info.outer_steps,
                "max_rel_residual": info.max_rel_residual, "seconds": info.seconds,
                "rel_residual": list(info.rel_residual)[:min(nrhs, 16)], "message": msg}
-        if st != 0 and (raise_on_failure or st not in (5,)):
+        # IMQ_NOT_CONVERGED (5) and IMQ_NUMERICAL (6) still return the best iterate and its info
+        if st != 0 and (raise_on_failure or st not in (5, 6)):
             raise ImqError(st, "imq_cg_solve", msg)
         return coef, out
 
