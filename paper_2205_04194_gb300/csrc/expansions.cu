@@ -183,78 +183,101 @@ __device__ __forceinline__ void irregular_column(int m, int p, T a, T t, T gmm_r
 }
 
 // ------------------------------------------------------------------ P2L (X list)
-// Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c; lane l owns column l.
+// Lh_k^l(B) += sum_j u_j G_k^l(Y_j - C_B), vertical component -c, for the k+l
+// parity PAR.  One warp per box; the sources of all X entries form one
+// concatenated range and lane q takes positions q, q+32, ...; each lane
+// accumulates its own row of K coefficients in shared memory (row stride
+// Kpad odd: conflict-free), and the 32 rows are summed per coefficient at the
+// end.
+constexpr int kP2LWarps = 2;
+
 template <class T, int PAR>
-__global__ void k_p2l(int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff,
-                      const int32_t *__restrict__ xitems, const int32_t *__restrict__ begin,
-                      const int32_t *__restrict__ end, const int32_t *__restrict__ level,
-                      const double2 *__restrict__ centre, const float2 *__restrict__ loc,
-                      const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p,
-                      double S, T c) {
-    __shared__ T tab2[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)], tabi[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)];
+__global__ void __launch_bounds__(32 * kP2LWarps) k_p2l(
+    int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff, const int32_t *__restrict__ xitems,
+    const int32_t *__restrict__ xcum, const int32_t *__restrict__ xtot, const int32_t *__restrict__ begin,
+    const int32_t *__restrict__ level, const double2 *__restrict__ centre, const float2 *__restrict__ loc,
+    const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p, double S, T c) {
+    extern __shared__ __align__(16) unsigned char smraw_p2l[];
+    T *tab2 = reinterpret_cast<T *>(smraw_p2l);
+    T *tabi = tab2 + (IMQ_MAX_P + 1) * (IMQ_MAX_P + 1);
+    T *fmm_ = tabi + (IMQ_MAX_P + 1) * (IMQ_MAX_P + 1);       // sqrt((2m-1)/(2m)), m = 1..p
+    T *accb = fmm_ + (IMQ_MAX_P + 2);
     fill_recurrence_tables<T>(tab2, tabi, p);
+    for (int m = threadIdx.x; m <= p; m += blockDim.x) fmm_[m] = m ? sqrt((T)(2 * m - 1) / (T)(2 * m)) : (T)1;
+    const int Kpad = K | 1;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *acc = accb + (size_t)w * 32 * Kpad;
+    for (int e = lane; e < 32 * Kpad; e += 32) acc[e] = 0;
     __syncthreads();
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= nxb || lane > p) return;
-    const int b = xboxes[warp];
-    const int l = lane;
+    const int widx = blockIdx.x * kP2LWarps + w;
+    if (widx >= nxb) return;
+    const int b = xboxes[widx];
     const T h = box_side<T>(S, level[b]);
     const double2 cb = centre[b];
-    T ar[kMaxCol], ai[kMaxCol];
-#pragma unroll
-    for (int k = 0; k < kMaxCol; ++k) ar[k] = ai[k] = 0;
-    T dmm = 1;
-    for (int i = 1; i <= l; ++i) dmm *= sqrt((T)(2 * i - 1) / (T)(2 * i));
-    for (int e = xoff[b]; e < xoff[b + 1]; ++e) {
-        const int s = xitems[e];
-        const double2 cs = centre[s];
-        for (int j = begin[s]; j < end[s]; ++j) {
-            T vx, vy;
-            point_offset<T>(j, loc, pos, cb, cs, vx, vy);
-            const T inv = rsq<T>(vx * vx + vy * vy + c * c);
-            const T a = h * inv, t = -c * inv;
-            const T zr0 = vx * inv * a, zi0 = vy * inv * a;
-            T gr = dmm * inv * u[j], gi = 0;
-            for (int q = 0; q < l; ++q) {   // times (zeta a)^l
-                const T nr = gr * zr0 - gi * zi0;
-                gi = gr * zi0 + gi * zr0;
+    const int x0 = xoff[b], x1 = xoff[b + 1], St = xtot[b];
+    T *row = acc + lane * Kpad;
+    int r = x0;
+    for (int q = lane; q < St; q += 32) {
+        while (r + 1 < x1 && xcum[r + 1] <= q) ++r;
+        const int sb = xitems[r];
+        const int j = begin[sb] + (q - xcum[r]);
+        T vx, vy;
+        point_offset<T>(j, loc, pos, cb, centre[sb], vx, vy);
+        const T inv = rsq<T>(vx * vx + vy * vy + c * c);
+        const T a = h * inv, t = -c * inv;
+        const T zr0 = vx * inv * a, zi0 = vy * inv * a;
+        const T ta = t * a, a2 = a * a;
+        T gr = inv * u[j], gi = 0;   // G_0^0 times u_j
+        int slot = 0;
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) {
+                const T f = fmm_[m];
+                const T nr = (gr * zr0 - gi * zi0) * f;
+                gi = (gr * zi0 + gi * zr0) * f;
                 gr = nr;
             }
+            const int step = m ? 2 : 1;
             if (PAR == 0) {
-                ar[0] += gr;
-                ai[0] += gi;
+                row[slot] += gr;
+                if (m) row[slot + 1] += gi;
+                slot += step;
             }
             T g2r = 0, g2i = 0, g1r = gr, g1i = gi;
-            const T a2 = a * a, ta = t * a;
-#pragma unroll
-            for (int st = 1; st <= IMQ_MAX_P; ++st) {
-                const int n = l + st;
-                if (n <= p) {
-                    const T c1 = (T)(2 * n - 1) * ta;
-                    const T c2 = tab2[n * (p + 1) + l] * a2;
-                    const T iv = tabi[n * (p + 1) + l];
-                    const T nr = (c1 * g1r - c2 * g2r) * iv;
-                    const T ni = (c1 * g1i - c2 * g2i) * iv;
-                    g2r = g1r; g2i = g1i; g1r = nr; g1i = ni;
-                    if ((st & 1) == PAR) {
-                        ar[st / 2] += nr;
-                        ai[st / 2] += ni;
-                    }
+            for (int n = m + 1; n <= p; ++n) {
+                const T c1 = (T)(2 * n - 1) * ta;
+                const T c2 = tab2[n * (p + 1) + m] * a2;
+                const T iv = tabi[n * (p + 1) + m];
+                const T nr = (c1 * g1r - c2 * g2r) * iv;
+                const T ni = (c1 * g1i - c2 * g2i) * iv;
+                g2r = g1r; g2i = g1i; g1r = nr; g1i = ni;
+                if (((n - m) & 1) == PAR) {
+                    row[slot] += nr;
+                    if (m) row[slot + 1] += ni;
+                    slot += step;
                 }
             }
         }
     }
-    int slot = col_base(l, p, PAR);
+    __syncwarp();
     T *Lb = L + (int64_t)b * K;
-#pragma unroll
-    for (int k = 0; k < kMaxCol; ++k) {
-        if (l + PAR + 2 * k <= p) {
-            Lb[slot] += ar[k];
-            if (l > 0) Lb[slot + 1] += ai[k];
-            slot += l ? 2 : 1;
-        }
+    for (int e = lane; e < K; e += 32) {
+        T sum = 0;
+        for (int l2 = 0; l2 < 32; ++l2) sum += acc[l2 * Kpad + e];
+        Lb[e] += sum;
     }
+}
+
+template <class T, int PAR>
+void p2l_launch_impl(Plan &P, const T *u, T *L, int K, cudaStream_t s) {
+    if (P.X.total == 0) return;
+    const size_t smem = sizeof(T) * (2 * (IMQ_MAX_P + 1) * (IMQ_MAX_P + 1) + (IMQ_MAX_P + 2) +
+                                     (size_t)kP2LWarps * 32 * (K | 1));
+    IMQ_CUDA(cudaFuncSetAttribute(k_p2l<T, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_p2l<T, PAR><<<(unsigned)((P.nxbox + kP2LWarps - 1) / kP2LWarps), 32 * kP2LWarps, smem, s>>>(
+        P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(), P.xcum.as<int32_t>(),
+        P.xtot.as<int32_t>(), P.begin.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
+        P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, P.p, P.side, (T)P.c);
+    IMQ_LAUNCH_CHECK();
 }
 
 // ------------------------------------------------------------------ L2P + M2P (W list)
@@ -351,7 +374,7 @@ int64_t Plan::device_bytes() const {
     int64_t t = 0;
     const DevMem *all[] = {&codes, &perm, &level, &prefix, &begin, &end, &parent, &child, &centre, &leaves,
                            &U.off, &U.items, &V.off, &V.items, &W.off, &W.items, &X.off, &X.items,
-                           &colleagues, &vtab, &ucum, &uoff, &pos, &loc, &leaf_of,
+                           &colleagues, &vtab, &ucum, &uoff, &pos, &loc, &rec4, &leaf_of,
                            &ops32.m2m, &ops32.l2l, &ops32.m2l, &ops32.p2mc, &ops32.M, &ops32.L,
                            &ops64.m2m, &ops64.l2l, &ops64.m2l, &ops64.p2mc, &ops64.M, &ops64.L,
                            &schwarz.patch_off, &schwarz.patch_pts, &schwarz.fac_off, &schwarz.factor,
@@ -378,6 +401,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
         }
     }
     const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    if (!fp64 && !P.rec4.ptr) P.rec4.alloc(sizeof(float4) * (size_t)P.N);
     O.M.alloc(es * (size_t)P.nbox * K);
     O.L.alloc(es * (size_t)P.nbox * K);
     if (fp64) {
@@ -406,15 +430,13 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 
 template <class T>
 void p2l_odd_launch(Plan &P, const T *u, T *Lodd, cudaStream_t s) {
-    if (P.X.total == 0) return;
-    k_p2l<T, 1><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
-        P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(), P.begin.as<int32_t>(),
-        P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(),
-        u, Lodd, P.layout_odd.K, P.p, P.side, (T)P.c);
-    IMQ_LAUNCH_CHECK();
+    p2l_launch_impl<T, 1>(P, u, Lodd, P.layout_odd.K, s);
 }
 template void p2l_odd_launch<float>(Plan &, const float *, float *, cudaStream_t);
 template void p2l_odd_launch<double>(Plan &, const double *, double *, cudaStream_t);
+
+template <class T>
+void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches);
 
 template <class T>
 void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaStream_t s, int *launches) {
@@ -424,7 +446,12 @@ void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaS
         P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, P.p, coef, P.side);
     IMQ_LAUNCH_CHECK();
     ++*launches;
-    for (int lev = P.max_level - 1; lev >= 2; --lev) {
+    m2m_levels<T>(P, M, m2m, s, launches);
+}
+
+template <class T>
+void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches) {
+    const int K = P.layout.K;    for (int lev = P.max_level - 1; lev >= 2; --lev) {
         const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
         if (nl <= 0) continue;
         k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
@@ -432,6 +459,8 @@ void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaS
         ++*launches;
     }
 }
+template void m2m_levels<float>(Plan &, float *, const float *, cudaStream_t, int *);
+template void m2m_levels<double>(Plan &, double *, const double *, cudaStream_t, int *);
 template void upward_launch<float>(Plan &, const float *, float *, const float *, const float *, cudaStream_t, int *);
 template void upward_launch<double>(Plan &, const double *, double *, const double *, const double *, cudaStream_t, int *);
 
@@ -490,13 +519,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         ++launches;
         t1();
         t0(kPhM2M);
-        for (int lev = P.max_level - 1; lev >= 2; --lev) {
-            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-            if (nl <= 0) continue;
-            k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
-            IMQ_LAUNCH_CHECK();
-            ++launches;
-        }
+        m2m_levels<T>(P, M, m2m, s, &launches);
         t1();
         // interaction: M2L per level, P2L over X lists
         t0(kPhM2L);
@@ -511,23 +534,13 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t1();
         t0(kPhP2L);
         if (P.X.total > 0) {
-            k_p2l<T, 0><<<blocks_for((int64_t)P.nxbox * 32, 128), 128, 0, s>>>(
-                P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(),
-                P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
-                P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, p, P.side, (T)P.c);
-            IMQ_LAUNCH_CHECK();
+            p2l_launch_impl<T, 0>(P, u, L, K, s);
             ++launches;
         }
         t1();
         // downward pass
         t0(kPhL2L);
-        for (int lev = 3; lev <= P.max_level; ++lev) {
-            const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-            if (nl <= 0) continue;
-            k_l2l<T><<<nl, 128, sizeof(T) * K, s>>>(lb, P.parent.as<int32_t>(), P.prefix.as<uint32_t>(), L, l2l, K);
-            IMQ_LAUNCH_CHECK();
-            ++launches;
-        }
+        l2l_launch<T>(P, L, l2l, K, s, &launches);
         t1();
         // evaluation: L2P + M2P writes b, P2P adds the near field
         t0(kPhFar);

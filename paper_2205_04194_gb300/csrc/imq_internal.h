@@ -145,9 +145,12 @@ struct Plan {
     ListCSR U, V, W, X;
     DevMem colleagues; // int32[9*nbox]
     DevMem vtab;       // int32[40*nbox] V source per offset class, -1 if none
-    DevMem m2l_tiles;  // int4[n_m2l_tiles]: (level - m2l_level_lo, first box, boxes) per M2L tile
+    DevMem m2l_tiles;  // int4[n_m2l_tiles]: (level - m2l_level_lo, first index into m2l_tbox, boxes)
+    DevMem m2l_tbox;   // int32[]: boxes of the M2L levels grouped by (level, quadrant)
     int n_m2l_tiles = 0;
     DevMem xboxes;     // int32[nxbox] boxes whose X list is not empty
+    DevMem xcum;       // int32[n_x]: per box list, exclusive prefix of source counts
+    DevMem xtot;       // int32[nbox] total X-list source points of a box
     int nxbox = 0;
     DevMem utot;       // int32[nbox] total U-list source points of a leaf
     DevMem ucum;       // int32[n_u]: per leaf list, exclusive prefix of source counts
@@ -155,6 +158,7 @@ struct Plan {
     // points, device, sorted order
     DevMem pos;        // double2[N]
     DevMem loc;        // float2[N]  offset from the leaf centre
+    DevMem rec4;       // float4[N]  P2P source records (x, y, u, 0) of the current product
     DevMem leaf_of;    // int32[N]
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])

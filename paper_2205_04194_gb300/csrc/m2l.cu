@@ -25,6 +25,7 @@ constexpr int kThreads = 256;
 
 template <int RR>
 __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__ tiles,
+                                                        const int32_t *__restrict__ tbox,
                                                         const int32_t *__restrict__ vtab,
                                                         const float *__restrict__ M, float *__restrict__ L,
                                                         const float *__restrict__ ops, int K, int Kout, int Kpad) {
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int4 tile = tiles[blockIdx.x];
-    const int li = tile.x, b0 = tile.y, nbt = tile.z;
+    const int li = tile.x, b0 = tile.y, nbt = tile.z;   // boxes tbox[b0 .. b0+nbt)
     const float *opl = ops + (size_t)li * kOffsetClasses * K * Kp;
     float acc[RR][8];
 #pragma unroll
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__
     for (int o = 0; o < kOffsetClasses; ++o) {
         int s = -1;
         if (tid < kTB) {
-            s = tid < nbt ? vtab[(int64_t)kOffsetClasses * (b0 + tid) + o] : -1;
+            s = tid < nbt ? vtab[(int64_t)kOffsetClasses * tbox[b0 + tid] + o] : -1;
             srcs[tid] = s;
         }
         if (!__syncthreads_or(s >= 0)) continue;
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__
     for (int c = 0; c < 8; ++c) {
         const int col = tx + 16 * c;
         if (col >= nbt) continue;
-        float *Lb = L + (int64_t)(b0 + col) * Kout;
+        float *Lb = L + (int64_t)tbox[b0 + col] * Kout;
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const int row = ty * RR + r;
@@ -124,7 +125,8 @@ void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops,
     case R: {                                                                                             \
         auto kern = k_m2l_tiled<R>;                                                                       \
         IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-        kern<<<P.n_m2l_tiles, kThreads, smem, s>>>(P.m2l_tiles.as<int4>(), P.vtab.as<int32_t>(), M, L,    \
+        kern<<<P.n_m2l_tiles, kThreads, smem, s>>>(P.m2l_tiles.as<int4>(), P.m2l_tbox.as<int32_t>(),     \
+                                                   P.vtab.as<int32_t>(), M, L,                            \
                                                    ops, K, Kout, Kpad);                                   \
         break;                                                                                            \
     }
@@ -142,16 +144,34 @@ void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops,
     IMQ_LAUNCH_CHECK();
 }
 
+// Tiles hold boxes of one level and one quadrant within the parent: the V list
+// of a box draws its offsets from the 27 classes fixed by its quadrant, so the
+// other 13 class passes are skipped for the whole tile.
 void build_m2l_tiles(Plan &P, cudaStream_t s) {
+    std::vector<uint32_t> prefix(P.nbox);
+    IMQ_CUDA(cudaMemcpyAsync(prefix.data(), P.prefix.ptr, sizeof(uint32_t) * P.nbox, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
     std::vector<int4> t;
+    std::vector<int32_t> order;
     for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
-        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-        for (int b = 0; b < nl; b += kTB) t.push_back(make_int4(lev - P.m2l_level_lo, lb + b, std::min(kTB, nl - b), 0));
+        const int lb = P.level_start[lev], le = P.level_start[lev + 1];
+        for (int q = 0; q < 4; ++q) {
+            const int start = (int)order.size();
+            for (int b = lb; b < le; ++b)
+                if ((int)(prefix[b] & 3u) == q) order.push_back(b);
+            const int cnt = (int)order.size() - start;
+            for (int k = 0; k < cnt; k += kTB)
+                t.push_back(make_int4(lev - P.m2l_level_lo, start + k, std::min(kTB, cnt - k), 0));
+        }
     }
     P.n_m2l_tiles = (int)t.size();
     P.m2l_tiles.alloc(sizeof(int4) * std::max<size_t>(1, t.size()));
-    if (!t.empty())
+    P.m2l_tbox.alloc(sizeof(int32_t) * std::max<size_t>(1, order.size()));
+    if (!t.empty()) {
         IMQ_CUDA(cudaMemcpyAsync(P.m2l_tiles.ptr, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, s));
+        IMQ_CUDA(cudaMemcpyAsync(P.m2l_tbox.ptr, order.data(), sizeof(int32_t) * order.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
     IMQ_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -72,10 +72,6 @@ __device__ __forceinline__ T lane_reduce(T (&acc)[TC], int lane) {
     return v;
 }
 
-struct SrcCursor {
-    int r;
-};
-
 // Position q of the concatenated U-list source range -> sorted point index j, entry r.
 __device__ __forceinline__ int source_index(int q, int &r, int u1, const int32_t *__restrict__ ucum,
                                             const int32_t *__restrict__ uitems, const int32_t *__restrict__ begin) {
@@ -83,11 +79,93 @@ __device__ __forceinline__ int source_index(int q, int &r, int u1, const int32_t
     return begin[uitems[r]] + (q - ucum[r]);
 }
 
+// Per product: one 16-byte record (x, y, u, 0) per sorted point, x and y the
+// offset from the point's leaf centre.
+__global__ void k_pack_records(const float2 *__restrict__ loc, const float *__restrict__ u, int64_t n,
+                               float4 *__restrict__ rec) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float2 l = loc[i];
+        rec[i] = make_float4(l.x, l.y, u[i], 0.f);
+    }
+}
+
+constexpr int kStageCap = 1024;   // source records staged per warp at a time (16 KB)
+
+struct WarpStage {
+    float4 rec[kStageCap];
+    uint64_t bar;
+};
+
+// Stage concatenated positions [q0, q0 + len) of the U-list sources of one leaf
+// into shared memory with 1-D TMA bulk copies (one per overlapping U entry), wait
+// for them (bounded), then shift each record into the target leaf's frame.
+// Returns false if the wait timed out.
+__device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, int q0, int len, int u0, int u1,
+                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ uitems,
+                                              const int32_t *__restrict__ ucum, const float2 *__restrict__ udelta,
+                                              const float4 *__restrict__ rec, int lane, int *err) {
+    if (lane == 0) {
+        // earlier generic-proxy writes to ws.rec must be ordered before the async-proxy copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&ws.bar, (uint32_t)len * 16u);
+        for (int r = u0; r < u1; ++r) {
+            const int lo = ucum[r];
+            const int cnt = (r + 1 < u1 ? ucum[r + 1] : 0x7FFFFFFF) - lo;
+            const int a = max(lo, q0), bnd = min(lo + cnt, q0 + len);
+            if (bnd <= a) {
+                if (lo >= q0 + len) break;
+                continue;
+            }
+            const int src0 = begin[uitems[r]] + (a - lo);
+            bulk_g2s(&ws.rec[a - q0], rec + src0, (uint32_t)(bnd - a) * 16u, &ws.bar);
+        }
+    }
+    const bool ok = mbar_wait(&ws.bar, phase & 1u);
+    phase++;
+    if (!__all_sync(0xFFFFFFFFu, ok)) {
+        if (lane == 0) set_error(err, kErrWaitTimeout);
+        return false;
+    }
+    int r = u0;
+    for (int q = lane; q < len; q += 32) {
+        const int gq = q0 + q;
+        while (r + 1 < u1 && ucum[r + 1] <= gq) ++r;
+        const float2 d = udelta[r];
+        float4 v = ws.rec[q];
+        v.x -= d.x;
+        v.y -= d.y;
+        ws.rec[q] = v;
+    }
+    __syncwarp();
+    return true;
+}
+
 template <int TC>
-__device__ __forceinline__ float p2p_chunk_f32(int ti, int ntc, int lane, int u0, int u1, int St,
-                                               const int32_t *__restrict__ begin, const int32_t *__restrict__ uitems,
-                                               const int32_t *__restrict__ ucum, const float2 *__restrict__ udelta,
-                                               const float2 *__restrict__ loc, const float *__restrict__ u, float c2) {
+__device__ __forceinline__ void p2p_tile_f32(const float4 *__restrict__ srec, int len, int lane, const u64 (&tx)[TC / 2],
+                                             const u64 (&ty)[TC / 2], u64 (&acc)[TC / 2], u64 cc) {
+    for (int q0 = 0; q0 < len; q0 += 32) {
+        const int q = q0 + lane;
+        const float4 sr = q < len ? srec[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const u64 nx = pk2(-sr.x, -sr.x), ny = pk2(-sr.y, -sr.y), uu = pk2(sr.z, sr.z);
+#pragma unroll
+        for (int k = 0; k < TC / 2; ++k) {
+            const u64 dx = add2(tx[k], nx);
+            const u64 dy = add2(ty[k], ny);
+            const u64 d2 = fma2(dx, dx, fma2(dy, dy, cc));
+            float a, b;
+            up2(d2, a, b);
+            acc[k] = fma2(pk2(rsqrtf(a), rsqrtf(b)), uu, acc[k]);
+        }
+    }
+}
+
+template <int TC>
+__device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase, bool staged_all, int ti, int ntc,
+                                                  int lane, int u0, int u1, int St, const int32_t *__restrict__ begin,
+                                                  const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
+                                                  const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
+                                                  const float4 *__restrict__ rec, float c2, int *err) {
     u64 tx[TC / 2], ty[TC / 2], acc[TC / 2];
 #pragma unroll
     for (int q = 0; q < TC / 2; ++q) {
@@ -99,27 +177,14 @@ __device__ __forceinline__ float p2p_chunk_f32(int ti, int ntc, int lane, int u0
         acc[q] = 0ull;
     }
     const u64 cc = pk2(c2, c2);
-    int r = u0;
-    for (int q0 = 0; q0 < St; q0 += 32) {
-        const int q = q0 + lane;
-        float xs = 0.f, ys = 0.f, us = 0.f;
-        if (q < St) {
-            const int j = source_index(q, r, u1, ucum, uitems, begin);
-            const float2 l = loc[j];
-            const float2 d = udelta[r];
-            xs = l.x - d.x;
-            ys = l.y - d.y;
-            us = u[j];
-        }
-        const u64 nx = pk2(-xs, -xs), ny = pk2(-ys, -ys), uu = pk2(us, us);
-#pragma unroll
-        for (int k = 0; k < TC / 2; ++k) {
-            const u64 dx = add2(tx[k], nx);
-            const u64 dy = add2(ty[k], ny);
-            const u64 d2 = fma2(dx, dx, fma2(dy, dy, cc));
-            float a, b;
-            up2(d2, a, b);
-            acc[k] = fma2(pk2(rsqrtf(a), rsqrtf(b)), uu, acc[k]);
+    if (staged_all) {
+        p2p_tile_f32<TC>(ws.rec, St, lane, tx, ty, acc, cc);
+    } else {
+        for (int q0 = 0; q0 < St; q0 += kStageCap) {
+            const int len = min(kStageCap, St - q0);
+            if (!stage_sources(ws, phase, q0, len, u0, u1, begin, uitems, ucum, udelta, rec, lane, err)) break;
+            p2p_tile_f32<TC>(ws.rec, len, lane, tx, ty, acc, cc);
+            __syncwarp();
         }
     }
     float s[TC];
@@ -132,26 +197,39 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
     const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-    const float *__restrict__ u, float c2, float *__restrict__ bs) {
+    const float4 *__restrict__ rec, float c2, float *__restrict__ bs, int *err) {
+    extern __shared__ __align__(128) unsigned char smraw_p2p[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStage &ws = reinterpret_cast<WarpStage *>(smraw_p2p)[w];
+    if (lane == 0) {
+        mbar_init(&ws.bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
     const int widx = blockIdx.x * kP2PWarps + w;
     if (widx >= nleaf) return;
     const int b = leaves[widx];
     const int tb = begin[b], nt = end[b] - tb;
     const int u0 = uoffs[b], u1 = uoffs[b + 1];
     const int St = utot[b];
+    uint32_t phase = 0;
+    const bool staged_all = St <= kStageCap;
+    if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, begin, uitems, ucum, udelta, rec, lane, err)) return;
     for (int tc = 0; tc < nt; tc += 32) {
         const int ntc = min(32, nt - tc);
         float tot;
         int tcap;
         if (ntc <= 8) {
-            tot = p2p_chunk_f32<8>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tot = p2p_chunk_staged<8>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
+                                      udelta, loc, rec, c2, err);
             tcap = 8;
         } else if (ntc <= 16) {
-            tot = p2p_chunk_f32<16>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tot = p2p_chunk_staged<16>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
+                                       udelta, loc, rec, c2, err);
             tcap = 16;
         } else {
-            tot = p2p_chunk_f32<32>(tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum, udelta, loc, u, c2);
+            tot = p2p_chunk_staged<32>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
+                                       udelta, loc, rec, c2, err);
             tcap = 32;
         }
         if (lane < tcap && lane < ntc) bs[tb + tc + lane] += tot;
@@ -212,10 +290,16 @@ template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
     const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
     if constexpr (std::is_same<T, float>::value) {
-        k_p2p_f32<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
-                                                  P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
-                                                  P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
-                                                  P.loc.as<float2>(), u, (float)(P.c * P.c), bs);
+        if (!P.rec4.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace missing");
+        k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u, P.N, P.rec4.as<float4>());
+        IMQ_LAUNCH_CHECK();
+        const size_t smem = sizeof(WarpStage) * kP2PWarps;
+        IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2p_f32<<<grid, 32 * kP2PWarps, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
+                                                     P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
+                                                     P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
+                                                     P.loc.as<float2>(), P.rec4.as<float4>(), (float)(P.c * P.c), bs,
+                                                     device_error_word());
     } else {
         k_p2p_f64<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
                                                   P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),

@@ -445,6 +445,19 @@ __global__ void u_aux(int nbox, const int8_t *isleaf, const int32_t *begin, cons
     atomicAdd(pairs, (unsigned long long)run * (unsigned long long)(end[b] - begin[b]));
 }
 
+// per X entry: exclusive prefix of source points within the box's list; per box: total
+__global__ void x_aux(int nbox, const int32_t *begin, const int32_t *end, const int32_t *xoff,
+                      const int32_t *xitems, int32_t *xcum, int32_t *xtot) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int run = 0;
+    for (int k = xoff[b]; k < xoff[b + 1]; ++k) {
+        xcum[k] = run;
+        run += end[xitems[k]] - begin[xitems[k]];
+    }
+    xtot[b] = run;
+}
+
 __global__ void v_table(int nbox, const int2 *ixy, const int32_t *voff, const int32_t *vitems, int32_t *vtab) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
@@ -766,6 +779,11 @@ void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups
             }
         }
     }
+    P.xcum.alloc(sizeof(int32_t) * std::max<int64_t>(1, P.X.total));
+    P.xtot.alloc(sizeof(int32_t) * nb);
+    x_aux<<<blocks_for(nb, 128), 128, 0, s>>>(nb, P.begin.as<int32_t>(), P.end.as<int32_t>(), P.X.off.as<int32_t>(),
+                                              P.X.items.as<int32_t>(), P.xcum.as<int32_t>(), P.xtot.as<int32_t>());
+    IMQ_LAUNCH_CHECK();
     build_m2l_tiles(P, s);
     int herr = 0;
     IMQ_CUDA(cudaMemcpyAsync(&herr, lerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));

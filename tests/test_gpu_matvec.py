@@ -79,6 +79,13 @@ def test_fast_uniform_ragged_leaf():
     _fast_case(pts, 0.02, 12, 17, (0.0, 0.0, 1.0))
 
 
+def test_fast_large_leaves_stage_sources_in_chunks():
+    # leaf 200: U-list sources exceed one shared-memory stage (1024 records) and
+    # leaves hold several 32-target chunks
+    pts = W.uniform_points(12000, 12)
+    _fast_case(pts, 0.02, 10, 200, (0.0, 0.0, 1.0))
+
+
 def test_fast_degenerate_single_leaf_and_single_point():
     imq = _imq()
     pts = W.uniform_points(90, 9)
