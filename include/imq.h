@@ -111,6 +111,22 @@ imq_status imq_plan_eval(const double *nodes, int64_t n_nodes, const double *tar
                          double c, int p, int leaf, const imq_options *opt, void *stream,
                          imq_plan_t *out);
 
+/* ------------------------------------------------------------------------- *
+ * imq_plan_batched -- one plan for nprob independent problems (their own
+ * points and shape c, one order p and leaf size), merged into one flattened
+ * tree so that every phase of imq_matvec / imq_cg_solve is one launch over
+ * all problems.  Problem b owns points [offsets[b], offsets[b+1]) of
+ * `points` (double[N][2], host or device); offsets (int64[nprob+1], host,
+ * offsets[0] = 0, strictly increasing) and cvals (double[nprob], host).
+ * Vectors of the batched plan are [nrhs][N] in the same concatenated order;
+ * the product is block diagonal (no interaction between problems).  The
+ * problems share the square D (opt->has_domain, else the bounding square of
+ * all points).  imq_matvec_dc and evaluation are not available on batched
+ * plans (IMQ_UNSUPPORTED).  Errors as imq_plan.
+ * ------------------------------------------------------------------------- */
+imq_status imq_plan_batched(const double *points, const int64_t *offsets, int nprob, const double *cvals,
+                            int p, int leaf, const imq_options *opt, void *stream, imq_plan_t *out);
+
 /* Release every device allocation of the plan (after synchronising its work). */
 void imq_plan_destroy(imq_plan_t plan);
 
@@ -230,6 +246,30 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
                         const imq_cg_options *opt, imq_cg_info *info, void *stream);
 
 /* ------------------------------------------------------------------------- *
+ * imq_cg_solve_batched -- imq_cg_solve on a plan from imq_plan_batched: the
+ * nprob systems A_b coef_b = f_b (Section 2, Eq. (3)-(4), one per problem)
+ * are solved together, one fast product over all problems per iteration,
+ * with per-problem CG scalars and convergence tests.  imq_cg_solve on a
+ * batched plan does the same without the per-problem outputs.
+ *
+ *   f, coef      : double[nrhs][N_total], problems in the plan's order.
+ *   rel_residual : host double[nrhs][nprob] or NULL: true relative residual
+ *                  ||f_b - A_b coef_b|| / ||f_b|| of each problem (FP64 fast
+ *                  product of the plan).
+ *   iterations   : host int32[nrhs][nprob] or NULL: inner iterations of each
+ *                  problem.
+ *   info         : iterations = sum over right-hand sides of the largest
+ *                  per-problem count; rel_residual[r] and max_rel_residual
+ *                  are maxima over the problems.
+ *   Errors: as imq_cg_solve; IMQ_INVALID_ARG if the plan is not batched;
+ *   IMQ_UNSUPPORTED for the dense inner operator or residual (they would
+ *   couple the problems) and for residual_plan.
+ * ------------------------------------------------------------------------- */
+imq_status imq_cg_solve_batched(imq_plan_t plan, const double *f, double *coef, int nrhs,
+                                const imq_cg_options *opt, imq_cg_info *info, double *rel_residual,
+                                int32_t *iterations, void *stream);
+
+/* ------------------------------------------------------------------------- *
  * imq_interp_loss_grad -- validation loss of the interpolant (Eq. (2)) and its
  * gradient in the shape c and the data values f (adjoint method).
  *   coef = A^{-1} f (CG on `train`), P = E coef on `eval` (a plan from
@@ -295,6 +335,8 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
 typedef struct imq_plan_info {
     int64_t n_points;
     int64_t n_nodes;                     /* evaluation plans: nodes among n_points (else 0) */
+    int32_t n_problems;                  /* batched plans: independent problems (else 1)     */
+    int32_t reserved0;
     int32_t n_boxes, n_leaves, max_level, p, leaf, k_real;  /* k_real: reals per expansion */
     double x0, y0, side, c;
     int64_t n_u, n_v, n_w, n_x;          /* total entries of each interaction list */

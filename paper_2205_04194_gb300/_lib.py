@@ -34,7 +34,7 @@ class ImqOptions(ctypes.Structure):
 
 
 class PlanInfo(ctypes.Structure):
-    _fields_ = [("n_points", I64), ("n_nodes", I64), ("n_boxes", I32), ("n_leaves", I32), ("max_level", I32), ("p", I32),
+    _fields_ = [("n_points", I64), ("n_nodes", I64), ("n_problems", I32), ("reserved0", I32), ("n_boxes", I32), ("n_leaves", I32), ("max_level", I32), ("p", I32),
                 ("leaf", I32), ("k_real", I32), ("x0", D), ("y0", D), ("side", D), ("c", D),
                 ("n_u", I64), ("n_v", I64), ("n_w", I64), ("n_x", I64), ("p2p_pairs", I64),
                 ("m2l_pairs", I64), ("device_bytes", I64)]
@@ -56,6 +56,7 @@ class CgInfo(ctypes.Structure):
 SIGNATURES = {
     "imq_plan": (INT, [P, I64, D, INT, INT, P, P, P]),
     "imq_plan_eval": (INT, [P, I64, P, I64, D, INT, INT, P, P, P]),
+    "imq_plan_batched": (INT, [P, P, INT, P, INT, INT, P, P, P]),
     "imq_plan_destroy": (None, [P]),
     "imq_matvec_dc": (INT, [P, P, P, INT, INT, P]),
     "imq_evaluate": (INT, [P, P, P, INT, INT, P]),
@@ -66,6 +67,7 @@ SIGNATURES = {
     "imq_dense_matvec": (INT, [P, I64, D, P, P, INT, INT, P]),
     "imq_cg_default_options": (None, [P]),
     "imq_cg_solve": (INT, [P, P, P, INT, P, P, P]),
+    "imq_cg_solve_batched": (INT, [P, P, P, INT, P, P, P, P, P]),
     "imq_interp_loss_grad": (INT, [P, P, P, P, P, INT, P, P, P, P, P, P]),
     "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
     "imq_plan_get_info": (INT, [P, P]),

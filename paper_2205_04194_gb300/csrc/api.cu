@@ -234,6 +234,65 @@ imq_status imq_plan_eval(const double *nodes, int64_t n_nodes, const double *tar
     });
 }
 
+imq_status imq_plan_batched(const double *points, const int64_t *offsets, int nprob, const double *cvals, int p,
+                            int leaf, const imq_options *opt, void *stream, imq_plan_t *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out || !points || !offsets || !cvals) fail(IMQ_INVALID_ARG, "imq_plan_batched: NULL pointer");
+        if (nprob < 1) fail(IMQ_INVALID_ARG, "imq_plan_batched: nprob must be >= 1");
+        std::vector<int64_t> offs(offsets, offsets + nprob + 1);
+        std::vector<double> cs(cvals, cvals + nprob);
+        if (offs[0] != 0) fail(IMQ_INVALID_ARG, "imq_plan_batched: offsets[0] must be 0");
+        for (int b = 0; b < nprob; ++b) {
+            if (offs[b + 1] <= offs[b]) fail(IMQ_INVALID_ARG, "imq_plan_batched: every problem needs >= 1 point");
+            if (!std::isfinite(cs[b]) || cs[b] <= 0) fail(IMQ_INVALID_ARG, "imq_plan_batched: c must be finite and > 0");
+        }
+        const int64_t N = offs[nprob];
+        double x0, y0, side;
+        bool dups;
+        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups);
+        check_device();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
+        if (side <= 0) {   // one square containing every problem's points
+            std::vector<double> h(2 * (size_t)N);
+            IMQ_CUDA(cudaMemcpyAsync(h.data(), pts.ptr, sizeof(double) * 2 * N, cudaMemcpyDefault, s));
+            IMQ_CUDA(cudaStreamSynchronize(s));
+            double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1]))
+                    fail(IMQ_INVALID_ARG, "imq_plan_batched: a coordinate is NaN or infinite");
+                mnx = std::min(mnx, h[2 * i]); mxx = std::max(mxx, h[2 * i]);
+                mny = std::min(mny, h[2 * i + 1]); mxy = std::max(mxy, h[2 * i + 1]);
+            }
+            x0 = mnx;
+            y0 = mny;
+            side = std::max(mxx - mnx, mxy - mny);
+            if (!(side > 0)) side = 1.0;
+        }
+        auto *hp = new imq_plan_s;
+        try {
+            Plan &P = hp->P;
+            IMQ_CUDA(cudaGetDevice(&P.device));
+            P.N = N;
+            P.c = cs[0];
+            P.p = p;
+            P.leaf = leaf;
+            P.x0 = x0;
+            P.y0 = y0;
+            P.side = side;
+            P.layout.build(p, 0);
+            build_batched_plan(P, static_cast<const double *>(pts.ptr), offs, cs, dups, s);
+            ensure_ops(P, false, s);
+            IMQ_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            delete hp;
+            throw;
+        }
+        *out = hp;
+    });
+}
+
 void imq_plan_destroy(imq_plan_t plan) {
     if (!plan) return;
     cudaDeviceSynchronize();
@@ -344,8 +403,10 @@ void imq_cg_default_options(imq_cg_options *o) {
     o->residual = IMQ_RESIDUAL_PLAN_F64;
 }
 
-imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs, const imq_cg_options *opt,
-                        imq_cg_info *info, void *stream) {
+namespace {
+
+imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, const imq_cg_options *opt,
+                    imq_cg_info *info, double *rel_out, int32_t *iters_out, bool batched_call, void *stream) {
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->status = IMQ_CUDA_ERROR;
@@ -372,6 +433,8 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
         if (o.residual != IMQ_RESIDUAL_PLAN_F64 && o.residual != IMQ_RESIDUAL_DENSE_F64)
             fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown residual mode");
         Plan &P = plan->P;
+        if (batched_call && P.prob_off.empty())
+            fail(IMQ_INVALID_ARG, "imq_cg_solve_batched: plan was not made by imq_plan_batched");
         Plan *RP = o.residual_plan ? &o.residual_plan->P : nullptr;
         if (RP && RP->N != P.N) fail(IMQ_INVALID_ARG, "imq_cg_solve: residual_plan has a different N");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -380,7 +443,11 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
         DevOut dx(coef, bytes, s);
         if (o.x0_given && dx.tmp) IMQ_CUDA(cudaMemcpyAsync(dx.ptr, coef, bytes, cudaMemcpyHostToDevice, s));
         try {
-            cg_solve(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o, RP, info, s);
+            if (!P.prob_off.empty())
+                cg_solve_batched(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o,
+                                 info, rel_out, iters_out, s);
+            else
+                cg_solve(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o, RP, info, s);
         } catch (const Error &e) {
             if (e.status == IMQ_NOT_CONVERGED || e.status == IMQ_NUMERICAL) dx.finish();
             throw;
@@ -389,6 +456,18 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
     });
     if (info) info->status = st;
     return st;
+}
+
+}  // namespace
+
+imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs, const imq_cg_options *opt,
+                        imq_cg_info *info, void *stream) {
+    return cg_entry(plan, f, coef, nrhs, opt, info, nullptr, nullptr, false, stream);
+}
+
+imq_status imq_cg_solve_batched(imq_plan_t plan, const double *f, double *coef, int nrhs, const imq_cg_options *opt,
+                                imq_cg_info *info, double *rel_residual, int32_t *iterations, void *stream) {
+    return cg_entry(plan, f, coef, nrhs, opt, info, rel_residual, iterations, true, stream);
 }
 
 imq_status imq_dense_matvec(const double *points, int64_t N, double c, const void *v, void *out, int nrhs,
@@ -417,6 +496,7 @@ imq_status imq_plan_get_info(imq_plan_t plan, imq_plan_info *info) {
         std::memset(info, 0, sizeof(*info));
         info->n_points = P.N;
         info->n_nodes = P.n_nodes;
+        info->n_problems = P.nprob;
         info->n_boxes = P.nbox;
         info->n_leaves = P.nleaf;
         info->max_level = P.max_level;

@@ -223,13 +223,16 @@ __global__ void k_scatter_f64(const double *__restrict__ v, const int32_t *__res
 // singular).  Output: n x n column-major lower factor.
 template <class T>
 __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
-                                 const int64_t *__restrict__ foff, const double2 *__restrict__ pos, T c2,
-                                 T shift, T dmin, T *__restrict__ factor, int *nclamped) {
+                                 const int64_t *__restrict__ foff, const double2 *__restrict__ pos,
+                                 const int32_t *__restrict__ leaves, ShapeC shape, double shift_rel,
+                                 double dmin_rel, T *__restrict__ factor, int *nclamped) {
     extern __shared__ __align__(16) unsigned char smraw_f[];
     T *A = reinterpret_cast<T *>(smraw_f);   // n x n, column-major
     const int b = blockIdx.x;
     if (b >= npatch) return;
     const int o = poff[b], n = poff[b + 1] - o;
+    const double cb = shape.of(leaves[b]);
+    const T c2 = (T)(cb * cb), shift = (T)(shift_rel / cb), dmin = (T)(dmin_rel / cb);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int j = e / n, i = e - j * n;   // column j, row i
         const double2 pi = pos[ppts[o + i]], pj = pos[ppts[o + j]];
@@ -273,7 +276,7 @@ template <class T>
 __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
                                 const int64_t *__restrict__ foff, const T *__restrict__ factor,
                                 const double *__restrict__ r, double *__restrict__ ypatch, const CGScalars *S) {
-    if (S->done) return;
+    if (S && S->done) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= npatch) return;
@@ -325,12 +328,13 @@ __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, co
 // z_j = sum over the patch slots holding point j (fixed order); points in no patch get c r_j.
 __global__ void k_schwarz_gather(int64_t n, const int32_t *__restrict__ ptoff, const int32_t *__restrict__ ptslot,
                                  const double *__restrict__ ypatch, const double *__restrict__ r, double cdiag,
+                                 const int32_t *__restrict__ pt_prob, const double *__restrict__ prob_c,
                                  double *__restrict__ z, const CGScalars *S) {
-    if (S->done) return;
+    if (S && S->done) return;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const int a = ptoff[j], e = ptoff[j + 1];
         if (a == e) {
-            z[j] = cdiag * r[j];
+            z[j] = (pt_prob ? prob_c[pt_prob[j]] : cdiag) * r[j];
         } else {
             double s = 0;
             for (int k = a; k < e; ++k) s += ypatch[ptslot[k]];
@@ -403,18 +407,18 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     AsyncMem ncl(sizeof(int), s);
     IMQ_CUDA(cudaMemsetAsync(ncl.ptr, 0, sizeof(int), s));
     const size_t smem = es * (size_t)maxn * maxn;
-    const double diag = 1.0 / P.c;
     if (fp64) {
         IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_schwarz_factor<double><<<Z.npatch, 256, smem, s>>>(
             Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
-            P.pos.as<double2>(), P.c * P.c, shift * diag, 1e-14 * diag, Z.factor.as<double>(), ncl.as<int>());
+            P.pos.as<double2>(), P.leaves.as<int32_t>(), P.shape(), shift, 1e-14, Z.factor.as<double>(),
+            ncl.as<int>());
     } else {
         IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_schwarz_factor<float><<<Z.npatch, 256, smem, s>>>(
             Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
-            P.pos.as<double2>(), (float)(P.c * P.c), (float)(shift * diag), (float)(1e-6 * diag),
-            Z.factor.as<float>(), ncl.as<int>());
+            P.pos.as<double2>(), P.leaves.as<int32_t>(), P.shape(), shift, 1e-6, Z.factor.as<float>(),
+            ncl.as<int>());
     }
     IMQ_LAUNCH_CHECK();
     IMQ_CUDA(cudaStreamSynchronize(s));
@@ -424,8 +428,11 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     Z.ready = true;
 }
 
-void schwarz_apply(const Schwarz &Z, const double *r, double *z, double c, int64_t n, const CGScalars *S,
+}  // namespace
+
+void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, double c, int64_t n, const void *Sv,
                    cudaStream_t s) {
+    const CGScalars *S = static_cast<const CGScalars *>(Sv);
     const unsigned g = blocks_for((int64_t)Z.npatch * 32, 128);
     if (Z.fp64)
         k_schwarz_solve<double><<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
@@ -436,9 +443,13 @@ void schwarz_apply(const Schwarz &Z, const double *r, double *z, double c, int64
                                                  Z.fac_off.as<int64_t>(), Z.factor.as<float>(), r,
                                                  Z.ypatch.as<double>(), S);
     k_schwarz_gather<<<kRedBlocks, kRedThreads, 0, s>>>(n, Z.pt_off.as<int32_t>(), Z.pt_slot.as<int32_t>(),
-                                                        Z.ypatch.as<double>(), r, c, z, S);
+                                                        Z.ypatch.as<double>(), r, c,
+                                                        P.nprob > 1 ? P.pt_prob.as<int32_t>() : nullptr,
+                                                        P.nprob > 1 ? P.prob_c.as<double>() : nullptr, z, S);
     IMQ_LAUNCH_CHECK();
 }
+
+namespace {
 
 struct Work {
     DevMem x, xb, r, p, q, z, u32, b32, part, S, tmp;
@@ -478,6 +489,8 @@ void residual_product(Plan &P, Plan *RP, int mode, const double *vs, double *out
 }
 
 }  // namespace
+
+void schwarz_setup(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) { build_schwarz(P, nmax, shift, fp64, s); }
 
 double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s) {
     DevMem part, tmp;
@@ -535,7 +548,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         k_finish_rr<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S);
         k_copy_best<<<gr, kRedThreads, 0, cs>>>(x, w.xb.as<double>(), n, S);
         if (o.precond == IMQ_PRECOND_SCHWARZ) {
-            schwarz_apply(Z, r, z, P.c, n, S, cs);
+            schwarz_apply(P, Z, r, z, P.c, n, S, cs);
             k_dot_part<<<gr, kRedThreads, 0, cs>>>(r, z, n, w.part.as<double>(), S);
             k_finish_beta<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S, 0);
         } else {
@@ -611,7 +624,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                 if (o.precond == IMQ_PRECOND_SCHWARZ) {
                     CGScalars hz = h;
                     IMQ_CUDA(cudaMemcpyAsync(S, &hz, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
-                    schwarz_apply(Z, r, z, P.c, n, S, s);
+                    schwarz_apply(P, Z, r, z, P.c, n, S, s);
                     h.rz = read_dot(r, z, n, w.part, w.tmp, s);
                 } else {
                     h.rz = rr0;

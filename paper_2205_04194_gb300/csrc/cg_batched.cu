@@ -1,0 +1,416 @@
+// Conjugate gradients on a batched plan: nprob independent interpolation
+// systems A_b coef_b = f_b (Section 2, Eq. (3)-(4), one per problem) solved
+// together.  Every product is one fast product over the merged tree of all
+// problems; every scalar of CG (alpha, beta, the residual norms, the
+// convergence test) is per problem.
+//
+//  * points of problem b occupy the contiguous Morton-order range
+//    [prob_off[b], prob_off[b+1]), so each per-problem dot is one thread
+//    block over that range: a fixed stride and a fixed tree, hence
+//    bit-reproducible; the block finishes the scalar update itself, so an
+//    iteration needs no separate "finish" launches;
+//  * a problem that has converged (or broken down) sets its own done flag and
+//    its blocks skip the vector updates; the product still runs over the whole
+//    merged tree (the other problems need it);
+//  * kIterPerGraph iterations are captured into one CUDA graph; the host reads
+//    the nprob state records once per graph launch and stops when all are done;
+//  * refinement steps are taken together: r_b = f_b - A_b x_b in FP64 for all
+//    problems, problems already within rtol stay done through the inner pass.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "imq_internal.h"
+#include "util.cuh"
+
+namespace imq {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kIterPerGraph = 8;
+
+enum BState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3 };
+
+struct BScalars {
+    double rz, rr, alpha, rr_target, rr_best;
+    int iter, done, status, maxit;
+};
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[kThreads];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = kThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    const double t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+__global__ void k_to_f32(const double *__restrict__ p, float *__restrict__ u, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = (float)p[i];
+}
+
+// q = A p (from FP32 b32 or FP64 q64), alpha_b = rz_b / (p.q)_b
+__global__ void __launch_bounds__(kThreads) k_alpha(const float *__restrict__ b32, const double *__restrict__ p,
+                                                    double *__restrict__ q, const int64_t *__restrict__ off,
+                                                    BScalars *S) {
+    const int b = blockIdx.x;
+    if (S[b].done) return;
+    const int64_t lo = off[b], hi = off[b + 1];
+    double acc = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+        double qi;
+        if (b32) {
+            qi = (double)b32[i];
+            q[i] = qi;
+        } else {
+            qi = q[i];
+        }
+        acc += p[i] * qi;
+    }
+    const double pq = block_sum(acc);
+    if (threadIdx.x == 0) {
+        if (!(pq > 0) || !isfinite(pq)) {
+            S[b].status = kNumerical;
+            S[b].done = 1;
+        } else {
+            S[b].alpha = S[b].rz / pq;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, rr = r.r, convergence test, keep the best iterate
+__global__ void __launch_bounds__(kThreads) k_update(double *__restrict__ x, double *__restrict__ r,
+                                                     const double *__restrict__ p, const double *__restrict__ q,
+                                                     double *__restrict__ xb, const int64_t *__restrict__ off,
+                                                     BScalars *S) {
+    const int b = blockIdx.x;
+    __shared__ int s_go, s_improved;
+    if (threadIdx.x == 0) s_go = !S[b].done;
+    __syncthreads();
+    if (!s_go) return;
+    const int64_t lo = off[b], hi = off[b + 1];
+    const double a = S[b].alpha;
+    double acc = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    const double rr = block_sum(acc);
+    if (threadIdx.x == 0) {
+        BScalars &s = S[b];
+        s.rr = rr;
+        s.iter += 1;
+        s_improved = 0;
+        if (!isfinite(rr)) {
+            s.status = kNumerical;
+            s.done = 1;
+        } else {
+            if (rr < s.rr_best) {
+                s.rr_best = rr;
+                s_improved = 1;
+            }
+            if (rr <= s.rr_target) {
+                s.status = kConverged;
+                s.done = 1;
+            } else if (s.iter >= s.maxit) {
+                s.status = kMaxIter;
+                s.done = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_improved)
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) xb[i] = x[i];
+}
+
+// beta_b = (r.z)_b / rz_b, p = z + beta p, rz_b = (r.z)_b.  Run on problems
+// that finished in this iteration too: their p is never used again.
+__global__ void __launch_bounds__(kThreads) k_beta(const double *__restrict__ r, const double *__restrict__ z,
+                                                   double *__restrict__ p, const int64_t *__restrict__ off,
+                                                   BScalars *S) {
+    const int b = blockIdx.x;
+    __shared__ double s_beta;
+    __shared__ int s_go;
+    if (threadIdx.x == 0) s_go = !S[b].done;
+    __syncthreads();
+    if (!s_go) return;
+    const int64_t lo = off[b], hi = off[b + 1];
+    double acc = 0;
+    if (z != r)
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) acc += r[i] * z[i];
+    const double rzn = z != r ? block_sum(acc) : S[b].rr;
+    if (threadIdx.x == 0) {
+        BScalars &s = S[b];
+        if (!(s.rz > 0) || !isfinite(rzn)) {
+            s.status = kNumerical;
+            s.done = 1;
+            s_beta = 0;
+        } else {
+            s_beta = rzn / s.rz;
+            s.rz = rzn;
+        }
+    }
+    __syncthreads();
+    const double bt = s_beta;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) p[i] = z[i] + bt * p[i];
+}
+
+// out_b = (a.c)_b for every problem
+__global__ void __launch_bounds__(kThreads) k_seg_dot(const double *__restrict__ a, const double *__restrict__ c,
+                                                      const int64_t *__restrict__ off, double *__restrict__ out) {
+    const int b = blockIdx.x;
+    const int64_t lo = off[b], hi = off[b + 1];
+    double acc = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) acc += a[i] * c[i];
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) out[b] = t;
+}
+
+__global__ void k_sub(double *__restrict__ r, const double *__restrict__ f, const double *__restrict__ ax, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = f[i] - ax[i];
+}
+
+__global__ void k_add(double *__restrict__ y, const double *__restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+__global__ void k_gather(const double *__restrict__ v, const int32_t *__restrict__ perm, int64_t n,
+                         double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v[perm[i]];
+}
+
+__global__ void k_scatter(const double *__restrict__ v, const int32_t *__restrict__ perm, int64_t n,
+                          double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = v[i];
+}
+
+std::vector<double> read_seg_dots(const double *a, const double *c, const int64_t *off, int B, DevMem &tmp,
+                                  cudaStream_t s) {
+    k_seg_dot<<<B, kThreads, 0, s>>>(a, c, off, tmp.as<double>());
+    IMQ_LAUNCH_CHECK();
+    std::vector<double> h(B);
+    IMQ_CUDA(cudaMemcpyAsync(h.data(), tmp.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+}  // namespace
+
+void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o,
+                      imq_cg_info *info, double *rel_out, int32_t *iters_out, cudaStream_t s) {
+    const int64_t n = P.N;
+    const int B = P.nprob;
+    if (o.inner_operator == IMQ_OPERATOR_DENSE_F64 || o.residual == IMQ_RESIDUAL_DENSE_F64)
+        fail(IMQ_UNSUPPORTED, "imq_cg_solve: the dense product couples the problems of a batched plan");
+    if (o.residual_plan) fail(IMQ_UNSUPPORTED, "imq_cg_solve: residual_plan is not supported on batched plans");
+    ensure_ops(P, false, s);
+    ensure_ops(P, true, s);   // the FP64 residual product
+    if (o.precond == IMQ_PRECOND_SCHWARZ)
+        schwarz_setup(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    const bool pre = o.precond == IMQ_PRECOND_SCHWARZ;
+    const bool f64op = o.inner_operator == IMQ_OPERATOR_FAST_F64;
+
+    DevMem x, xb, r, p, q, z, u32, b32, St, tmp, off, xs, fs, ax;
+    for (DevMem *d : {&x, &xb, &r, &p, &q, &xs, &fs, &ax}) d->alloc(8 * n);
+    if (pre) z.alloc(8 * n);
+    u32.alloc(4 * n);
+    b32.alloc(4 * n);
+    St.alloc(sizeof(BScalars) * B);
+    tmp.alloc(sizeof(double) * B);
+    off.alloc(sizeof(int64_t) * (B + 1));
+    IMQ_CUDA(cudaMemcpyAsync(off.ptr, P.prob_off.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, s));
+    BScalars *S = St.as<BScalars>();
+    const int64_t *doff = off.as<int64_t>();
+    double *zp = pre ? z.as<double>() : r.as<double>();
+    const unsigned g = blocks_for(n, 256);
+    const unsigned gs = std::min<unsigned>(g, 4 * 152);
+
+    IMQ_CUDA(cudaMemsetAsync(u32.ptr, 0, 4 * n, s));
+    IMQ_CUDA(cudaMemsetAsync(p.ptr, 0, 8 * n, s));
+    if (f64op) fmm_apply<double>(P, p.as<double>(), q.as<double>(), 1, s);
+    else fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, s);
+    IMQ_CUDA(cudaStreamSynchronize(s));
+
+    cudaStream_t cs;
+    IMQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+    };
+    IMQ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int it = 0; it < kIterPerGraph; ++it) {
+            if (f64op) {
+                fmm_apply<double>(P, p.as<double>(), q.as<double>(), 1, cs);
+                k_alpha<<<B, kThreads, 0, cs>>>(nullptr, p.as<double>(), q.as<double>(), doff, S);
+            } else {
+                k_to_f32<<<gs, 256, 0, cs>>>(p.as<double>(), u32.as<float>(), n);
+                fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, cs);
+                k_alpha<<<B, kThreads, 0, cs>>>(b32.as<float>(), p.as<double>(), q.as<double>(), doff, S);
+            }
+            k_update<<<B, kThreads, 0, cs>>>(x.as<double>(), r.as<double>(), p.as<double>(), q.as<double>(),
+                                             xb.as<double>(), doff, S);
+            if (pre) schwarz_apply(P, P.schwarz, r.as<double>(), zp, P.c, n, nullptr, cs);
+            k_beta<<<B, kThreads, 0, cs>>>(r.as<double>(), zp, p.as<double>(), doff, S);
+        }
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        cleanup();
+        throw;
+    }
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) {
+        cleanup();
+        IMQ_CUDA(ce);
+    }
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+        cleanup();
+        IMQ_CUDA(ce);
+    }
+
+    const auto t0 = std::chrono::steady_clock::now();
+    int total_iter = 0, outer_done = 0, final_status = kConverged;
+    double worst_rel = 0;
+    std::vector<BScalars> h(B);
+    try {
+        for (int rhs = 0; rhs < nrhs; ++rhs) {
+            const double *f = f_dev + (size_t)rhs * n;
+            double *xo = x_dev + (size_t)rhs * n;
+            k_gather<<<g, 256, 0, s>>>(f, P.perm.as<int32_t>(), n, fs.as<double>());
+            if (o.x0_given) k_gather<<<g, 256, 0, s>>>(xo, P.perm.as<int32_t>(), n, xs.as<double>());
+            else IMQ_CUDA(cudaMemsetAsync(xs.ptr, 0, 8 * n, s));
+            IMQ_LAUNCH_CHECK();
+            const std::vector<double> ff = read_seg_dots(fs.as<double>(), fs.as<double>(), doff, B, tmp, s);
+            std::vector<double> rel(B, 1.0);
+            std::vector<int> status(B, kMaxIter), iters(B, 0);
+            const int max_outer = std::max(0, o.refine_steps);
+            auto true_residual = [&]() {
+                fmm_apply<double>(P, xs.as<double>(), ax.as<double>(), 1, s);
+                k_sub<<<gs, 256, 0, s>>>(r.as<double>(), fs.as<double>(), ax.as<double>(), n);
+                IMQ_LAUNCH_CHECK();
+                return read_seg_dots(r.as<double>(), r.as<double>(), doff, B, tmp, s);
+            };
+            for (int outer = 0; outer <= max_outer; ++outer) {
+                std::vector<double> rr0;
+                if (outer == 0 && !o.x0_given) {
+                    IMQ_CUDA(cudaMemcpyAsync(r.ptr, fs.ptr, 8 * n, cudaMemcpyDeviceToDevice, s));
+                    rr0 = ff;
+                } else {
+                    rr0 = true_residual();
+                }
+                bool any = false;
+                for (int b = 0; b < B; ++b) {
+                    const double fn = std::sqrt(ff[b]);
+                    rel[b] = fn > 0 ? std::sqrt(rr0[b]) / fn : 0.0;
+                    if (status[b] == kNumerical) continue;
+                    if (!std::isfinite(rel[b])) status[b] = kNumerical;
+                    else if (rel[b] <= o.rtol) status[b] = kConverged;
+                    else {
+                        status[b] = kMaxIter;
+                        if (iters[b] < o.maxit) any = true;
+                    }
+                }
+                if (!any || (outer == max_outer && outer > 0)) break;
+                IMQ_CUDA(cudaMemsetAsync(x.ptr, 0, 8 * n, s));
+                IMQ_CUDA(cudaMemsetAsync(xb.ptr, 0, 8 * n, s));
+                std::vector<double> rz = rr0;
+                if (pre) {
+                    schwarz_apply(P, P.schwarz, r.as<double>(), zp, P.c, n, nullptr, s);
+                    rz = read_seg_dots(r.as<double>(), zp, doff, B, tmp, s);
+                }
+                IMQ_CUDA(cudaMemcpyAsync(p.ptr, zp, 8 * n, cudaMemcpyDeviceToDevice, s));
+                for (int b = 0; b < B; ++b) {
+                    BScalars &e = h[b];
+                    e = BScalars{};
+                    const bool active = status[b] == kMaxIter && iters[b] < o.maxit;
+                    const double inner_rtol =
+                        max_outer > 0 ? std::max(o.inner_rtol, std::min(0.5, 0.5 * o.rtol / rel[b]))
+                                      : 0.5 * o.rtol / rel[b];
+                    e.rz = rz[b];
+                    e.rr = rr0[b];
+                    e.rr_best = rr0[b];
+                    e.rr_target = inner_rtol * inner_rtol * rr0[b];
+                    e.maxit = o.maxit - iters[b];
+                    e.done = active ? 0 : 1;
+                    e.status = active ? kRunning : kConverged;
+                }
+                IMQ_CUDA(cudaMemcpyAsync(S, h.data(), sizeof(BScalars) * B, cudaMemcpyHostToDevice, s));
+                for (;;) {
+                    IMQ_CUDA(cudaGraphLaunch(exec, s));
+                    IMQ_CUDA(cudaMemcpyAsync(h.data(), S, sizeof(BScalars) * B, cudaMemcpyDeviceToHost, s));
+                    IMQ_CUDA(cudaStreamSynchronize(s));
+                    bool all = true;
+                    for (int b = 0; b < B && all; ++b) all = h[b].done != 0;
+                    if (all) break;
+                }
+                k_add<<<gs, 256, 0, s>>>(xs.as<double>(), xb.as<double>(), n);
+                IMQ_LAUNCH_CHECK();
+                outer_done = std::max(outer_done, outer + 1);
+                for (int b = 0; b < B; ++b) {
+                    iters[b] += h[b].iter;
+                    if (h[b].status == kNumerical) status[b] = kNumerical;
+                }
+                if (max_outer == 0) {
+                    const std::vector<double> rr = true_residual();
+                    for (int b = 0; b < B; ++b) {
+                        const double fn = std::sqrt(ff[b]);
+                        rel[b] = fn > 0 ? std::sqrt(rr[b]) / fn : 0.0;
+                        if (status[b] != kNumerical) status[b] = rel[b] <= o.rtol ? kConverged : kMaxIter;
+                    }
+                    break;
+                }
+            }
+            k_scatter<<<g, 256, 0, s>>>(xs.as<double>(), P.perm.as<int32_t>(), n, xo);
+            IMQ_LAUNCH_CHECK();
+            IMQ_CUDA(cudaStreamSynchronize(s));
+            double rhs_worst = 0;
+            int rhs_iter = 0;
+            for (int b = 0; b < B; ++b) {
+                rhs_worst = std::max(rhs_worst, rel[b]);
+                rhs_iter = std::max(rhs_iter, iters[b]);
+                if (status[b] != kConverged) final_status = status[b] == kNumerical ? kNumerical
+                                                          : (final_status == kNumerical ? kNumerical : kMaxIter);
+                if (rel_out) rel_out[(size_t)rhs * B + b] = rel[b];
+                if (iters_out) iters_out[(size_t)rhs * B + b] = iters[b];
+            }
+            total_iter += rhs_iter;
+            worst_rel = std::max(worst_rel, rhs_worst);
+            if (info && rhs < IMQ_CG_MAX_RHS_INFO) info->rel_residual[rhs] = rhs_worst;
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+        info->iterations = total_iter;
+        info->outer_steps = outer_done;
+        info->max_rel_residual = worst_rel;
+        info->seconds = secs;
+        info->status = final_status == kConverged ? IMQ_OK
+                                                  : (final_status == kNumerical ? IMQ_NUMERICAL : IMQ_NOT_CONVERGED);
+    }
+    if (final_status == kNumerical) fail(IMQ_NUMERICAL, "imq_cg_solve: non-finite value or breakdown in CG");
+    if (final_status != kConverged)
+        fail(IMQ_NOT_CONVERGED, "imq_cg_solve: tolerance not reached; coef holds the best iterate");
+}
+
+}  // namespace imq

@@ -27,7 +27,8 @@ __global__ void k_far_dz(int nleaf, const int32_t *__restrict__ leaves, const in
                          const double2 *__restrict__ centre, const float2 *__restrict__ loc,
                          const double2 *__restrict__ pos, const int32_t *__restrict__ woff,
                          const int32_t *__restrict__ witems, const T *__restrict__ M, const T *__restrict__ Lodd,
-                         const T *__restrict__ dzc, int Ke, int Ko, int p, double S, T c, T *__restrict__ bs) {
+                         const T *__restrict__ dzc, int Ke, int Ko, int p, double S, ShapeC shape,
+                         T *__restrict__ bs) {
     __shared__ T tab2[(IMQ_MAX_P + 2) * (IMQ_MAX_P + 2)], tabi[(IMQ_MAX_P + 2) * (IMQ_MAX_P + 2)];
     fill_recurrence_tables<T>(tab2, tabi, p + 1);
     __syncthreads();
@@ -39,6 +40,7 @@ __global__ void k_far_dz(int nleaf, const int32_t *__restrict__ leaves, const in
     const double2 cb = centre[b];
     const T hb = box_side<T>(S, level[b]);
     const T inv_h = (T)1 / hb;
+    const T c = (T)shape.of(b);
     const T *Lb = Lodd + (int64_t)b * Ko;
     for (int i = begin[b] + lane; i < end[b]; i += 32) {
         T wx, wy;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(32 * kDzWarps) k_p2p_dz(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
     const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-    const double2 *__restrict__ pos, const T *__restrict__ u, T c, T *__restrict__ bs) {
+    const double2 *__restrict__ pos, const T *__restrict__ u, ShapeC shape, T *__restrict__ bs) {
     __shared__ T tgx[kDzWarps][32], tgy[kDzWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int widx = blockIdx.x * kDzWarps + w;
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(32 * kDzWarps) k_p2p_dz(
     const int tb = begin[b], nt = end[b] - tb;
     const int u0 = uoffs[b], u1 = uoffs[b + 1];
     const int St = utot[b];
+    const T c = (T)shape.of(b);
     const T c2 = c * c;
     for (int tc = 0; tc < nt; tc += 32) {
         const int ntc = min(32, nt - tc);
@@ -211,6 +214,7 @@ void upload_pad(DevMem &dst, const std::vector<double> &src, size_t blocks, int 
 }
 
 void ensure_ops_dz(Plan &P, bool fp64, cudaStream_t s) {
+    if (P.nprob > 1) fail(IMQ_UNSUPPORTED, "the c-derivative product is not available on batched plans");
     ensure_ops(P, fp64, s);
     TypedOps &O = fp64 ? P.ops64 : P.ops32;
     if (O.dz_ready) return;
@@ -275,12 +279,12 @@ int fmm_apply_dz(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s) {
         k_far_dz<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
             P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
             P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
-            P.W.items.as<int32_t>(), M, Lo, O.dzc.as<T>(), Ke, Ko, P.p, P.side, (T)P.c, b);
+            P.W.items.as<int32_t>(), M, Lo, O.dzc.as<T>(), Ke, Ko, P.p, P.side, P.shape(), b);
         IMQ_LAUNCH_CHECK();
         k_p2p_dz<T><<<(unsigned)((P.nleaf + kDzWarps - 1) / kDzWarps), 32 * kDzWarps, 0, s>>>(
             P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.U.off.as<int32_t>(),
             P.U.items.as<int32_t>(), P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
-            P.loc.as<float2>(), P.pos.as<double2>(), u, (T)P.c, b);
+            P.loc.as<float2>(), P.pos.as<double2>(), u, P.shape(), b);
         IMQ_LAUNCH_CHECK();
         launches += 2;
     }

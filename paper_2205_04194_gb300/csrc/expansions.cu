@@ -142,15 +142,22 @@ __global__ void k_l2l(int lb, const int32_t *__restrict__ parent, const uint32_t
 // read through the cache hierarchy.
 template <class T>
 __global__ void k_m2l_direct(int lb, int nl, const int32_t *__restrict__ vtab, const T *__restrict__ M,
-                             T *__restrict__ L, const T *__restrict__ ops, int Kin, int Kout) {
+                             T *__restrict__ L, const T *__restrict__ ops, int Kin, int Kout,
+                             const int32_t *__restrict__ box_opslot) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= (int64_t)nl * Kout) return;
     const int b = lb + (int)(g / Kout), row = (int)(g % Kout);
+    const T *opb = ops;
+    if (box_opslot) {   // batched plans: operators of the box's (problem, level)
+        const int sl = box_opslot[b];
+        if (sl < 0) return;
+        opb = ops + (size_t)sl * kOffsetClasses * Kin * Kout;
+    }
     T acc = 0;
     for (int o = 0; o < kOffsetClasses; ++o) {
         const int s = vtab[(int64_t)kOffsetClasses * b + o];
         if (s < 0) continue;
-        const T *op = ops + (size_t)o * Kin * Kout + row;
+        const T *op = opb + (size_t)o * Kin * Kout + row;
         const T *Ms = M + (int64_t)s * Kin;
         for (int i = 0; i < Kin; ++i) acc += op[(size_t)i * Kout] * Ms[i];
     }
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(32 * kP2LWarps) k_p2l(
     int nxb, const int32_t *__restrict__ xboxes, const int32_t *__restrict__ xoff, const int32_t *__restrict__ xitems,
     const int32_t *__restrict__ xcum, const int32_t *__restrict__ xtot, const int32_t *__restrict__ begin,
     const int32_t *__restrict__ level, const double2 *__restrict__ centre, const float2 *__restrict__ loc,
-    const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p, double S, T c) {
+    const double2 *__restrict__ pos, const T *__restrict__ u, T *__restrict__ L, int K, int p, double S, ShapeC shape) {
     extern __shared__ __align__(16) unsigned char smraw_p2l[];
     T *tab2 = reinterpret_cast<T *>(smraw_p2l);
     T *tabi = tab2 + (IMQ_MAX_P + 1) * (IMQ_MAX_P + 1);
@@ -214,6 +221,7 @@ __global__ void __launch_bounds__(32 * kP2LWarps) k_p2l(
     const int b = xboxes[widx];
     const T h = box_side<T>(S, level[b]);
     const double2 cb = centre[b];
+    const T c = (T)shape.of(b);
     const int x0 = xoff[b], x1 = xoff[b + 1], St = xtot[b];
     T *row = acc + lane * Kpad;
     int r = x0;
@@ -276,7 +284,7 @@ void p2l_launch_impl(Plan &P, const T *u, T *L, int K, cudaStream_t s) {
     k_p2l<T, PAR><<<(unsigned)((P.nxbox + kP2LWarps - 1) / kP2LWarps), 32 * kP2LWarps, smem, s>>>(
         P.nxbox, P.xboxes.as<int32_t>(), P.X.off.as<int32_t>(), P.X.items.as<int32_t>(), P.xcum.as<int32_t>(),
         P.xtot.as<int32_t>(), P.begin.as<int32_t>(), P.level.as<int32_t>(), P.centre.as<double2>(),
-        P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, P.p, P.side, (T)P.c);
+        P.loc.as<float2>(), P.pos.as<double2>(), u, L, K, P.p, P.side, P.shape());
     IMQ_LAUNCH_CHECK();
 }
 
@@ -287,7 +295,7 @@ __global__ void k_far(int nleaf, const int32_t *__restrict__ leaves, const int32
                       const double2 *__restrict__ centre, const float2 *__restrict__ loc,
                       const double2 *__restrict__ pos, const int32_t *__restrict__ woff,
                       const int32_t *__restrict__ witems, const T *__restrict__ M, const T *__restrict__ L,
-                      const T *__restrict__ coef, int K, int p, double S, T c, T *__restrict__ bs) {
+                      const T *__restrict__ coef, int K, int p, double S, ShapeC shape, T *__restrict__ bs) {
     __shared__ T tab2[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)], tabi[(IMQ_MAX_P + 1) * (IMQ_MAX_P + 1)];
     fill_recurrence_tables<T>(tab2, tabi, p);
     __syncthreads();
@@ -297,6 +305,7 @@ __global__ void k_far(int nleaf, const int32_t *__restrict__ leaves, const int32
     const int b = leaves[warp];
     const double2 cb = centre[b];
     const T inv_h = (T)1 / box_side<T>(S, level[b]);
+    const T c = (T)shape.of(b);
     const T *Lb = L + (int64_t)b * K;
     for (int i = begin[b] + lane; i < end[b]; i += 32) {
         T wx, wy;
@@ -378,7 +387,8 @@ int64_t Plan::device_bytes() const {
                            &ops32.m2m, &ops32.l2l, &ops32.m2l, &ops32.p2mc, &ops32.M, &ops32.L,
                            &ops64.m2m, &ops64.l2l, &ops64.m2l, &ops64.p2mc, &ops64.M, &ops64.L,
                            &schwarz.patch_off, &schwarz.patch_pts, &schwarz.fac_off, &schwarz.factor,
-                           &schwarz.pt_off, &schwarz.pt_slot, &schwarz.ypatch};
+                           &schwarz.pt_off, &schwarz.pt_slot, &schwarz.ypatch, &box_prob, &prob_c, &pt_prob,
+                           &box_opslot, &m2l_tiles, &m2l_tbox, &xcum, &xtot, &utot, &xboxes};
     for (auto *d : all) t += (int64_t)d->bytes;
     return t;
 }
@@ -388,6 +398,32 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     if (O.ready) return;
     const int K = P.layout.K;
     const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
+    if (P.nprob > 1) {   // batched: shared M2M/L2L, M2L per (problem, level) generated on the device
+        if (P.h_m2m.empty()) {
+            build_m2m_ops(P.layout, P.h_m2m);
+            build_l2l_ops(P.layout, P.h_l2l);
+            p2m_coefficients(P.layout, P.h_p2mc);
+        }
+        const size_t es = fp64 ? sizeof(double) : sizeof(float);
+        if (!fp64 && !P.rec4.ptr) P.rec4.alloc(sizeof(float4) * (size_t)P.N);
+        O.M.alloc(es * (size_t)P.nbox * K);
+        O.L.alloc(es * (size_t)P.nbox * K);
+        if (fp64) {
+            upload<double>(O.m2m, P.h_m2m, s);
+            upload<double>(O.l2l, P.h_l2l, s);
+            upload<double>(O.p2mc, P.h_p2mc, s);
+            generate_m2l_ops<double>(P.layout, P.layout, P.h_slot_hc, K, O.m2l, s);
+        } else {
+            upload<float>(O.m2m, P.h_m2m, s);
+            upload<float>(O.l2l, P.h_l2l, s);
+            upload<float>(O.p2mc, P.h_p2mc, s);
+            const int RR = m2l_tiled_rows(K);
+            if (RR < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
+            generate_m2l_ops<float>(P.layout, P.layout, P.h_slot_hc, 16 * RR, O.m2l, s);
+        }
+        O.ready = true;
+        return;
+    }
     if (P.h_m2m.empty()) {
         build_m2m_ops(P.layout, P.h_m2m);
         build_l2l_ops(P.layout, P.h_l2l);
@@ -484,9 +520,10 @@ template <class T>
 void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kout, cudaStream_t s, int *launches) {
     for (int lev = P.m2l_level_lo; lev <= P.m2l_level_hi; ++lev) {
         const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-        const T *opl = ops + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * Kin * Kout;
-        k_m2l_direct<T><<<blocks_for((int64_t)nl * Kout, 128), 128, 0, s>>>(lb, nl, P.vtab.as<int32_t>(), M, L, opl,
-                                                                             Kin, Kout);
+        const bool batched = P.nprob > 1;
+        const T *opl = batched ? ops : ops + (size_t)(lev - P.m2l_level_lo) * kOffsetClasses * Kin * Kout;
+        k_m2l_direct<T><<<blocks_for((int64_t)nl * Kout, 128), 128, 0, s>>>(
+            lb, nl, P.vtab.as<int32_t>(), M, L, opl, Kin, Kout, batched ? P.box_opslot.as<int32_t>() : nullptr);
         IMQ_LAUNCH_CHECK();
         ++*launches;
     }
@@ -547,7 +584,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
             P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
             P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
-            P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, (T)P.c, b);
+            P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, P.shape(), b);
         IMQ_LAUNCH_CHECK();
         ++launches;
         t1();

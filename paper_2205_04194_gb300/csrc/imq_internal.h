@@ -80,6 +80,17 @@ struct Layout {
     void build(int p_, int parity_ = 0);
 };
 
+// Shape parameter seen by a kernel: one value, or (batched plans) one per problem
+// looked up through the box's problem index.
+struct ShapeC {
+    double c0;
+    const int32_t *box_prob;   // nullptr: every box has c0
+    const double *prob_c;
+#ifdef __CUDACC__
+    __host__ __device__ __forceinline__ double of(int box) const { return box_prob ? prob_c[box_prob[box]] : c0; }
+#endif
+};
+
 constexpr int kOffsetClasses = 40;          // V-list offsets in [-3,3]^2 minus [-1,1]^2
 int offset_class(int dx, int dy);           // -1 for |dx|,|dy| <= 1 or out of range
 void offset_of_class(int k, int *dx, int *dy);
@@ -135,6 +146,17 @@ struct Plan {
     Layout layout;       // multipoles and value locals (n+m even)
     Layout layout_odd;   // locals of the c-derivative (n+m odd)
     int64_t n_nodes = 0; // evaluation plans: the first n_nodes points are nodes, the rest targets
+    int nprob = 1;       // batched plans: independent problems sharing one flattened tree
+    DevMem box_prob;     // int32[nbox] problem of each box (batched plans only)
+    DevMem prob_c;       // double[nprob] shape of each problem (batched plans only)
+    DevMem pt_prob;      // int32[N] problem of each sorted point (batched plans only)
+    std::vector<int64_t> prob_off;   // host: sorted point offsets of the problems [nprob+1]
+    std::vector<double> h_prob_c;
+    DevMem box_opslot;   // int32[nbox] M2L operator slot of each box (batched plans only)
+    std::vector<double2> h_slot_hc;  // (h, c) of each M2L operator slot (batched plans)
+    ShapeC shape() const {
+        return ShapeC{c, nprob > 1 ? box_prob.as<int32_t>() : nullptr, nprob > 1 ? prob_c.as<double>() : nullptr};
+    }
     std::vector<int> level_start;              // boxes of level l: [level_start[l], level_start[l+1])
     // tree, device
     DevMem codes;      // uint32[N] sorted
@@ -196,6 +218,14 @@ void scatter_sorted(const Plan &P, const T *bs, Tout *out, int nrhs, cudaStream_
 void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o, Plan *RP,
               imq_cg_info *info, cudaStream_t s);
 double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s);   // deterministic, synchronises
+void schwarz_setup(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s);
+// z = M r; Sv: per-solve state whose done flag skips the work (nullptr: always run)
+void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, double c, int64_t n, const void *Sv,
+                   cudaStream_t s);
+// cg_batched.cu
+// rel_out / iters_out: host [nrhs][nprob] or nullptr
+void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o,
+                      imq_cg_info *info, double *rel_out, int32_t *iters_out, cudaStream_t s);
 // m2l.cu
 int m2l_tiled_rows(int K);
 void m2l_tiled_launch(const Plan &P, const float *M, float *L, const float *ops, cudaStream_t s, int Kout = 0);
@@ -214,6 +244,12 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 template <class T>
 int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
 void build_m2l_tiles(Plan &P, cudaStream_t s);
+// batch.cu
+template <class T>
+void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,
+                      cudaStream_t s);
+void build_batched_plan(Plan &P, const double *d_points, const std::vector<int64_t> &offs,
+                        const std::vector<double> &cs, bool dups, cudaStream_t s);
 // dense.cu
 void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d_v, void *d_out,
                       int nrhs, imq_dtype dt, cudaStream_t s);

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
     const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-    const float4 *__restrict__ rec, float c2, float *__restrict__ bs, int *err) {
+    const float4 *__restrict__ rec, ShapeC shape, float *__restrict__ bs, int *err) {
     extern __shared__ __align__(128) unsigned char smraw_p2p[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStage &ws = reinterpret_cast<WarpStage *>(smraw_p2p)[w];
@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     const int tb = begin[b], nt = end[b] - tb;
     const int u0 = uoffs[b], u1 = uoffs[b + 1];
     const int St = utot[b];
+    const double cb = shape.of(b);
+    const float c2 = (float)(cb * cb);
     uint32_t phase = 0;
     const bool staged_all = St <= kStageCap;
     if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, begin, uitems, ucum, udelta, rec, lane, err)) return;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
 __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
-    const int32_t *__restrict__ utot, const double2 *__restrict__ pos, const double *__restrict__ u, double c2,
+    const int32_t *__restrict__ utot, const double2 *__restrict__ pos, const double *__restrict__ u, ShapeC shape,
     double *__restrict__ bs) {
     __shared__ double tgx[kP2PWarps][32], tgy[kP2PWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
     const int tb = begin[b], nt = end[b] - tb;
     const int u0 = uoffs[b], u1 = uoffs[b + 1];
     const int St = utot[b];
+    const double c2 = shape.of(b) * shape.of(b);
     for (int tc = 0; tc < nt; tc += 32) {
         const int ntc = min(32, nt - tc);
         if (lane < ntc) {
@@ -298,13 +301,13 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
         k_p2p_f32<<<grid, 32 * kP2PWarps, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
                                                      P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
                                                      P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
-                                                     P.loc.as<float2>(), P.rec4.as<float4>(), (float)(P.c * P.c), bs,
+                                                     P.loc.as<float2>(), P.rec4.as<float4>(), P.shape(), bs,
                                                      device_error_word());
     } else {
         k_p2p_f64<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
                                                   P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
                                                   P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.pos.as<double2>(), u,
-                                                  P.c * P.c, bs);
+                                                  P.shape(), bs);
     }
     IMQ_LAUNCH_CHECK();
 }

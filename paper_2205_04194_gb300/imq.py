@@ -105,6 +105,12 @@ class Plan:
               raise_on_failure=False):
         """imq_cg_solve: coef with A coef = f.  Returns (coef, info dict); info["status"] is the
         imq_status name (IMQ_NOT_CONVERGED keeps the best iterate in coef)."""
+        return self._solve("imq_cg_solve", f, coef, x0, stream, raise_on_failure, None, dict(
+            rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
+            refine_steps=refine_steps, inner_rtol=inner_rtol, residual=residual, residual_plan=residual_plan,
+            operator=operator, schwarz_fp64=schwarz_fp64))
+
+    def _solve(self, entry, f, coef, x0, stream, raise_on_failure, per_problem, kw):
         nrhs = 1 if len(np.shape(f)) == 1 else int(np.shape(f)[0])
         if coef is None:
             coef = _like(f, 0, F64) if x0 is None else (x0.clone() if isinstance(x0, torch.Tensor) else np.array(x0, dtype=np.float64))
@@ -112,29 +118,41 @@ class Plan:
             raise ValueError("pass either coef or x0")
         o = CgOptions()
         _lib.load().imq_cg_default_options(ctypes.byref(o))
-        o.rtol = float(rtol)
-        o.maxit = int(maxit)
-        o.precond = {"none": 0, None: 0, "schwarz": 1}[precond]
-        o.schwarz_nmax = int(schwarz_nmax)
-        o.schwarz_shift = float(schwarz_shift)
-        o.refine_steps = int(refine_steps)
-        o.inner_rtol = float(inner_rtol)
-        o.residual = {"plan": 0, "dense": 1}[residual]
+        o.rtol = float(kw["rtol"])
+        o.maxit = int(kw["maxit"])
+        o.precond = {"none": 0, None: 0, "schwarz": 1}[kw["precond"]]
+        o.schwarz_nmax = int(kw["schwarz_nmax"])
+        o.schwarz_shift = float(kw["schwarz_shift"])
+        o.refine_steps = int(kw["refine_steps"])
+        o.inner_rtol = float(kw["inner_rtol"])
+        o.residual = {"plan": 0, "dense": 1}[kw["residual"]]
         o.x0_given = 1 if x0 is not None else 0
-        o.residual_plan = residual_plan._h if residual_plan is not None else None
-        o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[operator]
-        o.schwarz_fp64 = 1 if schwarz_fp64 else 0
+        rp = kw.get("residual_plan")
+        o.residual_plan = rp._h if rp is not None else None
+        o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[kw["operator"]]
+        o.schwarz_fp64 = 1 if kw["schwarz_fp64"] else 0
         info = CgInfo()
         fp, kf = _buf(f, torch.float64)
         cp, kc = _buf(coef, torch.float64)
-        st = _lib.load().imq_cg_solve(self._h, fp, cp, nrhs, ctypes.byref(o), ctypes.byref(info), _stream(stream))
-        msg = _lib.load().imq_last_error().decode()
+        lib = _lib.load()
+        if per_problem is None:
+            st = lib.imq_cg_solve(self._h, fp, cp, nrhs, ctypes.byref(o), ctypes.byref(info), _stream(stream))
+        else:
+            rel = np.zeros((nrhs, per_problem), dtype=np.float64)
+            its = np.zeros((nrhs, per_problem), dtype=np.int32)
+            st = lib.imq_cg_solve_batched(self._h, fp, cp, nrhs, ctypes.byref(o), ctypes.byref(info),
+                                          ctypes.c_void_p(rel.ctypes.data), ctypes.c_void_p(its.ctypes.data),
+                                          _stream(stream))
+        msg = lib.imq_last_error().decode()
         out = {"status": _lib.status_name(st), "iterations": info.iterations, "outer_steps": info.outer_steps,
                "max_rel_residual": info.max_rel_residual, "seconds": info.seconds,
                "rel_residual": list(info.rel_residual)[:min(nrhs, 16)], "message": msg}
+        if per_problem is not None:
+            out["problem_rel_residual"] = rel
+            out["problem_iterations"] = its
         # IMQ_NOT_CONVERGED (5) and IMQ_NUMERICAL (6) still return the best iterate and its info
         if st != 0 and (raise_on_failure or st not in (5, 6)):
-            raise ImqError(st, "imq_cg_solve", msg)
+            raise ImqError(st, entry, msg)
         return coef, out
 
     def matvec_dc(self, v, out=None, stream=None):
@@ -238,6 +256,49 @@ class EvalPlan(Plan):
         return self._eval("imq_evaluate_dc", coef, self.n_nodes, self.n_targets, out, stream)
 
 
+class BatchedPlan(Plan):
+    """imq_plan_batched: independent problems (points_b, c_b) in one flattened tree."""
+
+    def __init__(self, points_list, c_list, p: int, leaf: int, domain=None, stream=None):
+        self._h = ctypes.c_void_p(0)
+        sizes = [int(np.shape(x)[0]) for x in points_list]
+        offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum(sizes)
+        if all(isinstance(x, torch.Tensor) and x.is_cuda for x in points_list):
+            pts = torch.cat([x.to(torch.float64) for x in points_list]).contiguous()
+        else:
+            pts = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in points_list]))
+        cs = np.ascontiguousarray(np.asarray(c_list, dtype=np.float64))
+        pp, kp = _buf(pts, torch.float64)
+        opt = ImqOptions()
+        opt.struct_size = ctypes.sizeof(ImqOptions)
+        if domain is not None:
+            opt.has_domain = 1
+            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+        call("imq_plan_batched", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes),
+             ctypes.c_void_p(cs.ctypes.data), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
+             ctypes.byref(self._h))
+        self.n = int(offs[-1])
+        self.offsets = offs
+        self.c_list = cs
+        self.c = float(cs[0])
+        self.p, self.leaf = int(p), int(leaf)
+
+    @property
+    def n_problems(self) -> int:
+        return len(self.c_list)
+
+    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
+              schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, x0=None, operator="fast_f32",
+              schwarz_fp64=False, stream=None, raise_on_failure=False):
+        """imq_cg_solve_batched: every problem's system at once, per-problem CG scalars.
+        info adds "problem_rel_residual" and "problem_iterations" ([nrhs, n_problems])."""
+        return self._solve("imq_cg_solve_batched", f, coef, x0, stream, raise_on_failure, self.n_problems, dict(
+            rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
+            refine_steps=refine_steps, inner_rtol=inner_rtol, residual="plan", residual_plan=None,
+            operator=operator, schwarz_fp64=schwarz_fp64))
+
+
 def dense_matvec(points, c: float, v, out=None, stream=None):
     """imq_dense_matvec: b = A v over all N^2 pairs (the plain product)."""
     code = _dtype_code(v)
@@ -273,4 +334,4 @@ def version() -> str:
     return _lib.load().imq_version().decode()
 
 
-__all__ = ["Plan", "EvalPlan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
+__all__ = ["Plan", "EvalPlan", "BatchedPlan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
