@@ -72,8 +72,18 @@ typedef struct imq_options {
     int32_t has_domain;        /* 1: use (x0, y0, side) as the square D (Section 2.2) */
     double x0, y0, side;       /*    otherwise D is the exact bounding square          */
     int32_t check_duplicates;  /* 1: imq_plan fails with IMQ_DUPLICATE_POINTS on equal points */
-    int32_t reserved[7];
+    int32_t m2l_kernel;        /* imq_m2l_kernel: how the FP32 product runs M2L             */
+    int32_t reserved[6];
 } imq_options;
+
+/* M2L kernel of the FP32 product.  AUTO takes the tensor cores when the
+ * expansion fits them (K, K_out <= 256 reals), else the CUDA cores.
+ * TENSOR fails the plan with IMQ_UNSUPPORTED when it does not fit. */
+typedef enum imq_m2l_kernel {
+    IMQ_M2L_AUTO = 0,
+    IMQ_M2L_CUDA_CORES = 1,    /* register-tiled FP32 FMA                          */
+    IMQ_M2L_TENSOR = 2         /* tcgen05 kind::tf32, 3xTF32 split, TMEM accumulator */
+} imq_m2l_kernel;
 
 /* ------------------------------------------------------------------------- *
  * imq_plan -- build the quadtree, its interaction lists and the operators.

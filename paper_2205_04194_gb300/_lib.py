@@ -30,7 +30,7 @@ class ImqError(RuntimeError):
 
 class ImqOptions(ctypes.Structure):
     _fields_ = [("struct_size", I32), ("has_domain", I32), ("x0", D), ("y0", D), ("side", D),
-                ("check_duplicates", I32), ("reserved", I32 * 7)]
+                ("check_duplicates", I32), ("m2l_kernel", I32), ("reserved", I32 * 6)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -140,7 +140,7 @@ const char *imq_version(void) { return "imq-gb300 0.1 (sm_103a)"; }
 namespace {
 
 void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
-                     double &side, bool &dups) {
+                     double &side, bool &dups, int *m2l_kernel = nullptr) {
     if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
     if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
     if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
@@ -160,6 +160,9 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
             side = opt->side;
         }
         dups = opt->check_duplicates != 0;
+        if (opt->m2l_kernel < IMQ_M2L_AUTO || opt->m2l_kernel > IMQ_M2L_TENSOR)
+            fail(IMQ_INVALID_ARG, "imq_plan: unknown m2l_kernel");
+        if (m2l_kernel) *m2l_kernel = opt->m2l_kernel;
     }
 }
 
@@ -167,7 +170,8 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
                         const imq_options *opt, cudaStream_t s) {
     double x0, y0, side;
     bool dups;
-    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups);
+    int m2lk = IMQ_M2L_AUTO;
+    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk);
     check_device();
     auto *h = new imq_plan_s;
     try {
@@ -181,6 +185,7 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
         P.x0 = x0;
         P.y0 = y0;
         P.side = side;
+        P.m2l_kernel = m2lk;
         P.layout.build(p, 0);
         build_tree(P, d_points, s, dups);
         ensure_ops(P, false, s);
@@ -250,7 +255,8 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
         const int64_t N = offs[nprob];
         double x0, y0, side;
         bool dups;
-        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups);
+        int m2lk = IMQ_M2L_AUTO;
+        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk);
         check_device();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
@@ -281,6 +287,7 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
             P.x0 = x0;
             P.y0 = y0;
             P.side = side;
+            P.m2l_kernel = m2lk;
             P.layout.build(p, 0);
             build_batched_plan(P, static_cast<const double *>(pts.ptr), offs, cs, dups, s);
             ensure_ops(P, false, s);

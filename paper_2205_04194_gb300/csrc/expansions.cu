@@ -393,6 +393,17 @@ int64_t Plan::device_bytes() const {
     return t;
 }
 
+// FP32 M2L on the tensor cores unless the plan asks for the CUDA cores
+static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
+    const int K = P.layout.K;
+    const bool fits = m2l_umma_supported(K, K);
+    if (P.m2l_kernel == IMQ_M2L_TENSOR && !fits)
+        fail(IMQ_UNSUPPORTED, "imq_plan: the expansion does not fit the tensor-core M2L");
+    if (P.m2l_kernel == IMQ_M2L_CUDA_CORES || !fits) return;
+    m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, s);
+    O.umma = true;
+}
+
 void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     TypedOps &O = fp64 ? P.ops64 : P.ops32;
     if (O.ready) return;
@@ -420,6 +431,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
             const int RR = m2l_tiled_rows(K);
             if (RR < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
             generate_m2l_ops<float>(P.layout, P.layout, P.h_slot_hc, 16 * RR, O.m2l, s);
+            prepare_tensor_m2l(P, O, (int)P.h_slot_hc.size(), s);
         }
         O.ready = true;
         return;
@@ -457,6 +469,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
             for (int i = 0; i < K; ++i)
                 for (int r = 0; r < K; ++r) pad[(blk * K + i) * Kp + r] = P.h_m2l[(blk * K + i) * K + r];
         upload<float>(O.m2l, pad, s);
+        prepare_tensor_m2l(P, O, std::max(1, nlev), s);
     }
     O.ready = true;
 }
@@ -561,7 +574,10 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         // interaction: M2L per level, P2L over X lists
         t0(kPhM2L);
         if constexpr (std::is_same<T, float>::value) {
-            if (P.n_m2l_tiles > 0) {
+            if (P.n_m2l_tiles > 0 && O.umma) {
+                m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), K, s);
+                launches += 2;
+            } else if (P.n_m2l_tiles > 0) {
                 m2l_tiled_launch(P, M, L, m2l, s);
                 ++launches;
             }

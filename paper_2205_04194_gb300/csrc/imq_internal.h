@@ -117,6 +117,9 @@ struct TypedOps {        // operator set in one precision
     // derivative in c (odd-parity locals): M2L even->odd, L2L odd, d/dz L2P coefficients
     DevMem m2l_odd, l2l_odd, dzc, Lodd;
     bool dz_ready = false;
+    // tensor-core M2L (FP32 only): swizzled tf32 hi/lo operator images, packed multipoles
+    DevMem m2l_img, Mpk;
+    bool umma = false;
 };
 
 // Additive Schwarz preconditioner over leaf neighbourhood patches (cg.cu).
@@ -146,6 +149,7 @@ struct Plan {
     Layout layout;       // multipoles and value locals (n+m even)
     Layout layout_odd;   // locals of the c-derivative (n+m odd)
     int64_t n_nodes = 0; // evaluation plans: the first n_nodes points are nodes, the rest targets
+    int m2l_kernel = 0;  // imq_m2l_kernel
     int nprob = 1;       // batched plans: independent problems sharing one flattened tree
     DevMem box_prob;     // int32[nbox] problem of each box (batched plans only)
     DevMem prob_c;       // double[nprob] shape of each problem (batched plans only)
@@ -244,6 +248,10 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 template <class T>
 int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
 void build_m2l_tiles(Plan &P, cudaStream_t s);
+// m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
+bool m2l_umma_supported(int K, int Kout);
+void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s);
+void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, int Kout, cudaStream_t s);
 // batch.cu
 template <class T>
 void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,

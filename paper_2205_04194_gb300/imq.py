@@ -54,20 +54,29 @@ def _like(v, n_total: int, code: int):
     return np.empty(np.shape(v), dtype=np.float32 if code == F32 else np.float64)
 
 
+M2L_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
+
+
+def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto"):
+    opt = ImqOptions()
+    opt.struct_size = ctypes.sizeof(ImqOptions)
+    if domain is not None:
+        opt.has_domain = 1
+        opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+    opt.check_duplicates = 1 if check_duplicates else 0
+    opt.m2l_kernel = M2L_KERNELS[m2l_kernel]
+    return opt
+
+
 class Plan:
     """imq_plan: quadtree, interaction lists and operators for (points, c, p, leaf)."""
 
     def __init__(self, points, c: float, p: int, leaf: int, domain=None,
-                 check_duplicates: bool = False, stream=None):
+                 check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto"):
         self._h = ctypes.c_void_p(0)
         pts_ptr, keep = _buf(points, torch.float64)
         n = int(np.shape(points)[0])
-        opt = ImqOptions()
-        opt.struct_size = ctypes.sizeof(ImqOptions)
-        if domain is not None:
-            opt.has_domain = 1
-            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
-        opt.check_duplicates = 1 if check_duplicates else 0
+        opt = _plan_options(domain, check_duplicates, m2l_kernel)
         call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
         del keep
@@ -214,16 +223,13 @@ class Plan:
 class EvalPlan(Plan):
     """imq_plan_eval: one tree over nodes and evaluation targets (interpolant of Eq. (2))."""
 
-    def __init__(self, nodes, targets, c: float, p: int, leaf: int, domain=None, stream=None):
+    def __init__(self, nodes, targets, c: float, p: int, leaf: int, domain=None, stream=None,
+                 m2l_kernel: str = "auto"):
         self._h = ctypes.c_void_p(0)
         np_, kn = _buf(nodes, torch.float64)
         tp_, kt = _buf(targets, torch.float64)
         nn, nt = int(np.shape(nodes)[0]), int(np.shape(targets)[0])
-        opt = ImqOptions()
-        opt.struct_size = ctypes.sizeof(ImqOptions)
-        if domain is not None:
-            opt.has_domain = 1
-            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+        opt = _plan_options(domain, False, m2l_kernel)
         call("imq_plan_eval", np_, nn, tp_, nt, float(c), int(p), int(leaf), ctypes.byref(opt),
              _stream(stream), ctypes.byref(self._h))
         self.n = nn + nt
@@ -259,7 +265,8 @@ class EvalPlan(Plan):
 class BatchedPlan(Plan):
     """imq_plan_batched: independent problems (points_b, c_b) in one flattened tree."""
 
-    def __init__(self, points_list, c_list, p: int, leaf: int, domain=None, stream=None):
+    def __init__(self, points_list, c_list, p: int, leaf: int, domain=None, stream=None,
+                 m2l_kernel: str = "auto"):
         self._h = ctypes.c_void_p(0)
         sizes = [int(np.shape(x)[0]) for x in points_list]
         offs = np.zeros(len(sizes) + 1, dtype=np.int64)
@@ -270,11 +277,7 @@ class BatchedPlan(Plan):
             pts = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in points_list]))
         cs = np.ascontiguousarray(np.asarray(c_list, dtype=np.float64))
         pp, kp = _buf(pts, torch.float64)
-        opt = ImqOptions()
-        opt.struct_size = ctypes.sizeof(ImqOptions)
-        if domain is not None:
-            opt.has_domain = 1
-            opt.x0, opt.y0, opt.side = (float(v) for v in domain)
+        opt = _plan_options(domain, False, m2l_kernel)
         call("imq_plan_batched", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes),
              ctypes.c_void_p(cs.ctypes.data), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))

@@ -106,3 +106,40 @@ def test_fast_full_size_clustered_1m_sampled_rows():
     rows = np.random.default_rng(0).choice(wl.n, 2048, replace=False)
     ref = dense.matvec_rows(wl.points, wl.c, wl.v, rows)
     assert rel2(b[rows], ref) < 1e-6
+
+
+@pytest.mark.parametrize("p,leaf", [(8, 32), (12, 64), (16, 40)])
+def test_tensor_core_m2l_matches_cuda_core_m2l_and_oracle(p, leaf):
+    """The tcgen05 M2L (3xTF32 split) against the register-tiled FP32 M2L and the
+    FP64 FMM reference on the same tree; p = 16 (K = 153) runs the two-stage pipeline."""
+    import torch
+    imq = _imq()
+    pts = W.clustered_points(2000, 6, 4000, 0.04, 5)
+    c = 0.005
+    v = W.random_vector(pts.shape[0], 13, nrhs=2)
+    tc = imq.Plan(cuda(pts), c, p, leaf, domain=(0.0, 0.0, 1.0), m2l_kernel="tensor")
+    cc = imq.Plan(cuda(pts), c, p, leaf, domain=(0.0, 0.0, 1.0), m2l_kernel="cuda_cores")
+    assert tc.info()["m2l_pairs"] > 1000
+    bt = host(tc.matvec(cuda(v, torch.float32)))
+    bc = host(cc.matvec(cuda(v, torch.float32)))
+    for r in range(2):
+        ofmm = fmm.fmm_matvec(pts, c, v[r], p, leaf, (0.0, 0.0, 1.0))
+        assert rel2(bt[r], bc[r]) < 5e-7
+        assert rel2(bt[r], ofmm) < 1e-6
+    tc.close()
+    cc.close()
+
+
+def test_tensor_core_m2l_batched_matches_cuda_cores():
+    import torch
+    imq = _imq()
+    pts = [W.uniform_points(n, 21, stream=s) for s, n in enumerate((700, 5000, 2300))]
+    cs = [0.02, 0.15, 0.05]
+    a = imq.BatchedPlan([cuda(x) for x in pts], cs, 12, 32, domain=(0.0, 0.0, 1.0), m2l_kernel="tensor")
+    b = imq.BatchedPlan([cuda(x) for x in pts], cs, 12, 32, domain=(0.0, 0.0, 1.0), m2l_kernel="cuda_cores")
+    v = W.random_vector(a.n, 5)
+    ref = host(a.matvec(cuda(v)))      # FP64 product, same tree and truncation: the rounding reference
+    et = rel2(host(a.matvec(cuda(v, torch.float32))), ref)
+    ec = rel2(host(b.matvec(cuda(v, torch.float32))), ref)
+    # c = 0.15 on 5000 points cancels strongly in M2L: both FP32 paths sit near 1e-6 here
+    assert et < 2e-6 and et < 1.5 * ec + 2e-7, (et, ec)
