@@ -407,6 +407,7 @@ static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
 void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     TypedOps &O = fp64 ? P.ops64 : P.ops32;
     if (O.ready) return;
+    if (!fp64) far_fixed_p_prepare(s);
     const int K = P.layout.K;
     const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
     if (P.nprob > 1) {   // batched: shared M2M/L2L, M2L per (problem, level) generated on the device
@@ -555,6 +556,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
     int launches = 0;
     auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
     auto t1 = [&]() { if (tm) tm->stop(s); };
+    bool far_generic = false;
     for (int r = 0; r < nrhs; ++r) {
         const T *u = us + (size_t)r * P.N;
         T *b = bs + (size_t)r * P.N;
@@ -597,11 +599,19 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t1();
         // evaluation: L2P + M2P writes b, P2P adds the near field
         t0(kPhFar);
-        k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
-            P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
-            P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
-            P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, P.shape(), b);
-        IMQ_LAUNCH_CHECK();
+        if constexpr (std::is_same<T, float>::value) {
+            if (far_fixed_p_supported(p)) far_fixed_p_launch(P, M, L, coef, b, s);
+            else far_generic = true;
+        } else {
+            far_generic = true;
+        }
+        if (far_generic) {
+            k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
+                P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
+                P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
+                P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, P.shape(), b);
+            IMQ_LAUNCH_CHECK();
+        }
         ++launches;
         t1();
         t0(kPhP2P);

@@ -1,0 +1,239 @@
+// Evaluation of the far field at the points of each leaf for a compile-time
+// order P, FP32: the local expansion of the leaf (L2P) plus the multipoles of
+// its W list (M2P), the two far-field parts of the paper's Algorithm 1
+// evaluation (the sum over S_p, Section 3).
+//
+// L2P.  Lh_n^m(B) against the regular harmonics of w = (x - c_B)/h in the
+// plane z = 0: only n + m even survive and R_n^m(w) = norm * |w|^{n-m} conj(w)^m,
+// so column m is  Re( conj(w)^m * P_m(|w|^2) )  with a polynomial P_m whose
+// complex coefficients are the leaf's local coefficients times eps_m and the
+// regular normalisation.  The warp builds these complex coefficients once per
+// leaf in its own shared-memory row (read back as broadcasts) and each lane
+// evaluates P_m by Horner's rule with packed f32x2 FMAs (real and imaginary
+// part in one instruction).
+//
+// M2P.  For a source S of the W list, G_n^m(x - c_S) with vertical component c
+// is G_m^m times a real sequence g_n (g_m = 1) that obeys the normalised
+// three-term recurrence in n; column m contributes Re( G_m^m * sum_n g_n Mh_n^m ).
+// The recurrence coefficients live in __constant__ memory, so with P fixed
+// every coefficient is an operand of the FMA that uses it.
+#include <cmath>
+#include <vector>
+
+#include "f32x2.cuh"
+#include "fmm_common.cuh"
+#include "imq_internal.h"
+#include "util.cuh"
+
+namespace imq {
+namespace {
+
+constexpr int kMaxP = IMQ_MAX_P;
+// g_n = A[n][m] * (t a) * g_{n-1} - B[n][m] * a^2 * g_{n-2};  f[m] = sqrt((2m-1)/(2m))
+__constant__ float c_rec_a[(kMaxP + 1) * (kMaxP + 1)];
+__constant__ float c_rec_b[(kMaxP + 1) * (kMaxP + 1)];
+__constant__ float c_fm[kMaxP + 2];
+
+__host__ __device__ constexpr int cnt_col(int P, int m) { return (P - m) / 2 + 1; }     // complex terms of column m
+__host__ __device__ constexpr int cbase(int P, int m) {                                  // first complex index of column m
+    int s = 0;
+    for (int mm = 0; mm < m; ++mm) s += cnt_col(P, mm);
+    return s;
+}
+__host__ __device__ constexpr int rbase(int P, int m) {                                  // first real slot of column m
+    int s = 0;
+    for (int mm = 0; mm < m; ++mm) s += cnt_col(P, mm) * (mm ? 2 : 1);
+    return s;
+}
+__host__ __device__ constexpr int ncplx(int P) { return cbase(P, P + 1); }
+
+constexpr int kFarWarps = 4;
+
+// complex index k -> (first complex index of its column, real slot of its term, m)
+template <int P>
+__device__ __forceinline__ void decode_term(int k, int &m, int &slot) {
+    m = 0;
+    int kb = 0, rb = 0;
+#pragma unroll
+    for (int mm = 1; mm <= P; ++mm)
+        if (k >= cbase(P, mm)) {
+            m = mm;
+            kb = cbase(P, mm);
+            rb = rbase(P, mm);
+        }
+    slot = rb + (k - kb) * (m ? 2 : 1);
+}
+
+template <int P>
+__global__ void __launch_bounds__(32 * kFarWarps, 8) k_far_t(
+    int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
+    const int32_t *__restrict__ level, const double2 *__restrict__ centre, const float2 *__restrict__ loc,
+    const int32_t *__restrict__ woff, const int32_t *__restrict__ witems, const float *__restrict__ M,
+    const float *__restrict__ L, const float *__restrict__ coef, int K, double S, ShapeC shape,
+    float *__restrict__ bs) {
+    constexpr int NC = ncplx(P);
+    __shared__ __align__(8) u64 s_cl[kFarWarps][NC];   // per-warp L2P coefficients
+    __shared__ __align__(8) u64 s_cm[kFarWarps][NC];   // per-warp multipole of the current W source
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * kFarWarps + wib;
+    if (warp >= nleaf) return;
+    u64 *cl = s_cl[wib];
+    u64 *cm = s_cm[wib];
+    const int b = leaves[warp];
+    const double2 cb = centre[b];
+    const float inv_h = 1.f / (float)(S / (double)(1 << level[b]));
+    const float c = (float)shape.of(b);
+    const float c2 = c * c;
+    const float *Lb = L + (int64_t)b * K;
+
+    // complex L2P coefficients of column m, term j: eps_m * norm * (Lr, Li)
+    for (int k = lane; k < NC; k += 32) {
+        int m, slot;
+        decode_term<P>(k, m, slot);
+        const float e = (m ? 2.f : 1.f) * coef[slot];
+        cl[k] = pk2(e * Lb[slot], m ? e * Lb[slot + 1] : 0.f);
+    }
+    __syncwarp();
+
+    const int i0 = begin[b], i1 = end[b];
+    const int we0 = woff[b], we1 = woff[b + 1];
+    for (int base = i0; base < i1; base += 32) {
+        const int i = base + lane;
+        const bool act = i < i1;
+        const float2 lp = act ? loc[i] : make_float2(0.f, 0.f);
+        float phi = 0.f;
+        // ---- L2P
+        {
+            const float ux = lp.x * inv_h, uy = lp.y * inv_h;
+            const float r2 = ux * ux + uy * uy;
+            const u64 R2 = pk2(r2, r2);
+            float zr = 1.f, zi = 0.f;
+#pragma unroll
+            for (int m = 0; m <= P; ++m) {
+                const int k0 = cbase(P, m), J = cnt_col(P, m);
+                u64 pm = cl[k0 + J - 1];
+#pragma unroll
+                for (int j = J - 2; j >= 0; --j) pm = fma2(pm, R2, cl[k0 + j]);
+                float pr, pi;
+                up2(pm, pr, pi);
+                phi = fmaf(zr, pr, fmaf(-zi, pi, phi));
+                const float nr = zr * ux + zi * uy;
+                zi = zi * ux - zr * uy;
+                zr = nr;
+            }
+        }
+        // ---- M2P over the W list
+        for (int e = we0; e < we1; ++e) {
+            const int s = witems[e];
+            const float *Ms = M + (int64_t)s * K;
+            __syncwarp();
+            for (int k = lane; k < NC; k += 32) {
+                int m, slot;
+                decode_term<P>(k, m, slot);
+                cm[k] = pk2(Ms[slot], m ? Ms[slot + 1] : 0.f);
+            }
+            __syncwarp();
+            const double2 cs = centre[s];
+            const float vx = lp.x + (float)(cb.x - cs.x), vy = lp.y + (float)(cb.y - cs.y);
+            const float hs = (float)(S / (double)(1 << level[s]));
+            const float inv = rsqrtf(vx * vx + vy * vy + c2);
+            const float a = hs * inv, t = c * inv;
+            const float ta = t * a, a2 = a * a;
+            const float zr0 = vx * inv * a, zi0 = vy * inv * a;
+            float gr = inv, gi = 0.f;   // G_m^m, from G_0^0
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m <= P; ++m) {
+                if (m > 0) {
+                    const float f = c_fm[m];
+                    const float nr = (gr * zr0 - gi * zi0) * f;
+                    gi = (gr * zi0 + gi * zr0) * f;
+                    gr = nr;
+                }
+                const int k0 = cbase(P, m);
+                u64 sm = cm[k0];   // g_m = 1
+                float g1 = 1.f, g2 = 0.f;
+#pragma unroll
+                for (int n = m + 1; n <= P; ++n) {
+                    const float g = c_rec_a[n * (kMaxP + 1) + m] * ta * g1 - c_rec_b[n * (kMaxP + 1) + m] * a2 * g2;
+                    g2 = g1;
+                    g1 = g;
+                    if (((n + m) & 1) == 0) sm = fma2(pk2(g, g), cm[k0 + (n - m) / 2], sm);
+                }
+                float sr, si;
+                up2(sm, sr, si);
+                const float eps = m ? 2.f : 1.f;
+                acc = fmaf(eps, gr * sr - gi * si, acc);
+            }
+            phi += acc;
+        }
+        if (act) bs[i] = phi;
+    }
+}
+
+std::vector<int> g_tables_ready;   // per device
+
+void upload_tables(cudaStream_t s) {
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    if ((int)g_tables_ready.size() <= dev) g_tables_ready.resize(dev + 1, 0);
+    if (g_tables_ready[dev]) return;
+    std::vector<float> A((kMaxP + 1) * (kMaxP + 1), 0.f), B(A.size(), 0.f), F(kMaxP + 2, 0.f);
+    for (int n = 0; n <= kMaxP; ++n)
+        for (int m = 0; m <= n; ++m) {
+            const double b2 = (double)n * n - (double)m * m;
+            if (b2 <= 0) continue;
+            const double iv = 1.0 / std::sqrt(b2);
+            const double a2 = (double)(n - 1) * (n - 1) - (double)m * m;
+            A[n * (kMaxP + 1) + m] = (float)((2 * n - 1) * iv);
+            B[n * (kMaxP + 1) + m] = (float)(a2 > 0 ? std::sqrt(a2) * iv : 0.0);
+        }
+    for (int m = 1; m <= kMaxP; ++m) F[m] = (float)std::sqrt((2.0 * m - 1.0) / (2.0 * m));
+    IMQ_CUDA(cudaMemcpyToSymbolAsync(c_rec_a, A.data(), sizeof(float) * A.size(), 0, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyToSymbolAsync(c_rec_b, B.data(), sizeof(float) * B.size(), 0, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyToSymbolAsync(c_fm, F.data(), sizeof(float) * F.size(), 0, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    g_tables_ready[dev] = 1;
+}
+
+}  // namespace
+
+bool far_fixed_p_supported(int p) { return p >= 1 && p <= 16; }
+
+void far_fixed_p_prepare(cudaStream_t s) { upload_tables(s); }
+
+void far_fixed_p_launch(const Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s) {
+    const unsigned grid = (unsigned)((P.nleaf + kFarWarps - 1) / kFarWarps);
+    if (grid == 0) return;
+#define IMQ_FAR_CASE(PP)                                                                                        \
+    case PP:                                                                                                   \
+        k_far_t<PP><<<grid, 32 * kFarWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),    \
+                                                    P.end.as<int32_t>(), P.level.as<int32_t>(),                \
+                                                    P.centre.as<double2>(), P.loc.as<float2>(),                \
+                                                    P.W.off.as<int32_t>(), P.W.items.as<int32_t>(), M, L, coef, \
+                                                    P.layout.K, P.side, P.shape(), b);                         \
+        break;
+    switch (P.p) {
+        IMQ_FAR_CASE(1)
+        IMQ_FAR_CASE(2)
+        IMQ_FAR_CASE(3)
+        IMQ_FAR_CASE(4)
+        IMQ_FAR_CASE(5)
+        IMQ_FAR_CASE(6)
+        IMQ_FAR_CASE(7)
+        IMQ_FAR_CASE(8)
+        IMQ_FAR_CASE(9)
+        IMQ_FAR_CASE(10)
+        IMQ_FAR_CASE(11)
+        IMQ_FAR_CASE(12)
+        IMQ_FAR_CASE(13)
+        IMQ_FAR_CASE(14)
+        IMQ_FAR_CASE(15)
+        IMQ_FAR_CASE(16)
+        default: fail(IMQ_UNSUPPORTED, "far field: no fixed-order kernel for this p");
+    }
+#undef IMQ_FAR_CASE
+    IMQ_LAUNCH_CHECK();
+}
+
+}  // namespace imq

@@ -248,6 +248,10 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 template <class T>
 int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
 void build_m2l_tiles(Plan &P, cudaStream_t s);
+// far.cu: L2P + M2P for a compile-time order (FP32)
+bool far_fixed_p_supported(int p);
+void far_fixed_p_prepare(cudaStream_t s);
+void far_fixed_p_launch(const Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s);

@@ -30,8 +30,8 @@ namespace imq {
 namespace {
 
 constexpr int kTB = 128;         // target boxes per tile = MMA M
-constexpr int kThreads = 128;    // thread b gathers and stores target row b
 constexpr int kAStage = 16384;   // 128 rows x 128 bytes, one of hi / lo
+constexpr size_t kStaticSmem = 1024;   // bound on the kernel's static shared memory
 
 struct UmmaDims {
     int K, Kout, KP, NKC, Kn, tcols, stages;
@@ -47,8 +47,8 @@ UmmaDims umma_dims(int K, int Kout) {
     d.KP = 32 * d.NKC;
     d.Kn = (Kout + 15) / 16 * 16;
     d.tcols = (d.Kn + 31) / 32;   // accumulator column groups (NC)
-    d.stages = 3;
-    while (d.stages > 2 && d.smem() + sizeof(int) * kOffsetClasses * (kTB + 1) + 256 > 227 * 1024) --d.stages;
+    d.stages = 4;
+    while (d.stages > 2 && d.smem() + kStaticSmem > 227 * 1024) --d.stages;
     return d;
 }
 
@@ -93,43 +93,82 @@ __global__ void k_m2l_images(const float *__restrict__ ops, int64_t nblk, int K,
     }
 }
 
-// S: shared-memory stages; NC: 32-column groups of the accumulator (Kn <= 32 NC)
+// Warp roles (288 threads):
+//   warps 0-3  drain: thread b owns target row b (TMEM lane b); after each chunk
+//              it adds the chunk's accumulator to FP32 registers, and at the end
+//              writes the target's local coefficients;
+//   warps 4-7  producers: gather the 128 rows of A (hi and lo) by cp.async,
+//              eight threads per 128-byte row, and arrive on the stage's
+//              barrier through cp.async.mbarrier.arrive.noinc; thread 128 also
+//              issues the bulk copy of the operator image;
+//   warp 8     lane 0 issues the 12 MMAs of each chunk into one of two TMEM
+//              accumulators and commits them to the stage's "empty" barrier and
+//              the accumulator's "full" barrier.
+// Barriers: full[S] (129 arrivals + image bytes), empty[S] (MMA commit),
+// acc_full[NA] (MMA commit), acc_empty[NA] (4 drain warps); NA accumulators
+// rotate so that the MMAs of chunk it wait only for the drain of chunk it - NA.
+constexpr int kDrainThreads = 128, kProdThreads = 128;
+constexpr int kThreadsWS = kDrainThreads + kProdThreads + 32;
+
 template <int S, int NC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsWS, 1)
     k_m2l_umma(const int4 *__restrict__ tiles, const int32_t *__restrict__ tbox, const int32_t *__restrict__ vtab,
                const float *__restrict__ Mpk, float *__restrict__ L, const float *__restrict__ img, int Kout, int Kn,
                int NKC, int *err) {
-    constexpr uint32_t kAccCols = NC <= 2 ? 64 : NC <= 4 ? 128 : 256;   // column offset of accumulator 1
-    constexpr uint32_t kTCols = 2 * kAccCols;
+    constexpr uint32_t kAccCols = NC <= 2 ? 64 : NC <= 4 ? 128 : 256;   // columns per accumulator
+    constexpr int NA = NC <= 4 ? 4 : 2;                                   // accumulators in rotation
+    constexpr uint32_t kTCols = NA * kAccCols;                            // <= 512
     extern __shared__ unsigned char smraw[];
-    __shared__ int s_src[kOffsetClasses][kTB];
     __shared__ int s_cls[kOffsetClasses];
     __shared__ int s_present[kOffsetClasses];
-    __shared__ int s_ncls, s_abort;
-    __shared__ __align__(8) uint64_t s_bar[S];
+    __shared__ int s_ncls;
+    __shared__ volatile int s_abort;
+    __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_accf[4], s_acce[4];
     __shared__ uint32_t s_tmem;
 
-    const int tid = threadIdx.x, w = tid >> 5;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const uint32_t raw0 = smem_u32(smraw);
     const uint32_t sbase = (raw0 + 1023u) & ~1023u;
-    const uint32_t stage_bytes = 2u * kAStage + 2u * (uint32_t)Kn * 128u;
+    const uint32_t img_bytes = 2u * (uint32_t)Kn * 128u;
+    const uint32_t stage_bytes = 2u * kAStage + img_bytes;
     const int KP = 32 * NKC;
     const int4 tile = tiles[blockIdx.x];
     const int blk = tile.x, b0 = tile.y, nbt = tile.z;
 
     if (w == 0) tmem_alloc(&s_tmem, kTCols);
     if (tid < kOffsetClasses) s_present[tid] = 0;
-    if (tid == 0) {
+    if (tid == 32) {
         s_abort = 0;
-        for (int i = 0; i < S; ++i) mbar_init(&s_bar[i], 1);
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&s_full[i], kProdThreads + 1);
+            mbar_init(&s_empty[i], 1);
+        }
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(&s_accf[i], 1);
+            mbar_init(&s_acce[i], kDrainThreads / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    const int t = tid < nbt ? tbox[b0 + tid] : -1;
-    for (int o = 0; o < kOffsetClasses; ++o) {
-        const int sb = t >= 0 ? vtab[(int64_t)kOffsetClasses * t + o] : -1;
-        s_src[o][tid] = sb;
-        if (sb >= 0) s_present[o] = 1;
+    // producer thread r gathers chunk (r & 7) of rows (r >> 3) + 16 k, k < 8: it keeps
+    // those rows' target boxes in registers and reads each source from vtab
+    int tgt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tgt[k] = -1;
+    if (tid >= kDrainThreads && tid < kDrainThreads + kProdThreads) {
+        const int r = tid - kDrainThreads;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int row = (r >> 3) + 16 * k;
+            tgt[k] = row < nbt ? tbox[b0 + row] : -1;
+        }
+        if ((r & 7) == 0) {   // one thread per row marks the classes present in the tile
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (tgt[k] >= 0)
+                    for (int o = 0; o < kOffsetClasses; ++o)
+                        if (vtab[(int64_t)kOffsetClasses * tgt[k] + o] >= 0) s_present[o] = 1;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -142,100 +181,121 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     const uint32_t tmem = s_tmem;
-    const uint32_t tlane = (uint32_t)(w * 32) << 16;
     const int nitems = s_ncls * NKC;
-    const unsigned char *imgb = reinterpret_cast<const unsigned char *>(img);
-
-    auto load = [&](int it) {
-        const int o = s_cls[it / NKC], kc = it - (it / NKC) * NKC;
-        const uint32_t st = sbase + (uint32_t)(it % S) * stage_bytes;
-        const int sb = s_src[o][tid];
-        const float *mh = Mpk + (int64_t)sb * 2 * KP + kc * 32;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t off = sw128_offset((uint32_t)tid, (uint32_t)j);
-            if (sb >= 0) {
-                cp_async16(st + off, mh + 4 * j);
-                cp_async16(st + kAStage + off, mh + KP + 4 * j);
-            } else {
-                st_shared_zero16(st + off);
-                st_shared_zero16(st + kAStage + off);
-            }
-        }
-        const unsigned char *src = imgb + (((size_t)blk * kOffsetClasses + o) * NKC + kc) * (2 * (size_t)Kn * 128);
-        const int n16 = Kn * 16;   // 2 parts x Kn rows x 8 chunks
-        for (int e = tid; e < n16; e += kThreads) cp_async16(st + 2 * kAStage + 16u * e, src + 16 * (size_t)e);
-    };
-
-    // Each chunk accumulates into a fresh TMEM accumulator (the two alternate)
-    // and is added to FP32 registers once its MMAs complete: long accumulation
-    // chains inside the tensor core lose precision, one chunk of 12 MMAs does not.
-    float acc[NC * 32];
-#pragma unroll
-    for (int i = 0; i < NC * 32; ++i) acc[i] = 0.f;
     bool ok = true;
-    auto drain = [&](int it) {   // every thread: wait for item it, add its accumulator
-        const bool got = mbar_wait(&s_bar[it % S], (uint32_t)(it / S) & 1u);
-        if (!__all_sync(0xFFFFFFFFu, got)) {   // the TMEM loads below need the whole warp
-            ok = false;
-            s_abort = 1;
-            return;
-        }
-        tc_fence_after();
-        const uint32_t a = tmem + tlane + (uint32_t)(it & 1) * kAccCols;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            float v[32];
-            tmem_ld32(a + (uint32_t)(c * 32), v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
-        }
-        tc_fence_before();
-    };
 
-    const uint32_t idesc = umma_idesc_tf32(kTB, (uint32_t)Kn);
+    if (w < 4) {
+        // ---------------------------------------------------------------- drain
+        float acc[NC * 32];
 #pragma unroll
-    for (int it = 0; it < S - 1; ++it) {
-        if (it < nitems) load(it);
-        cp_async_commit();
-    }
-    for (int it = 0; it < nitems; ++it) {
-        cp_async_wait<S - 2>();
-        fence_proxy_async_smem();
-        __syncthreads();   // stage it landed; accumulator (it & 1) drained (item it - 2)
-        if (s_abort) break;
-        if (tid == 0) {
+        for (int i = 0; i < NC * 32; ++i) acc[i] = 0.f;
+        const uint32_t tl = tmem + ((uint32_t)(w * 32) << 16);
+        for (int it = 0; it < nitems; ++it) {
+            const bool got = mbar_wait(&s_accf[it % NA], (uint32_t)(it / NA) & 1u);
+            if (!__all_sync(0xFFFFFFFFu, got) || s_abort) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
-            const uint32_t st = sbase + (uint32_t)(it % S) * stage_bytes;
-            const uint32_t bh = st + 2 * kAStage, bl = bh + (uint32_t)Kn * 128u;
-            const uint32_t d = tmem + (uint32_t)(it & 1) * kAccCols;
+            const uint32_t a = tl + (uint32_t)(it % NA) * kAccCols;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float v[32];
+                tmem_ld32(a + (uint32_t)(c * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_acce[it % NA]);
+        }
+        if (ok && nitems > 0 && tid < nbt) {
+            float *Lb = L + (int64_t)tbox[b0 + tid] * Kout;
+#pragma unroll
+            for (int i = 0; i < NC * 32; ++i)
+                if (i < Kout) Lb[i] = acc[i];
+        }
+    } else if (w < 8) {
+        // ---------------------------------------------------------------- producers
+        // No producer waits for its own copies: each chunk ends with an arrive
+        // that the hardware performs once the thread's copies have landed, so
+        // the producers run up to S chunks ahead of the MMAs.
+        const int r = tid - kDrainThreads;
+        const int j = r & 7;
+        const unsigned char *imgb = reinterpret_cast<const unsigned char *>(img);
+        for (int it = 0; it < nitems; ++it) {
+            const int st = it % S;
+            if (s_abort || (it >= S && !mbar_wait(&s_empty[st], (uint32_t)((it / S) + 1) & 1u))) {
+                ok = false;
+                break;
+            }
+            const int o = s_cls[it / NKC], kc = it - (it / NKC) * NKC;
+            const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
+            if (r == 0) {
+                mbar_arrive_expect_tx(&s_full[st], img_bytes);
+                bulk_g2s(smraw + (sa - raw0) + 2 * kAStage,
+                         imgb + (((size_t)blk * kOffsetClasses + o) * NKC + kc) * (size_t)img_bytes, img_bytes,
+                         &s_full[st]);
+            }
+            // 8 consecutive threads fetch the 8 16-byte chunks of one 128-byte row, so a
+            // warp instruction reads 4 whole rows (full sectors) rather than 32 fragments
+            int src[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) src[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + o) : -1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int row = (r >> 3) + 16 * k;
+                const int sb = src[k];
+                const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)j);
+                if (sb >= 0) {
+                    const float *mh = Mpk + (int64_t)sb * 2 * KP + kc * 32 + 4 * j;
+                    cp_async16(sa + off, mh);
+                    cp_async16(sa + kAStage + off, mh + KP);
+                } else {
+                    cp_async16_zero(sa + off, Mpk);
+                    cp_async16_zero(sa + kAStage + off, Mpk);
+                }
+            }
+            cp_async_arrive_noinc(&s_full[st]);
+        }
+        cp_async_wait<0>();
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        const uint32_t idesc = umma_idesc_tf32(kTB, (uint32_t)Kn);
+        for (int it = 0; it < nitems; ++it) {
+            const int st = it % S;
+            if (s_abort || !mbar_wait(&s_full[st], (uint32_t)(it / S) & 1u) ||
+                (it >= NA && !mbar_wait(&s_acce[it % NA], (uint32_t)((it / NA) + 1) & 1u))) {
+                ok = false;
+                break;
+            }
+            // the A rows were written by cp.async (generic proxy); the MMA reads them
+            // through the async proxy
+            fence_proxy_async_smem();
+            tc_fence_after();
+            const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
+            const uint32_t bh = sa + 2 * kAStage, bl = bh + (uint32_t)Kn * 128u;
+            const uint32_t d = tmem + (uint32_t)(it % NA) * kAccCols;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t dah = umma_desc_sw128(st + 32 * ks), dal = umma_desc_sw128(st + kAStage + 32 * ks);
+                const uint64_t dah = umma_desc_sw128(sa + 32 * ks), dal = umma_desc_sw128(sa + kAStage + 32 * ks);
                 const uint64_t dbh = umma_desc_sw128(bh + 32 * ks), dbl = umma_desc_sw128(bl + 32 * ks);
                 umma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
                 umma_tf32(d, dah, dbl, idesc, 1u);
                 umma_tf32(d, dal, dbh, idesc, 1u);
             }
-            umma_commit(&s_bar[it % S]);
+            umma_commit(&s_empty[st]);
+            umma_commit(&s_accf[it % NA]);
         }
-        __syncwarp();
-        // item it - 1 done: its accumulator is added and its stage is free for item it + S - 1
-        if (it >= 1) drain(it - 1);
-        const int nx = it + S - 1;
-        if (nx < nitems && ok) load(nx);
-        cp_async_commit();
+        // the last commits must land before the CTA releases its TMEM
+        if (ok && nitems > 0) {
+            const int last = nitems - 1;
+            if (!mbar_wait(&s_empty[last % S], (uint32_t)(last / S) & 1u)) ok = false;
+        }
     }
-    cp_async_wait<0>();
-    __syncthreads();
-    if (nitems > 0 && !s_abort) drain(nitems - 1);
-    if (!ok) set_error(err, kErrWaitTimeout);
-    const int all_ok = __syncthreads_and(ok ? 1 : 0);
-    if (nitems > 0 && all_ok && tid < nbt) {
-        float *Lb = L + (int64_t)tbox[b0 + tid] * Kout;
-#pragma unroll
-        for (int i = 0; i < NC * 32; ++i)
-            if (i < Kout) Lb[i] = acc[i];
+    if (!ok) {
+        s_abort = 1;
+        set_error(err, kErrWaitTimeout);
     }
     tc_fence_before();
     __syncthreads();
@@ -248,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 bool m2l_umma_supported(int K, int Kout) {
     if (K < 1 || Kout < 1 || K > 256 || Kout > 256) return false;
     const UmmaDims d = umma_dims(K, Kout);
-    return d.smem() + sizeof(int) * kOffsetClasses * (kTB + 2) + 256 <= 227 * 1024;
+    return d.smem() + kStaticSmem <= 227 * 1024;
 }
 
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s) {
@@ -275,12 +335,15 @@ void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, 
 #define IMQ_UMMA_CASE(SS, NCC)                                                                                    \
     if (d.stages == SS && d.tcols == NCC) {                                                                      \
         IMQ_CUDA(cudaFuncSetAttribute(k_m2l_umma<SS, NCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_m2l_umma<SS, NCC><<<P.n_m2l_tiles, kThreads, smem, s>>>(P.m2l_tiles.as<int4>(), P.m2l_tbox.as<int32_t>(), \
+        k_m2l_umma<SS, NCC><<<P.n_m2l_tiles, kThreadsWS, smem, s>>>(P.m2l_tiles.as<int4>(), P.m2l_tbox.as<int32_t>(), \
                                                                  P.vtab.as<int32_t>(), Mpk, L, img, Kout, d.Kn,    \
                                                                  d.NKC, err);                                      \
         launched = true;                                                                                          \
     }
     bool launched = false;
+    IMQ_UMMA_CASE(4, 1)
+    IMQ_UMMA_CASE(4, 2)
+    IMQ_UMMA_CASE(4, 3)
     IMQ_UMMA_CASE(3, 1)
     IMQ_UMMA_CASE(3, 2)
     IMQ_UMMA_CASE(3, 3)

@@ -23,6 +23,7 @@
 // error instead of O(eps * |x|).
 #include <type_traits>
 
+#include "f32x2.cuh"
 #include "imq_internal.h"
 #include "ptx.cuh"
 #include "util.cuh"
@@ -32,25 +33,6 @@ namespace {
 
 constexpr int kP2PWarps = 4;
 constexpr float kFar = 1.0e18f;   // coordinate of padding targets
-
-typedef unsigned long long u64;
-
-__device__ __forceinline__ u64 pk2(float a, float b) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void up2(u64 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 
 // Sum over the 32 lanes of each acc[i], i < TC; lane L ends with the total of
 // target L % TC.

@@ -31,6 +31,15 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t j
 __device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst_smem), "l"(src) : "memory");
 }
+// 16 bytes of zeros (no bytes read from src, which must still be a valid address)
+__device__ __forceinline__ void cp_async16_zero(uint32_t dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(dst_smem), "l"(src) : "memory");
+}
+// arrive on an mbarrier once every cp.async issued so far by this thread has
+// landed; the arrival is counted in the barrier's expected count (noinc)
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {

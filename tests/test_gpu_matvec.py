@@ -143,3 +143,20 @@ def test_tensor_core_m2l_batched_matches_cuda_cores():
     ec = rel2(host(b.matvec(cuda(v, torch.float32))), ref)
     # c = 0.15 on 5000 points cancels strongly in M2L: both FP32 paths sit near 1e-6 here
     assert et < 2e-6 and et < 1.5 * ec + 2e-7, (et, ec)
+
+
+@pytest.mark.parametrize("p", [1, 3, 6, 9, 14])
+def test_fixed_order_far_field_every_p(p):
+    """The far-field kernel is compiled per order p; odd and even p against the FP64
+    FMM reference on an adaptive tree (W lists present)."""
+    import torch
+    imq = _imq()
+    pts = W.clustered_points(800, 4, 1500, 0.03, 8)
+    c = 0.01
+    v = W.random_vector(pts.shape[0], 17)
+    plan = imq.Plan(cuda(pts), c, p, 24, domain=(0.0, 0.0, 1.0))
+    assert plan.info()["n_w"] > 0
+    b32 = host(plan.matvec(cuda(v, torch.float32)))
+    ofmm = fmm.fmm_matvec(pts, c, v, p, 24, (0.0, 0.0, 1.0))
+    assert rel2(b32, ofmm) < 1e-6
+    plan.close()
