@@ -91,50 +91,176 @@ __global__ void k_p2m(int nleaf, const int32_t *__restrict__ leaves, const int32
 }
 
 // ------------------------------------------------------------------ M2M / L2L
+// M2M and L2L (in-plane translations between a box and its four children,
+// level-independent operators [q][i][o] in the scaled layout), over the
+// internal boxes of one level.  A CTA takes 8 parents; warp q owns child
+// quadrant q, and lane t owns outputs t + 32 r (r < RC) for all 8 boxes, so per
+// input row a lane loads RC operator values (coalesced, reused for 8 boxes)
+// and 8 staged inputs (two vector shared loads) for 8 RC FMAs, and the
+// reduction chain is K rows long.  Operator rows are fetched kTransUnroll at a
+// time with every load issued before the FMAs.  M2M sums the four quadrant
+// partials in a fixed order; L2L adds warp q's result into child q.
+constexpr int kTransG = 8;        // parents per CTA
+constexpr int kTransUnroll = 4;   // operator rows in flight per step
+
 template <class T>
-__global__ void k_m2m(int lb, const int32_t *__restrict__ child, T *__restrict__ M, const T *__restrict__ op, int K) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *Mc = reinterpret_cast<T *>(smraw);
-    const int b = lb + blockIdx.x;
-    int ch[4];
-    bool any = false;
+__device__ __forceinline__ void lds8(const T *p, T (&v)[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ch[q] = child[4 * b + q];
-        any |= ch[q] >= 0;
-    }
-    if (!any) return;   // a leaf keeps its P2M moments
-    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
-        const int q = e / K, i = e - q * K;
-        Mc[e] = ch[q] >= 0 ? M[(int64_t)ch[q] * K + i] : (T)0;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < K; o += blockDim.x) {
-        T acc = 0;
-        for (int q = 0; q < 4; ++q) {
-            if (ch[q] < 0) continue;
-            const T *opq = op + (int64_t)q * K * K;
-            for (int i = 0; i < K; ++i) acc += opq[(int64_t)i * K + o] * Mc[q * K + i];
+        for (int k = 0; k < 4; ++k) {
+            const double2 a = reinterpret_cast<const double2 *>(p)[k];
+            v[2 * k] = a.x;
+            v[2 * k + 1] = a.y;
         }
-        M[(int64_t)b * K + o] = acc;
     }
 }
 
-template <class T>
-__global__ void k_l2l(int lb, const int32_t *__restrict__ parent, const uint32_t *__restrict__ prefix,
-                      T *__restrict__ L, const T *__restrict__ op, int K) {
+// acc[g][r] = sum_{i < K} A[i][lane + 32 r] * X[i][g]   (A: K x K row-major, X: K x 8)
+template <class T, int RC>
+__device__ __forceinline__ void trans_rows(const T *__restrict__ A, const T *X, int K, int lane, T (&acc)[8][RC]) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[g][r] = 0;
+    bool okr[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) okr[r] = lane + 32 * r < K;
+    for (int i0 = 0; i0 < K; i0 += kTransUnroll) {
+        T wv[kTransUnroll][RC];
+#pragma unroll
+        for (int u = 0; u < kTransUnroll; ++u)
+#pragma unroll
+            for (int r = 0; r < RC; ++r)
+                wv[u][r] = (okr[r] && i0 + u < K) ? __ldg(A + (int64_t)(i0 + u) * K + lane + 32 * r) : (T)0;
+#pragma unroll
+        for (int u = 0; u < kTransUnroll; ++u) {
+            if (i0 + u >= K) break;
+            T mv[8];
+            lds8<T>(X + (size_t)(i0 + u) * kTransG, mv);
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[g][r] += wv[u][r] * mv[g];
+        }
+    }
+}
+
+// M(parent) = sum_q T_q M(child q)
+template <class T, int RC>
+__global__ void __launch_bounds__(128) k_m2m(const int32_t *__restrict__ parents, int n,
+                                             const int32_t *__restrict__ child, T *__restrict__ M,
+                                             const T *__restrict__ op, int K) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Lp = reinterpret_cast<T *>(smraw);
-    const int b = lb + blockIdx.x;
-    const int pb = parent[b];
-    const int q = (int)(prefix[b] & 3u);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) Lp[i] = L[(int64_t)pb * K + i];
+    T *Mc = reinterpret_cast<T *>(smraw);          // [4][K][8]
+    T *red = Mc + (size_t)4 * K * kTransG;           // [4][8][K]
+    __shared__ int s_ch[kTransG * 4], s_par[kTransG];
+    const int p0 = blockIdx.x * kTransG;
+    const int ng = min(kTransG, n - p0);
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < kTransG * 4) {
+        const int g = threadIdx.x >> 2;
+        const int pb = g < ng ? parents[p0 + g] : -1;
+        s_ch[threadIdx.x] = pb >= 0 ? child[4 * pb + (threadIdx.x & 3)] : -1;
+        if ((threadIdx.x & 3) == 0) s_par[g] = pb;
+    }
     __syncthreads();
-    const T *opq = op + (int64_t)q * K * K;
-    for (int o = threadIdx.x; o < K; o += blockDim.x) {
-        T acc = 0;
-        for (int i = 0; i < K; ++i) acc += opq[(int64_t)i * K + o] * Lp[i];
-        L[(int64_t)b * K + o] += acc;
+    {   // warp q stages child q of the 8 parents: all loads first, then the shared stores
+        T v[kTransG][RC];
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g) {
+            const int ch = s_ch[4 * g + q];
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int i = lane + 32 * r;
+                v[g][r] = (ch >= 0 && i < K) ? M[(int64_t)ch * K + i] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int i = lane + 32 * r;
+                if (i < K) Mc[((size_t)q * K + i) * kTransG + g] = v[g][r];
+            }
+    }
+    __syncwarp();
+    T acc[8][RC];
+    trans_rows<T, RC>(op + (int64_t)q * K * K, Mc + (size_t)q * K * kTransG, K, lane, acc);
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            const int o = lane + 32 * r;
+            if (o < K) red[((size_t)q * kTransG + g) * K + o] = acc[g][r];
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTransG * K; e += blockDim.x) {
+        const int g = e / K, o = e - g * K;
+        if (g >= ng) continue;
+        const T sum = ((red[(0 * kTransG + g) * K + o] + red[(1 * kTransG + g) * K + o]) +
+                       red[(2 * kTransG + g) * K + o]) + red[(3 * kTransG + g) * K + o];
+        M[(int64_t)s_par[g] * K + o] = sum;
+    }
+}
+
+// L(child q) += T_q L(parent)
+template <class T, int RC>
+__global__ void __launch_bounds__(128) k_l2l(const int32_t *__restrict__ parents, int n,
+                                             const int32_t *__restrict__ child, T *__restrict__ L,
+                                             const T *__restrict__ op, int K) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Lp = reinterpret_cast<T *>(smraw);          // [K][8]
+    __shared__ int s_ch[kTransG * 4], s_par[kTransG];
+    const int p0 = blockIdx.x * kTransG;
+    const int ng = min(kTransG, n - p0);
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < kTransG * 4) {
+        const int g = threadIdx.x >> 2;
+        const int pb = g < ng ? parents[p0 + g] : -1;
+        s_ch[threadIdx.x] = pb >= 0 ? child[4 * pb + (threadIdx.x & 3)] : -1;
+        if ((threadIdx.x & 3) == 0) s_par[g] = pb;
+    }
+    __syncthreads();
+    for (int g = q; g < kTransG; g += 4) {   // warp q stages parents q, q + 4
+        const int pb = s_par[g];
+        T v[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            const int i = lane + 32 * r;
+            v[r] = (pb >= 0 && i < K) ? L[(int64_t)pb * K + i] : (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K) Lp[(size_t)i * kTransG + g] = v[r];
+        }
+    }
+    __syncthreads();
+    T acc[8][RC];
+    trans_rows<T, RC>(op + (int64_t)q * K * K, Lp, K, lane, acc);
+    // children rows are distinct: read all old values, then write all sums
+    T old[8][RC];
+    int chs[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        chs[g] = g < ng ? s_ch[4 * g + q] : -1;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            const int o = lane + 32 * r;
+            old[g][r] = (chs[g] >= 0 && o < K) ? L[(int64_t)chs[g] * K + o] : (T)0;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        if (chs[g] < 0) continue;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            const int o = lane + 32 * r;
+            if (o < K) L[(int64_t)chs[g] * K + o] = old[g][r] + acc[g][r];
+        }
     }
 }
 
@@ -499,15 +625,64 @@ void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaS
     m2m_levels<T>(P, M, m2m, s, launches);
 }
 
-template <class T>
-void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches) {
-    const int K = P.layout.K;    for (int lev = P.max_level - 1; lev >= 2; --lev) {
-        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-        if (nl <= 0) continue;
-        k_m2m<T><<<nl, 128, sizeof(T) * 4 * K, s>>>(lb, P.child.as<int32_t>(), M, m2m, K);
+// internal boxes of each level, in box order (built once per plan)
+void ensure_parents(Plan &P, cudaStream_t s) {
+    if (!P.parent_start.empty()) return;
+    std::vector<int32_t> ch(4 * (size_t)P.nbox);
+    IMQ_CUDA(cudaMemcpyAsync(ch.data(), P.child.ptr, sizeof(int32_t) * ch.size(), cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> par;
+    P.parent_start.assign(P.level_start.size(), 0);
+    for (size_t lev = 0; lev + 1 < P.level_start.size(); ++lev) {
+        P.parent_start[lev] = (int)par.size();
+        for (int b = P.level_start[lev]; b < P.level_start[lev + 1]; ++b)
+            if (ch[4 * (size_t)b] >= 0 || ch[4 * (size_t)b + 1] >= 0 || ch[4 * (size_t)b + 2] >= 0 ||
+                ch[4 * (size_t)b + 3] >= 0)
+                par.push_back(b);
+    }
+    P.parent_start.back() = (int)par.size();
+    P.parents.alloc(sizeof(int32_t) * std::max<size_t>(1, par.size()));
+    if (!par.empty())
+        IMQ_CUDA(cudaMemcpyAsync(P.parents.ptr, par.data(), sizeof(int32_t) * par.size(), cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+}
+
+template <class T, bool UP>
+void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, bool downward, cudaStream_t s,
+                  int *launches) {
+    ensure_parents(P, s);
+    const int RC = (K + 31) / 32;
+    void (*kern)(const int32_t *, int, const int32_t *, T *, const T *, int) = nullptr;
+#define IMQ_TRANS_CASE(R)                                \
+    case R:                                              \
+        kern = UP ? k_m2m<T, R> : k_l2l<T, R>;           \
+        break;
+    switch (RC) {
+        IMQ_TRANS_CASE(1)
+        IMQ_TRANS_CASE(2)
+        IMQ_TRANS_CASE(3)
+        IMQ_TRANS_CASE(4)
+        IMQ_TRANS_CASE(5)
+        IMQ_TRANS_CASE(6)
+        default: fail(IMQ_UNSUPPORTED, "M2M/L2L: expansion too large");
+    }
+#undef IMQ_TRANS_CASE
+    const size_t smem = sizeof(T) * (UP ? (size_t)4 * K * kTransG * 2 : (size_t)K * kTransG);
+    IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int k = 0; k <= lev_hi - lev_lo; ++k) {
+        const int lev = downward ? lev_lo + k : lev_hi - k;
+        const int pb = P.parent_start[lev], np = P.parent_start[lev + 1] - pb;
+        if (np <= 0) continue;
+        kern<<<(np + kTransG - 1) / kTransG, 128, smem, s>>>(P.parents.as<int32_t>() + pb, np, P.child.as<int32_t>(),
+                                                           X, op, K);
         IMQ_LAUNCH_CHECK();
         ++*launches;
     }
+}
+
+template <class T>
+void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches) {
+    trans_launch<T, true>(P, M, m2m, P.layout.K, 2, P.max_level - 1, false, s, launches);
 }
 template void m2m_levels<float>(Plan &, float *, const float *, cudaStream_t, int *);
 template void m2m_levels<double>(Plan &, double *, const double *, cudaStream_t, int *);
@@ -516,13 +691,8 @@ template void upward_launch<double>(Plan &, const double *, double *, const doub
 
 template <class T>
 void l2l_launch(Plan &P, T *L, const T *op, int K, cudaStream_t s, int *launches) {
-    for (int lev = 3; lev <= P.max_level; ++lev) {
-        const int lb = P.level_start[lev], nl = P.level_start[lev + 1] - lb;
-        if (nl <= 0) continue;
-        k_l2l<T><<<nl, 128, sizeof(T) * K, s>>>(lb, P.parent.as<int32_t>(), P.prefix.as<uint32_t>(), L, op, K);
-        IMQ_LAUNCH_CHECK();
-        ++*launches;
-    }
+    // parents at levels 2 .. max_level - 1, children one level below
+    trans_launch<T, false>(P, L, op, K, 2, P.max_level - 1, true, s, launches);
 }
 template void l2l_launch<float>(Plan &, float *, const float *, int, cudaStream_t, int *);
 template void l2l_launch<double>(Plan &, double *, const double *, int, cudaStream_t, int *);

@@ -162,6 +162,8 @@ struct Plan {
         return ShapeC{c, nprob > 1 ? box_prob.as<int32_t>() : nullptr, nprob > 1 ? prob_c.as<double>() : nullptr};
     }
     std::vector<int> level_start;              // boxes of level l: [level_start[l], level_start[l+1])
+    std::vector<int> parent_start;             // internal boxes of level l: parents[parent_start[l] ..]
+    DevMem parents;                            // int32: internal boxes, level by level, in box order
     // tree, device
     DevMem codes;      // uint32[N] sorted
     DevMem perm;       // int64[N] sorted -> input
