@@ -404,6 +404,12 @@ __global__ void __launch_bounds__(32 * kP2LWarps) k_p2l(
 template <class T, int PAR>
 void p2l_launch_impl(Plan &P, const T *u, T *L, int K, cudaStream_t s) {
     if (P.X.total == 0) return;
+    if constexpr (std::is_same<T, float>::value && PAR == 0) {
+        if (p2m_fixed_p_supported(P.p)) {
+            p2l_fixed_p_launch(P, u, L, s);
+            return;
+        }
+    }
     const size_t smem = sizeof(T) * (2 * (IMQ_MAX_P + 1) * (IMQ_MAX_P + 1) + (IMQ_MAX_P + 2) +
                                      (size_t)kP2LWarps * 32 * (K | 1));
     IMQ_CUDA(cudaFuncSetAttribute(k_p2l<T, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -533,7 +539,10 @@ static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
 void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
     TypedOps &O = fp64 ? P.ops64 : P.ops32;
     if (O.ready) return;
-    if (!fp64) far_fixed_p_prepare(s);
+    if (!fp64) {
+        far_fixed_p_prepare(s);
+        p2l_fixed_p_prepare(s);
+    }
     const int K = P.layout.K;
     const int nlev = std::max(0, P.m2l_level_hi - P.m2l_level_lo + 1);
     if (P.nprob > 1) {   // batched: shared M2M/L2L, M2L per (problem, level) generated on the device
@@ -614,13 +623,24 @@ template void p2l_odd_launch<double>(Plan &, const double *, double *, cudaStrea
 template <class T>
 void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches);
 
+// P2M: the fixed-order FP32 kernel where one is compiled, else the generic one
 template <class T>
-void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaStream_t s, int *launches) {
-    const int K = P.layout.K;
+void p2m_launch(Plan &P, const T *u, T *M, const T *coef, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (p2m_fixed_p_supported(P.p)) {
+            p2m_fixed_p_launch(P, u, M, coef, s);
+            return;
+        }
+    }
     k_p2m<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
         P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
-        P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, P.p, coef, P.side);
+        P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, P.layout.K, P.p, coef, P.side);
     IMQ_LAUNCH_CHECK();
+}
+
+template <class T>
+void upward_launch(Plan &P, const T *u, T *M, const T *coef, const T *m2m, cudaStream_t s, int *launches) {
+    p2m_launch<T>(P, u, M, coef, s);
     ++*launches;
     m2m_levels<T>(P, M, m2m, s, launches);
 }
@@ -734,10 +754,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)nb * K, s));
         // upward pass
         t0(kPhP2M);
-        k_p2m<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
-            P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
-            P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), u, M, K, p, coef, P.side);
-        IMQ_LAUNCH_CHECK();
+        p2m_launch<T>(P, u, M, coef, s);
         ++launches;
         t1();
         t0(kPhM2M);

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "f32x2.cuh"
+#include "fixed_order.cuh"
 #include "fmm_common.cuh"
 #include "imq_internal.h"
 #include "util.cuh"
@@ -34,35 +35,7 @@ __constant__ float c_rec_a[(kMaxP + 1) * (kMaxP + 1)];
 __constant__ float c_rec_b[(kMaxP + 1) * (kMaxP + 1)];
 __constant__ float c_fm[kMaxP + 2];
 
-__host__ __device__ constexpr int cnt_col(int P, int m) { return (P - m) / 2 + 1; }     // complex terms of column m
-__host__ __device__ constexpr int cbase(int P, int m) {                                  // first complex index of column m
-    int s = 0;
-    for (int mm = 0; mm < m; ++mm) s += cnt_col(P, mm);
-    return s;
-}
-__host__ __device__ constexpr int rbase(int P, int m) {                                  // first real slot of column m
-    int s = 0;
-    for (int mm = 0; mm < m; ++mm) s += cnt_col(P, mm) * (mm ? 2 : 1);
-    return s;
-}
-__host__ __device__ constexpr int ncplx(int P) { return cbase(P, P + 1); }
-
 constexpr int kFarWarps = 4;
-
-// complex index k -> (first complex index of its column, real slot of its term, m)
-template <int P>
-__device__ __forceinline__ void decode_term(int k, int &m, int &slot) {
-    m = 0;
-    int kb = 0, rb = 0;
-#pragma unroll
-    for (int mm = 1; mm <= P; ++mm)
-        if (k >= cbase(P, mm)) {
-            m = mm;
-            kb = cbase(P, mm);
-            rb = rbase(P, mm);
-        }
-    slot = rb + (k - kb) * (m ? 2 : 1);
-}
 
 template <int P>
 __global__ void __launch_bounds__(32 * kFarWarps, 8) k_far_t(

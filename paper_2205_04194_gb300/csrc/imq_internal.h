@@ -250,6 +250,11 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s);
 template <class T>
 int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t s);
 void build_m2l_tiles(Plan &P, cudaStream_t s);
+// p2m.cu: P2M for a compile-time order (FP32)
+bool p2m_fixed_p_supported(int p);
+void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s);
+void p2l_fixed_p_prepare(cudaStream_t s);
+void p2l_fixed_p_launch(const Plan &P, const float *u, float *L, cudaStream_t s);
 // far.cu: L2P + M2P for a compile-time order (FP32)
 bool far_fixed_p_supported(int p);
 void far_fixed_p_prepare(cudaStream_t s);
