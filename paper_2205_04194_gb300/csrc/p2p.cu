@@ -72,7 +72,7 @@ __global__ void k_pack_records(const float2 *__restrict__ loc, const float *__re
     }
 }
 
-constexpr int kStageCap = 1024;   // source records staged per warp at a time (16 KB)
+constexpr int kStageCap = 512;    // source records staged per warp at a time (8 KB)
 
 struct WarpStage {
     float4 rec[kStageCap];
@@ -80,10 +80,12 @@ struct WarpStage {
 };
 
 // Stage concatenated positions [q0, q0 + len) of the U-list sources of one leaf
-// into shared memory with 1-D TMA bulk copies (one per overlapping U entry), wait
-// for them (bounded), then shift each record into the target leaf's frame.
-// Returns false if the wait timed out.
-__device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, int q0, int len, int u0, int u1,
+// into shared memory with 1-D TMA bulk copies, one per overlapping U entry, the
+// entries spread over the lanes (lane e sets up entry u0 + e, u0 + e + 32, ...);
+// wait for them (bounded), then shift each entry's records into the target
+// leaf's frame, the entry bounds and offset broadcast from the lane that loaded
+// them.  St: total source count of the leaf.  Returns false if the wait timed out.
+__device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, int q0, int len, int u0, int u1, int St,
                                               const int32_t *__restrict__ begin, const int32_t *__restrict__ uitems,
                                               const int32_t *__restrict__ ucum, const float2 *__restrict__ udelta,
                                               const float4 *__restrict__ rec, int lane, int *err) {
@@ -91,17 +93,20 @@ __device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, in
         // earlier generic-proxy writes to ws.rec must be ordered before the async-proxy copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&ws.bar, (uint32_t)len * 16u);
-        for (int r = u0; r < u1; ++r) {
-            const int lo = ucum[r];
-            const int cnt = (r + 1 < u1 ? ucum[r + 1] : 0x7FFFFFFF) - lo;
-            const int a = max(lo, q0), bnd = min(lo + cnt, q0 + len);
-            if (bnd <= a) {
-                if (lo >= q0 + len) break;
-                continue;
-            }
-            const int src0 = begin[uitems[r]] + (a - lo);
-            bulk_g2s(&ws.rec[a - q0], rec + src0, (uint32_t)(bnd - a) * 16u, &ws.bar);
+    }
+    __syncwarp();
+    int my_lo = 0, my_hi = 0;
+    float2 my_d = make_float2(0.f, 0.f);
+    for (int r = u0 + lane; r < u1; r += 32) {
+        const int lo = ucum[r];
+        const int hi = r + 1 < u1 ? ucum[r + 1] : St;
+        if (r - u0 < 32) {
+            my_lo = lo;
+            my_hi = hi;
+            my_d = udelta[r];
         }
+        const int a = max(lo, q0), bnd = min(hi, q0 + len);
+        if (a < bnd) bulk_g2s(&ws.rec[a - q0], rec + begin[uitems[r]] + (a - lo), (uint32_t)(bnd - a) * 16u, &ws.bar);
     }
     const bool ok = mbar_wait(&ws.bar, phase & 1u);
     phase++;
@@ -109,15 +114,27 @@ __device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, in
         if (lane == 0) set_error(err, kErrWaitTimeout);
         return false;
     }
-    int r = u0;
-    for (int q = lane; q < len; q += 32) {
-        const int gq = q0 + q;
-        while (r + 1 < u1 && ucum[r + 1] <= gq) ++r;
-        const float2 d = udelta[r];
-        float4 v = ws.rec[q];
-        v.x -= d.x;
-        v.y -= d.y;
-        ws.rec[q] = v;
+    const int ne = u1 - u0;
+    for (int e = 0; e < ne; ++e) {
+        int lo, hi;
+        float2 d;
+        if (e < 32) {
+            lo = __shfl_sync(0xFFFFFFFFu, my_lo, e);
+            hi = __shfl_sync(0xFFFFFFFFu, my_hi, e);
+            d.x = __shfl_sync(0xFFFFFFFFu, my_d.x, e);
+            d.y = __shfl_sync(0xFFFFFFFFu, my_d.y, e);
+        } else {
+            lo = ucum[u0 + e];
+            hi = e + 1 < ne ? ucum[u0 + e + 1] : St;
+            d = udelta[u0 + e];
+        }
+        const int a = max(lo, q0), bnd = min(hi, q0 + len);
+        for (int q = a + lane; q < bnd; q += 32) {
+            float4 v = ws.rec[q - q0];
+            v.x -= d.x;
+            v.y -= d.y;
+            ws.rec[q - q0] = v;
+        }
     }
     __syncwarp();
     return true;
@@ -164,7 +181,7 @@ __device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase
     } else {
         for (int q0 = 0; q0 < St; q0 += kStageCap) {
             const int len = min(kStageCap, St - q0);
-            if (!stage_sources(ws, phase, q0, len, u0, u1, begin, uitems, ucum, udelta, rec, lane, err)) break;
+            if (!stage_sources(ws, phase, q0, len, u0, u1, St, begin, uitems, ucum, udelta, rec, lane, err)) break;
             p2p_tile_f32<TC>(ws.rec, len, lane, tx, ty, acc, cc);
             __syncwarp();
         }
@@ -198,23 +215,19 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     const float c2 = (float)(cb * cb);
     uint32_t phase = 0;
     const bool staged_all = St <= kStageCap;
-    if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, begin, uitems, ucum, udelta, rec, lane, err)) return;
-    for (int tc = 0; tc < nt; tc += 32) {
-        const int ntc = min(32, nt - tc);
+    if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, St, begin, uitems, ucum, udelta, rec, lane, err)) return;
+    for (int tc = 0; tc < nt; tc += 16) {
+        const int ntc = min(16, nt - tc);
         float tot;
         int tcap;
         if (ntc <= 8) {
             tot = p2p_chunk_staged<8>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
                                       udelta, loc, rec, c2, err);
             tcap = 8;
-        } else if (ntc <= 16) {
+        } else {
             tot = p2p_chunk_staged<16>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
                                        udelta, loc, rec, c2, err);
             tcap = 16;
-        } else {
-            tot = p2p_chunk_staged<32>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
-                                       udelta, loc, rec, c2, err);
-            tcap = 32;
         }
         if (lane < tcap && lane < ntc) bs[tb + tc + lane] += tot;
     }
