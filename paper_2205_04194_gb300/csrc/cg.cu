@@ -40,7 +40,12 @@ constexpr int kRedBlocks = 608;
 constexpr int kRedThreads = 256;
 constexpr int kIterPerGraph = 8;
 
-enum CGState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3 };
+// kBreakdown: a finite p.q <= 0 or r.z <= 0.  A is positive definite, but the
+// FP32 product and the shifted patch factors are not exactly so when A is
+// nearly singular; the pass then ends and the host restarts from the true
+// residual of the best iterate.  kNumerical is reserved for NaN / Inf.
+enum CGState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3, kBreakdown = 4 };
+constexpr int kMaxRestarts = 16;   // restarts after a breakdown when no refinement steps are requested
 
 struct CGScalars {
     double rz, rz_new, pq, rr, alpha, beta, rr_target, rr_best, rr0;
@@ -92,8 +97,11 @@ __global__ void __launch_bounds__(kRedThreads) k_finish_alpha(const double *__re
     const double pq = final_sum(part);
     if (threadIdx.x == 0) {
         S->pq = pq;
-        if (!(pq > 0) || !isfinite(pq)) {
+        if (!isfinite(pq)) {
             S->status = kNumerical;
+            S->done = 1;
+        } else if (!(pq > 0)) {
+            S->status = kBreakdown;
             S->done = 1;
         } else {
             S->alpha = S->rz / pq;
@@ -168,8 +176,11 @@ __global__ void __launch_bounds__(kRedThreads) k_finish_beta(const double *__res
     const double rzn = use_rr ? S->rr : final_sum(part);
     if (threadIdx.x == 0) {
         S->rz_new = rzn;
-        if (!(S->rz > 0) || !isfinite(rzn)) {
+        if (!isfinite(rzn)) {
             S->status = kNumerical;
+            S->done = 1;
+        } else if (!(rzn > 0)) {
+            S->status = kBreakdown;
             S->done = 1;
         } else {
             S->beta = rzn / S->rz;
@@ -586,7 +597,9 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
             int status = kMaxIter;
             int iters = 0;
             const int max_outer = std::max(0, o.refine_steps);
-            for (int outer = 0; outer <= max_outer; ++outer) {
+            int restarts = 0;
+            bool numerical = false;
+            for (int outer = 0;; ++outer) {
                 // residual r = f - A x (FP64 product unless x = 0)
                 if (outer == 0 && !o.x0_given) {
                     IMQ_CUDA(cudaMemcpyAsync(r, fs.ptr, 8 * n, cudaMemcpyDeviceToDevice, s));
@@ -606,8 +619,9 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                     status = kConverged;
                     break;
                 }
-                if (outer == max_outer && outer > 0) break;
+                status = kMaxIter;
                 if (iters >= o.maxit) break;
+                if (max_outer > 0 ? outer >= max_outer : outer > restarts) break;
                 // inner PCG on A d = r from d = 0
                 // the recursive residual of the inner operator drifts from the true one by about the
                 // operator's rounding error, so a single pass aims at half the tolerance
@@ -629,6 +643,11 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                 } else {
                     h.rz = rr0;
                 }
+                if (!std::isfinite(h.rz)) {
+                    status = kNumerical;
+                    break;
+                }
+                if (!(h.rz > 0)) break;   // the preconditioner is not positive on r: keep x
                 IMQ_CUDA(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, s));
                 IMQ_CUDA(cudaMemcpyAsync(S, &h, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
                 CGScalars hs{};
@@ -639,28 +658,34 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                     if (hs.done) break;
                 }
                 iters += hs.iter;
-                // x += best inner iterate
+                // x += best inner iterate (the pass's x = 0 start if no iterate improved)
                 k_axpby<<<g, 256, 0, s>>>(xs.as<double>(), w.xb.as<double>(), 1.0, 1.0, n);
                 IMQ_LAUNCH_CHECK();
                 outer_done = std::max(outer_done, outer + 1);
                 if (hs.status == kNumerical) {
-                    status = kNumerical;
+                    numerical = true;
                     break;
                 }
+                // without refinement steps, a pass that broke down after improving on its start is
+                // restarted from the true residual of its best iterate while iterations are left;
+                // otherwise the next round only computes the final true residual
                 if (max_outer == 0) {
-                    // single pass: report the true residual of the final iterate
-                    residual_product(P, RP, o.residual == IMQ_RESIDUAL_DENSE_F64 ? 1 : 0, xs.as<double>(),
-                                     ax.as<double>(), s);
-                    k_sub<<<g, 256, 0, s>>>(r, fs.as<double>(), ax.as<double>(), n);
-                    IMQ_LAUNCH_CHECK();
-                    rel = std::sqrt(read_dot(r, r, n, w.part, w.tmp, s)) / fn;
-                    status = rel <= o.rtol ? kConverged : kMaxIter;
-                    break;
+                    if (hs.status == kBreakdown && hs.rr_best < hs.rr0 && restarts < kMaxRestarts) ++restarts;
+                    else restarts = -1;
                 }
+            }
+            if (numerical) {
+                // report the true residual of the iterate that is returned
+                residual_product(P, RP, o.residual == IMQ_RESIDUAL_DENSE_F64 ? 1 : 0, xs.as<double>(),
+                                 ax.as<double>(), s);
+                k_sub<<<g, 256, 0, s>>>(r, fs.as<double>(), ax.as<double>(), n);
+                IMQ_LAUNCH_CHECK();
+                rel = std::sqrt(read_dot(r, r, n, w.part, w.tmp, s)) / fn;
+                status = kNumerical;
             }
             k_scatter_f64<<<g, 256, 0, s>>>(xs.as<double>(), P.perm.as<int32_t>(), n, xo);
             IMQ_LAUNCH_CHECK();
-            IMQ_CUDA(cudaStreamSynchronize(s));
+            check_device_errors(s);   // synchronises; a wait that ran out invalidates the solve
             total_iter += iters;
             worst_rel = std::max(worst_rel, rel);
             if (status != kConverged) final_status = status == kNumerical ? kNumerical : kMaxIter;

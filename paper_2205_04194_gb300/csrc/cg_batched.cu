@@ -31,10 +31,14 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kIterPerGraph = 8;
 
-enum BState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3 };
+// kBreakdown: a finite p.q <= 0 or r.z <= 0 (the FP32 product or the shifted
+// patch factors are not exactly positive definite for a nearly singular A);
+// the problem's pass ends and it is restarted from its true residual.
+enum BState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3, kBreakdown = 4 };
+constexpr int kMaxRestarts = 16;   // restarts after a breakdown when no refinement steps are requested
 
 struct BScalars {
-    double rz, rr, alpha, rr_target, rr_best;
+    double rz, rr, alpha, rr_target, rr_best, rr0;
     int iter, done, status, maxit;
 };
 
@@ -76,8 +80,11 @@ __global__ void __launch_bounds__(kThreads) k_alpha(const float *__restrict__ b3
     }
     const double pq = block_sum(acc);
     if (threadIdx.x == 0) {
-        if (!(pq > 0) || !isfinite(pq)) {
+        if (!isfinite(pq)) {
             S[b].status = kNumerical;
+            S[b].done = 1;
+        } else if (!(pq > 0)) {
+            S[b].status = kBreakdown;
             S[b].done = 1;
         } else {
             S[b].alpha = S[b].rz / pq;
@@ -150,8 +157,12 @@ __global__ void __launch_bounds__(kThreads) k_beta(const double *__restrict__ r,
     const double rzn = z != r ? block_sum(acc) : S[b].rr;
     if (threadIdx.x == 0) {
         BScalars &s = S[b];
-        if (!(s.rz > 0) || !isfinite(rzn)) {
+        if (!isfinite(rzn)) {
             s.status = kNumerical;
+            s.done = 1;
+            s_beta = 0;
+        } else if (!(rzn > 0)) {
+            s.status = kBreakdown;
             s.done = 1;
             s_beta = 0;
         } else {
@@ -301,13 +312,14 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             std::vector<double> rel(B, 1.0);
             std::vector<int> status(B, kMaxIter), iters(B, 0);
             const int max_outer = std::max(0, o.refine_steps);
+            int restarts = 0;
             auto true_residual = [&]() {
                 fmm_apply<double>(P, xs.as<double>(), ax.as<double>(), 1, s);
                 k_sub<<<gs, 256, 0, s>>>(r.as<double>(), fs.as<double>(), ax.as<double>(), n);
                 IMQ_LAUNCH_CHECK();
                 return read_seg_dots(r.as<double>(), r.as<double>(), doff, B, tmp, s);
             };
-            for (int outer = 0; outer <= max_outer; ++outer) {
+            for (int outer = 0;; ++outer) {
                 std::vector<double> rr0;
                 if (outer == 0 && !o.x0_given) {
                     IMQ_CUDA(cudaMemcpyAsync(r.ptr, fs.ptr, 8 * n, cudaMemcpyDeviceToDevice, s));
@@ -327,7 +339,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                         if (iters[b] < o.maxit) any = true;
                     }
                 }
-                if (!any || (outer == max_outer && outer > 0)) break;
+                if (!any || (max_outer > 0 ? outer >= max_outer : outer > restarts)) break;
                 IMQ_CUDA(cudaMemsetAsync(x.ptr, 0, 8 * n, s));
                 IMQ_CUDA(cudaMemsetAsync(xb.ptr, 0, 8 * n, s));
                 std::vector<double> rz = rr0;
@@ -345,6 +357,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                                       : 0.5 * o.rtol / rel[b];
                     e.rz = rz[b];
                     e.rr = rr0[b];
+                    e.rr0 = rr0[b];
                     e.rr_best = rr0[b];
                     e.rr_target = inner_rtol * inner_rtol * rr0[b];
                     e.maxit = o.maxit - iters[b];
@@ -368,18 +381,20 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                     if (h[b].status == kNumerical) status[b] = kNumerical;
                 }
                 if (max_outer == 0) {
-                    const std::vector<double> rr = true_residual();
-                    for (int b = 0; b < B; ++b) {
-                        const double fn = std::sqrt(ff[b]);
-                        rel[b] = fn > 0 ? std::sqrt(rr[b]) / fn : 0.0;
-                        if (status[b] != kNumerical) status[b] = rel[b] <= o.rtol ? kConverged : kMaxIter;
-                    }
-                    break;
+                    // restart the problems whose pass broke down after improving on its start,
+                    // from the true residual of their best iterate; otherwise the next round only
+                    // computes the final true residuals
+                    bool restart = false;
+                    for (int b = 0; b < B; ++b)
+                        restart |= status[b] != kNumerical && h[b].status == kBreakdown && h[b].rr_best < h[b].rr0 &&
+                                   iters[b] < o.maxit;
+                    if (restart && restarts < kMaxRestarts) ++restarts;
+                    else restarts = -1;
                 }
             }
             k_scatter<<<g, 256, 0, s>>>(xs.as<double>(), P.perm.as<int32_t>(), n, xo);
             IMQ_LAUNCH_CHECK();
-            IMQ_CUDA(cudaStreamSynchronize(s));
+            check_device_errors(s);   // synchronises; a wait that ran out invalidates the solve
             double rhs_worst = 0;
             int rhs_iter = 0;
             for (int b = 0; b < B; ++b) {

@@ -1,9 +1,11 @@
+#include <string>
 // Host utilities of the library: error handling, device memory, exclusive scan.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 
 #include "imq_internal.h"
+#include "ptx.cuh"
 #include "util.cuh"
 
 namespace imq {
@@ -99,6 +101,19 @@ int *device_error_word() {
         g_err_word[dev] = p;
     }
     return g_err_word[dev];
+}
+
+void check_device_errors(cudaStream_t s) {
+    int *w = device_error_word();
+    int h = 0;
+    IMQ_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        IMQ_CUDA(cudaMemsetAsync(w, 0, sizeof(int), s));
+        IMQ_CUDA(cudaStreamSynchronize(s));
+        if (h & kErrWaitTimeout) fail(IMQ_TIMEOUT, "a bounded wait in a kernel ran out; results are invalid");
+        fail(IMQ_CUDA_ERROR, "a kernel reported error flags " + std::to_string(h));
+    }
 }
 
 // ------------------------------------------------------------------ scan

@@ -14,6 +14,10 @@ void exclusive_scan(const T *d_in, T *d_out, int64_t n, T *d_total, cudaStream_t
 // Per-device error word that kernels OR their DeviceError codes into.
 int *device_error_word();
 
+// Synchronise `s`, read and clear the device error word; throws IMQ_TIMEOUT if a
+// bounded wait ran out since the last check (the affected results are invalid).
+void check_device_errors(cudaStream_t s);
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace imq

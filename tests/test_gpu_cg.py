@@ -96,3 +96,21 @@ def test_multiple_rhs_host_buffers_and_determinism():
     assert np.array_equal(a, host(b))                        # bit-reproducible
     for r in range(2):
         assert OS.true_relres(pts, c, a[r], F[r]) < 2e-7
+
+
+def test_flat_shape_breakdown_returns_best_iterate():
+    """c = 30 x the mean nearest-neighbour spacing: A is SPD but numerically
+    singular, the FP32 product is not positive on every direction, and CG can
+    break down.  The solve must then restart from its best iterate, never report
+    a breakdown as a NaN, and report the true residual of the iterate it returns."""
+    imq = _imq()
+    pts = W.uniform_points(4000, 6)
+    c = 30.0 * W.mean_nn_spacing(pts)
+    f = W.franke(pts)
+    plan = imq.Plan(cuda(pts), c, 12, 64)
+    coef, info = plan.solve(cuda(f), rtol=1e-6, maxit=400, precond="schwarz", schwarz_nmax=128,
+                            schwarz_shift=1e-5, residual="dense")
+    assert info["status"] in ("IMQ_OK", "IMQ_NOT_CONVERGED"), info
+    r = OS.true_relres(pts, c, host(coef), f)
+    assert np.isfinite(r) and r < 0.1, (r, info)
+    assert info["max_rel_residual"] == pytest.approx(r, rel=1e-2, abs=1e-12)
