@@ -63,7 +63,7 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -136,7 +136,7 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "n": n, "c": wl.c, "p": args.p, "leaf": wl.leaf},
+            "config": {"workload": wl.name, "n": n, "c": wl.c, "p": wl.p, "leaf": wl.leaf},
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": dense.num_threads(), "kind": "oracle",
                              "sample": f"{rows_per_step} rows of the FP64 dense product per step, "
                                        f"scaled by N/rows to one full A v"},
@@ -153,9 +153,16 @@ def run_batched(args, imq, dev):
     pts = [torch.from_numpy(x).to(dev) for x, _, _ in probs]
     cs = [c for _, c, _ in probs]
     f = torch.from_numpy(np.concatenate([r for _, _, r in probs], axis=1)).to(dev)   # [4, N_total]
+    # leaf size and p by the autotuner: 1e-6 on 32 sampled rows of every problem, 4 right-hand sides
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bp = imq.BatchedPlan(pts, cs, 12, 64, domain=(0.0, 0.0, 1.0))
+    tune = imq.autotune(pts, cs, 1e-6, p_candidates=(8, 10, 12, 14, 16), leaf_candidates=(32, 64, 128), nrhs=4,
+                        domain=(0.0, 0.0, 1.0))
+    tune_s = time.perf_counter() - t0
+    P_b, leaf_b = tune["p"], tune["leaf"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bp = imq.BatchedPlan(pts, cs, P_b, leaf_b, domain=(0.0, 0.0, 1.0))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     n_tot = bp.n
@@ -183,7 +190,10 @@ def run_batched(args, imq, dev):
                           schwarz_shift=1e-5)
     rel = info["problem_rel_residual"]
     bp.close()
-    return {"n_problems": len(probs), "n_total": n_tot, "nrhs": 4, "p": 12, "leaf": 64,
+    return {"n_problems": len(probs), "n_total": n_tot, "nrhs": 4, "p": P_b, "leaf": leaf_b,
+            "autotune": {"seconds": tune_s, "met": tune["met"], "rel_err": tune["rel_err"],
+                         "sampled_rows": tune["sampled_rows"],
+                         "tried": [(t["p"], t["leaf"], t["rel_err"], t["matvec_ms"]) for t in tune["tried"]]},
             "plan_build_s": build_s, "matvec_f32_ms": mv_ms,
             "matvec_points_per_s": 4 * n_tot / (mv_ms * 1e-3),
             "sampled_rel2_err_max": max(errs), "sampled_problems": 8,
@@ -276,10 +286,12 @@ def run_solves(args, imq, wl, d_pts, plan, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--p", type=int, default=12)
+    ap.add_argument("--p", type=int, default=None,
+                    help="expansion order; default: the autotuner's smallest p in {8, 12, 16} that meets 1e-6")
+    ap.add_argument("--phase-steps", type=int, default=20, help="products timed phase by phase (after the timed region)")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the clustered workload (tests)")
     ap.add_argument("--dense-reps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -295,7 +307,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_2205_04194_gb300 import workloads as W
-    wl = W.clustered_1m(p=args.p, scale=args.scale)
+    wl = W.clustered_1m(p=args.p or 12, scale=args.scale)
 
     if args.impl == "reference":
         if rank == 0:
@@ -324,6 +336,15 @@ def main():
     d_out = torch.empty_like(d_v)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    tune = None
+    if args.p is None:
+        # the configuration's p in {8, 12, 16}: the smallest whose product meets 1e-6 on sampled rows
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tune = imq.autotune(d_pts, wl.c, 1e-6, p_candidates=(8, 12, 16), leaf_candidates=(wl.leaf,),
+                            domain=wl.domain)
+        tune["seconds"] = time.perf_counter() - t0
+        wl.p = tune["p"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plan = imq.Plan(d_pts, wl.c, wl.p, wl.leaf, domain=wl.domain)
@@ -335,9 +356,9 @@ def main():
         plan.matvec(d_v, d_out)
     torch.cuda.synchronize()
 
+    # launches of one product (counted by the library), for gpu_launches
+    _, _, per_product = plan.matvec_timed(d_v, d_out)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    phase_tot = {k: 0.0 for k in imq.Plan.PHASES}
-    launches = 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -345,21 +366,26 @@ def main():
         for k in range(args.steps):
             flush.fill_(float(k))                 # untimed L2 flush
             ev[k][0].record(stream)
-            _, ph, nl = plan.matvec_timed(d_v, d_out)
+            plan.matvec(d_v, d_out)
             ev[k][1].record(stream)
-            for key, val in ph.items():
-                phase_tot[key] += val
-            launches += nl
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    launches = per_product * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    phase_ms = {k: v / args.steps for k, v in phase_tot.items()}
+    # phase breakdown (library events around each phase's kernels), outside the timed region
+    phase_tot = {k: 0.0 for k in imq.Plan.PHASES}
+    for k in range(args.phase_steps):
+        flush.fill_(float(k))
+        _, ph, _ = plan.matvec_timed(d_v, d_out)
+        for key, val in ph.items():
+            phase_tot[key] += val
+    phase_ms = {k: v / max(1, args.phase_steps) for k, v in phase_tot.items()}
 
     # dense GPU product (the plain form) on the same input
     dense_ms = None
@@ -461,6 +487,8 @@ def main():
         "dense_gpu_ms": dense_ms,
         "speedup_vs_dense_gpu": (dense_ms / ms) if dense_ms else None,
         "plan_ms": plan_ms,
+        "autotune": tune,
+        "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         "phase_ms": phase_ms,
         "p2p_gpair_s": p2p_gps, "m2l_tflop_s": m2l_tf,
         "errors": err,

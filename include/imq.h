@@ -340,6 +340,76 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
                                     float *out, void *stream);
 
 /* ------------------------------------------------------------------------- *
+ * imq_autotune -- choose the truncation order p and the leaf size.
+ *
+ *   The paper fixes M (= p) from the a-priori bound of Theorem 2.1 (worked
+ *   example, Section 2.2) and the number of levels L by balancing the far-
+ *   and near-field multiplication counts (Section 2.3).  Here both are
+ *   measured: for each leaf size in leaf_cand, the smallest p in p_cand whose
+ *   FP32 fast product meets `target` (relative 2-norm error on sampled rows,
+ *   worst over problems and right-hand sides), then the fastest of those.
+ *   If no candidate meets the target, the most accurate one is returned and
+ *   met = 0.
+ *
+ *   points  : double[N][2], host or device, N = offsets[nprob].
+ *   offsets : HOST int64[nprob + 1], offsets[0] = 0 (problem q owns points
+ *             [offsets[q], offsets[q+1])); nprob = 1 tunes imq_plan, nprob > 1
+ *             tunes imq_plan_batched.
+ *   cvals   : HOST double[nprob], the shapes c.
+ *   target  : > 0, e.g. 1e-6.
+ *   p_cand  : HOST int32[n_p], 1 <= n_p <= 16, each in [1, IMQ_MAX_P].
+ *   leaf_cand : HOST int32[n_leaf], 1 <= n_leaf <= 16, each >= 1.
+ *   nrhs    : right-hand sides of the timed product, 1..16.
+ *   opt     : plan options (domain, M2L kernel), may be NULL.
+ *   out     : HOST result; out->tried lists every configuration measured.
+ *
+ *   Sample: 2048 rows (single problem) or 32 rows per problem, evenly spaced
+ *   in the caller's order; the test vectors are SplitMix64 values in [-1, 1);
+ *   exact rows are FP64 direct sums.  The time of a configuration is the best
+ *   of 3 products after one warm-up (CUDA events on `stream`).  Builds and
+ *   frees one plan per configuration; synchronises `stream`.
+ *   Errors: IMQ_INVALID_ARG, those of imq_plan / imq_plan_batched /
+ *   imq_matvec.
+ * ------------------------------------------------------------------------- */
+#define IMQ_TUNE_MAX_TRIED 64
+typedef struct imq_tune_entry {
+    int32_t p, leaf;
+    double rel_err;          /* sampled relative 2-norm error of the FP32 product */
+    float matvec_ms;         /* best of the timed products                         */
+    int32_t reserved;
+} imq_tune_entry;
+
+typedef struct imq_tune_result {
+    int32_t p, leaf;         /* the choice                                         */
+    double rel_err;
+    float matvec_ms;
+    int32_t met;             /* 1 if rel_err <= target                             */
+    int32_t n_tried;
+    int32_t sampled_rows;
+    imq_tune_entry tried[IMQ_TUNE_MAX_TRIED];
+} imq_tune_result;
+
+imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals,
+                        double target, const int32_t *p_cand, int n_p, const int32_t *leaf_cand,
+                        int n_leaf, int nrhs, const imq_options *opt, void *stream,
+                        imq_tune_result *out);
+
+/* ------------------------------------------------------------------------- *
+ * imq_sync_check -- synchronise `stream` and report a failed bounded wait.
+ *
+ *   The kernels that wait on shared-memory barriers or on a grid barrier (the
+ *   tensor-core M2L, the P2P source staging, the one-launch M2M/L2L) give up
+ *   after a fixed number of polls instead of hanging, and record that in a
+ *   per-device error word.  Calls that synchronise anyway (host output
+ *   buffers, imq_matvec_timed, imq_cg_solve) check it themselves; after
+ *   asynchronous imq_matvec calls on device buffers, call this before using
+ *   the results.  Clears the word.  (Not an operation of the paper.)
+ *   Errors: IMQ_TIMEOUT (a wait ran out since the last check: the results of
+ *   the products in between are invalid), IMQ_CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+imq_status imq_sync_check(void *stream);
+
+/* ------------------------------------------------------------------------- *
  * Introspection of a plan, for tests and benchmarks.
  * ------------------------------------------------------------------------- */
 typedef struct imq_plan_info {

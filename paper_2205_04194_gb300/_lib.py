@@ -52,6 +52,15 @@ class CgInfo(ctypes.Structure):
                 ("seconds", D), ("rel_residual", D * 16)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("p", I32), ("leaf", I32), ("rel_err", D), ("matvec_ms", ctypes.c_float), ("reserved", I32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("p", I32), ("leaf", I32), ("rel_err", D), ("matvec_ms", ctypes.c_float), ("met", I32),
+                ("n_tried", I32), ("sampled_rows", I32), ("tried", TuneEntry * 64)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "imq_plan": (INT, [P, I64, D, INT, INT, P, P, P]),
@@ -70,6 +79,8 @@ SIGNATURES = {
     "imq_cg_solve_batched": (INT, [P, P, P, INT, P, P, P, P, P]),
     "imq_interp_loss_grad": (INT, [P, P, P, P, P, INT, P, P, P, P, P, P]),
     "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
+    "imq_autotune": (INT, [P, P, INT, P, D, P, INT, P, INT, INT, P, P, P]),
+    "imq_sync_check": (INT, [P]),
     "imq_plan_get_info": (INT, [P, P]),
     "imq_plan_export_tree": (INT, [P, P, P, P, P, P, P, P, P]),
     "imq_plan_export_list": (INT, [P, CHAR, P, P]),

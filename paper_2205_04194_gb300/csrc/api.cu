@@ -334,6 +334,7 @@ static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq
     else scatter_sorted<double, double>(P, bs.as<double>(), static_cast<double *>(dout.ptr), nrhs, s);
     if (tm) { tm->stop(s); tm->launches += nrhs; }
     dout.finish();
+    if (dout.tmp || tm) check_device_errors(s);   // the call synchronises anyway
 }
 
 imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs, imq_dtype dt, void *stream) {
@@ -394,6 +395,37 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
         tm.collect(phase_ms, n_phases);
         if (launches) *launches = tm.launches;
     });
+}
+
+imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
+                        const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+                        const imq_options *opt, void *stream, imq_tune_result *out) {
+    return guard([&] {
+        if (!points || !offsets || !cvals || !p_cand || !leaf_cand || !out)
+            fail(IMQ_INVALID_ARG, "imq_autotune: NULL pointer");
+        if (nprob < 1) fail(IMQ_INVALID_ARG, "imq_autotune: nprob must be >= 1");
+        if (!(target > 0) || !std::isfinite(target)) fail(IMQ_INVALID_ARG, "imq_autotune: target must be > 0");
+        if (n_p < 1 || n_p > 16 || n_leaf < 1 || n_leaf > 16)
+            fail(IMQ_INVALID_ARG, "imq_autotune: need 1..16 candidates of p and of leaf");
+        if (nrhs < 1 || nrhs > 16) fail(IMQ_INVALID_ARG, "imq_autotune: nrhs must be in [1, 16]");
+        for (int k = 0; k < n_p; ++k)
+            if (p_cand[k] < 1 || p_cand[k] > IMQ_MAX_P) fail(IMQ_INVALID_ARG, "imq_autotune: p out of [1, IMQ_MAX_P]");
+        for (int k = 0; k < n_leaf; ++k)
+            if (leaf_cand[k] < 1) fail(IMQ_INVALID_ARG, "imq_autotune: leaf must be >= 1");
+        if (offsets[0] != 0) fail(IMQ_INVALID_ARG, "imq_autotune: offsets[0] must be 0");
+        for (int q = 0; q < nprob; ++q) {
+            if (offsets[q + 1] <= offsets[q]) fail(IMQ_INVALID_ARG, "imq_autotune: every problem needs >= 1 point");
+            if (!std::isfinite(cvals[q]) || cvals[q] <= 0) fail(IMQ_INVALID_ARG, "imq_autotune: c must be finite and > 0");
+        }
+        if (offsets[nprob] > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_autotune: too many points");
+        check_device();
+        autotune(points, offsets, nprob, cvals, target, p_cand, n_p, leaf_cand, n_leaf, nrhs, opt,
+                 static_cast<cudaStream_t>(stream), out);
+    });
+}
+
+imq_status imq_sync_check(void *stream) {
+    return guard([&] { check_device_errors(static_cast<cudaStream_t>(stream)); });
 }
 
 void imq_cg_default_options(imq_cg_options *o) {

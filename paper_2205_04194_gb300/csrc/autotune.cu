@@ -1,0 +1,206 @@
+// Autotuner: choose the truncation order p and the leaf size for a point set.
+//
+// The paper fixes M (= p) from its a-priori bound (Theorem 2.1 and the worked
+// example of Section 2.2) and picks the number of levels L by balancing the
+// far-field count against the near-field count (Section 2.3).  On the adaptive
+// tree the leaf size plays the role of L, and the bound is pessimistic for the
+// M2L-based product, so both are chosen here by measurement: for each leaf
+// size the smallest p whose FP32 product meets the target relative 2-norm
+// error on a sample of exactly computed rows, then the fastest of those.
+//
+// Everything runs through the public entry points (imq_plan, imq_plan_batched,
+// imq_matvec, imq_plan_destroy); the exact rows are an FP64 direct sum over
+// every source of the row's problem.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "imq_internal.h"
+#include "util.cuh"
+
+namespace imq {
+namespace {
+
+constexpr int kRowThreads = 256;
+constexpr int kRowsSingle = 2048;   // sampled rows of a single problem
+constexpr int kRowsPerProblem = 32; // sampled rows per problem of a batch
+constexpr int kTimedReps = 3;
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014), mapped to a float in [-1, 1).
+__device__ __forceinline__ float splitmix_pm1(uint64_t i) {
+    uint64_t z = (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)((double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0);
+}
+
+__global__ void k_fill_pm1(float *__restrict__ v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = splitmix_pm1((uint64_t)i);
+}
+
+// exact[r * S + s] = sum_{j in [lo_s, hi_s)} v[r * N + j] / sqrt(|x_i - x_j|^2 + c_s^2), FP64,
+// for sampled row s (point i = row[s]); a fixed reduction tree per block.
+__global__ void __launch_bounds__(kRowThreads) k_exact_rows(const double2 *__restrict__ pts, int64_t N,
+                                                           const float *__restrict__ v, int nrhs,
+                                                           const int64_t *__restrict__ row, const int64_t *__restrict__ lo,
+                                                           const int64_t *__restrict__ hi, const double *__restrict__ cs,
+                                                           int S, double *__restrict__ exact) {
+    __shared__ double sh[kRowThreads];
+    const int s = blockIdx.x;
+    const double2 xi = pts[row[s]];
+    const double c2 = cs[s] * cs[s];
+    for (int r = 0; r < nrhs; ++r) {
+        const float *vr = v + (int64_t)r * N;
+        double acc = 0;
+        for (int64_t j = lo[s] + threadIdx.x; j < hi[s]; j += kRowThreads) {
+            const double dx = xi.x - pts[j].x, dy = xi.y - pts[j].y;
+            acc += (double)vr[j] * rsqrt(dx * dx + dy * dy + c2);
+        }
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int off = kRowThreads / 2; off > 0; off >>= 1) {
+            if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) exact[(int64_t)r * S + s] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_pick_rows(const float *__restrict__ b, int64_t N, int nrhs, const int64_t *__restrict__ row, int S,
+                            float *__restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < (int64_t)nrhs * S) {
+        const int r = (int)(e / S), s = (int)(e - (int64_t)r * S);
+        out[e] = b[(int64_t)r * N + row[s]];
+    }
+}
+
+void check(imq_status st) {
+    if (st != IMQ_OK) fail(st, std::string("imq_autotune: ") + imq_last_error());
+}
+
+struct PlanHolder {
+    imq_plan_t h = nullptr;
+    ~PlanHolder() { imq_plan_destroy(h); }
+};
+
+}  // namespace
+
+void autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
+              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+              const imq_options *opt, cudaStream_t s, imq_tune_result *out) {
+    const int64_t N = offsets ? offsets[nprob] : 0;
+    // ---- sampled rows: evenly spaced within each problem, in the caller's order
+    std::vector<int64_t> row, lo, hi;
+    std::vector<double> cs;
+    std::vector<int> prob_of;
+    for (int q = 0; q < nprob; ++q) {
+        const int64_t a = offsets[q], n = offsets[q + 1] - offsets[q];
+        const int64_t m = std::min<int64_t>(n, nprob == 1 ? kRowsSingle : kRowsPerProblem);
+        for (int64_t k = 0; k < m; ++k) {
+            row.push_back(a + (k * n) / m);
+            lo.push_back(a);
+            hi.push_back(a + n);
+            cs.push_back(cvals[q]);
+            prob_of.push_back(q);
+        }
+    }
+    const int S = (int)row.size();
+    AsyncMem d_pts(sizeof(double) * 2 * (size_t)N, s), d_v(sizeof(float) * (size_t)nrhs * N, s),
+        d_b(sizeof(float) * (size_t)nrhs * N, s), d_row(8 * (size_t)S, s), d_lo(8 * (size_t)S, s),
+        d_hi(8 * (size_t)S, s), d_c(8 * (size_t)S, s), d_exact(8 * (size_t)S * nrhs, s),
+        d_pick(4 * (size_t)S * nrhs, s);
+    IMQ_CUDA(cudaMemcpyAsync(d_pts.ptr, points, sizeof(double) * 2 * (size_t)N, cudaMemcpyDefault, s));
+    IMQ_CUDA(cudaMemcpyAsync(d_row.ptr, row.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyAsync(d_lo.ptr, lo.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyAsync(d_hi.ptr, hi.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyAsync(d_c.ptr, cs.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
+    k_fill_pm1<<<blocks_for((int64_t)nrhs * N, 256), 256, 0, s>>>(d_v.as<float>(), (int64_t)nrhs * N);
+    IMQ_LAUNCH_CHECK();
+    k_exact_rows<<<S, kRowThreads, 0, s>>>(d_pts.as<double2>(), N, d_v.as<float>(), nrhs, d_row.as<int64_t>(),
+                                           d_lo.as<int64_t>(), d_hi.as<int64_t>(), d_c.as<double>(), S,
+                                           d_exact.as<double>());
+    IMQ_LAUNCH_CHECK();
+    std::vector<double> exact((size_t)S * nrhs);
+    IMQ_CUDA(cudaMemcpyAsync(exact.data(), d_exact.ptr, 8 * exact.size(), cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+
+    std::vector<int32_t> ps(p_cand, p_cand + n_p);
+    std::sort(ps.begin(), ps.end());
+    ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
+    cudaEvent_t e0, e1;
+    IMQ_CUDA(cudaEventCreate(&e0));
+    IMQ_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev{e0, e1};
+    std::vector<float> picked((size_t)S * nrhs);
+    std::memset(out, 0, sizeof(*out));
+    for (int li = 0; li < n_leaf; ++li) {
+        for (int p : ps) {
+            PlanHolder plan;
+            if (nprob == 1)
+                check(imq_plan(d_pts.as<double>(), N, cvals[0], p, leaf_cand[li], opt, s, &plan.h));
+            else
+                check(imq_plan_batched(d_pts.as<double>(), offsets, nprob, cvals, p, leaf_cand[li], opt, s, &plan.h));
+            check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));   // warm-up, and the error sample
+            k_pick_rows<<<blocks_for((int64_t)S * nrhs, 256), 256, 0, s>>>(d_b.as<float>(), N, nrhs,
+                                                                           d_row.as<int64_t>(), S, d_pick.as<float>());
+            IMQ_LAUNCH_CHECK();
+            IMQ_CUDA(cudaMemcpyAsync(picked.data(), d_pick.ptr, 4 * picked.size(), cudaMemcpyDeviceToHost, s));
+            float best_ms = INFINITY;
+            for (int rep = 0; rep < kTimedReps; ++rep) {
+                IMQ_CUDA(cudaEventRecord(e0, s));
+                check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));
+                IMQ_CUDA(cudaEventRecord(e1, s));
+                IMQ_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                IMQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                best_ms = std::min(best_ms, ms);
+            }
+            // relative 2-norm error over the sampled rows, per problem and right-hand side; the worst
+            std::vector<double> num((size_t)nprob * nrhs, 0.0), den((size_t)nprob * nrhs, 0.0);
+            for (int r = 0; r < nrhs; ++r)
+                for (int k = 0; k < S; ++k) {
+                    const double e = exact[(size_t)r * S + k], d = (double)picked[(size_t)r * S + k] - e;
+                    num[(size_t)r * nprob + prob_of[k]] += d * d;
+                    den[(size_t)r * nprob + prob_of[k]] += e * e;
+                }
+            double err = 0;
+            for (size_t k = 0; k < num.size(); ++k)
+                err = std::max(err, den[k] > 0 ? std::sqrt(num[k] / den[k]) : std::sqrt(num[k]));
+            if (out->n_tried < IMQ_TUNE_MAX_TRIED) {
+                imq_tune_entry &t = out->tried[out->n_tried++];
+                t.p = p;
+                t.leaf = leaf_cand[li];
+                t.rel_err = err;
+                t.matvec_ms = best_ms;
+            }
+            if (err <= target) break;   // the smallest p that meets the target at this leaf size
+        }
+    }
+    // the fastest configuration that meets the target, else the most accurate one
+    int best = -1;
+    for (int k = 0; k < out->n_tried; ++k) {
+        const imq_tune_entry &t = out->tried[k];
+        if (t.rel_err > target) continue;
+        if (best < 0 || t.matvec_ms < out->tried[best].matvec_ms) best = k;
+    }
+    out->met = best >= 0 ? 1 : 0;
+    if (best < 0)
+        for (int k = 0; k < out->n_tried; ++k)
+            if (best < 0 || out->tried[k].rel_err < out->tried[best].rel_err) best = k;
+    out->p = out->tried[best].p;
+    out->leaf = out->tried[best].leaf;
+    out->rel_err = out->tried[best].rel_err;
+    out->matvec_ms = out->tried[best].matvec_ms;
+    out->sampled_rows = S;
+}
+
+}  // namespace imq

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CgInfo, CgOptions, ImqError, ImqOptions, PlanInfo, call
+from ._lib import CgInfo, CgOptions, ImqError, ImqOptions, PlanInfo, TuneResult, call
 
 F32 = 0
 F64 = 1
@@ -333,8 +333,49 @@ def dense_matvec_noalloc(points, c: float, v, out, stream=None):
     return out
 
 
+def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
+             leaf_candidates=(32, 64, 128), nrhs: int = 1, domain=None, m2l_kernel: str = "auto", stream=None):
+    """imq_autotune: the measured choice of (p, leaf) for one point set, or for a batch.
+
+    points: [N, 2] float64 (host or CUDA) with a scalar c, or a list of [N_b, 2]
+    arrays with a list of c_b (batched plans).  Returns a dict with the choice
+    ("p", "leaf", "rel_err", "matvec_ms", "met") and every measured
+    configuration under "tried".
+    """
+    if isinstance(points, (list, tuple)):
+        sizes = [int(np.shape(x)[0]) for x in points]
+        if all(isinstance(x, torch.Tensor) and x.is_cuda for x in points):
+            pts = torch.cat([x.to(torch.float64) for x in points]).contiguous()
+        else:
+            pts = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in points]))
+        cs = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+    else:
+        sizes = [int(np.shape(points)[0])]
+        pts = points
+        cs = np.array([float(c)], dtype=np.float64)
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(sizes)
+    pc = np.ascontiguousarray(np.asarray(p_candidates, dtype=np.int32))
+    lc = np.ascontiguousarray(np.asarray(leaf_candidates, dtype=np.int32))
+    pp, kp = _buf(pts, torch.float64)
+    opt = _plan_options(domain, False, m2l_kernel)
+    res = TuneResult()
+    call("imq_autotune", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes), ctypes.c_void_p(cs.ctypes.data),
+         float(target), ctypes.c_void_p(pc.ctypes.data), len(pc), ctypes.c_void_p(lc.ctypes.data), len(lc),
+         int(nrhs), ctypes.byref(opt), _stream(stream), ctypes.byref(res))
+    tried = [{"p": res.tried[k].p, "leaf": res.tried[k].leaf, "rel_err": res.tried[k].rel_err,
+              "matvec_ms": res.tried[k].matvec_ms} for k in range(res.n_tried)]
+    return {"p": res.p, "leaf": res.leaf, "rel_err": res.rel_err, "matvec_ms": res.matvec_ms,
+            "met": bool(res.met), "sampled_rows": res.sampled_rows, "tried": tried}
+
+
+def sync_check(stream=None) -> None:
+    """imq_sync_check: synchronise the stream; raise ImqError(IMQ_TIMEOUT) if a kernel's bounded wait ran out."""
+    call("imq_sync_check", _stream(stream))
+
+
 def version() -> str:
     return _lib.load().imq_version().decode()
 
 
-__all__ = ["Plan", "EvalPlan", "BatchedPlan", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
+__all__ = ["Plan", "EvalPlan", "BatchedPlan", "autotune", "sync_check", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]

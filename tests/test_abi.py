@@ -70,3 +70,27 @@ def test_oracle_builds_and_is_not_linked_by_the_product(lib):
     # the product library references no oracle symbol
     for name in ("oracle_dense_matvec", "oracle_evaluate"):
         assert not hasattr(lib, name)
+
+
+def test_autotune_arguments_rejected_before_any_gpu_work(lib):
+    from paper_2205_04194_gb300 import _lib
+    L = _lib.load()
+    res = _lib.TuneResult()
+    pts = (ctypes.c_double * 4)(0.0, 0.0, 1.0, 1.0)
+    offs = (ctypes.c_int64 * 2)(0, 2)
+    cs = (ctypes.c_double * 1)(0.1)
+    ps = (ctypes.c_int32 * 2)(8, 12)
+    leaves = (ctypes.c_int32 * 1)(32)
+    args = lambda **kw: [kw.get("pts", pts), kw.get("offs", offs), kw.get("nprob", 1), kw.get("cs", cs),
+                         kw.get("target", 1e-6), kw.get("ps", ps), kw.get("n_p", 2), leaves, kw.get("n_leaf", 1),
+                         kw.get("nrhs", 1), None, None, ctypes.byref(res)]
+    assert L.imq_autotune(*args(target=0.0)) == 1
+    assert L.imq_autotune(*args(target=float("nan"))) == 1
+    assert L.imq_autotune(*args(n_p=0)) == 1
+    assert L.imq_autotune(*args(n_leaf=17)) == 1
+    assert L.imq_autotune(*args(nrhs=0)) == 1
+    assert L.imq_autotune(*args(ps=(ctypes.c_int32 * 2)(8, 99))) == 1
+    assert L.imq_autotune(*args(cs=(ctypes.c_double * 1)(-1.0))) == 1
+    assert L.imq_autotune(*args(offs=(ctypes.c_int64 * 2)(0, 0))) == 1
+    assert L.imq_autotune(*args(pts=None)) == 1
+    assert ctypes.sizeof(_lib.TuneResult) == 32 + 64 * 24   # the C struct (sizeof checked with gcc)

@@ -1,0 +1,94 @@
+"""imq_autotune: the measured choice of (p, leaf).
+
+The autotuner's test vectors are SplitMix64 values (Steele, Lea and Flood,
+OOPSLA 2014), re-generated here from that published definition, so every
+error it reports is recomputed independently: the GPU product of a plan with
+the same (p, leaf) against the FP64 oracle rows at the same sampled rows.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, need_gpu
+from oracle import dense
+from paper_2205_04194_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def splitmix_pm1(n):
+    """Outputs 0..n-1 of SplitMix64 from state 0, mapped to float32 in [-1, 1)."""
+    with np.errstate(over="ignore"):
+        z = (np.arange(n, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return ((z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 * 2.0 - 1.0).astype(np.float32)
+
+
+def _rows(n, m):
+    m = min(n, m)
+    return (np.arange(m, dtype=np.int64) * n) // m
+
+
+def _imq():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    return imq
+
+
+def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
+    import torch
+    imq = _imq()
+    pts = W.uniform_points(20000, 21)
+    c = 2.0 * W.mean_nn_spacing(pts)
+    target = 1e-6
+    res = imq.autotune(cuda(pts), c, target, p_candidates=(4, 6, 8, 10, 12, 14), leaf_candidates=(32, 64))
+    assert res["met"] and res["rel_err"] <= target, res
+    assert res["sampled_rows"] == 2048
+    v = splitmix_pm1(pts.shape[0])
+    rows = _rows(pts.shape[0], 2048)
+    exact = dense.matvec_rows(pts, c, v.astype(np.float64), rows)
+    for leaf in (32, 64):
+        tried = [t for t in res["tried"] if t["leaf"] == leaf]
+        ps = [t["p"] for t in tried]
+        assert ps == sorted(ps) and ps[0] == 4
+        # ascending p until the first that meets the target
+        assert all(t["rel_err"] > target for t in tried[:-1]) and tried[-1]["rel_err"] <= target
+        for t in tried:
+            plan = imq.Plan(cuda(pts), c, t["p"], leaf)
+            b = host(plan.matvec(cuda(v, torch.float32)))
+            err = np.linalg.norm(b[rows] - exact) / np.linalg.norm(exact)
+            assert err == pytest.approx(t["rel_err"], rel=1e-3), (t, err)
+            plan.close()
+    chosen = [t for t in res["tried"] if t["p"] == res["p"] and t["leaf"] == res["leaf"]]
+    assert chosen and all(chosen[0]["matvec_ms"] <= t["matvec_ms"] for t in res["tried"] if t["rel_err"] <= target)
+
+
+def test_batched_choice_meets_the_target_on_every_problem():
+    import torch
+    imq = _imq()
+    g = np.random.default_rng(22)
+    sizes = [1500, 2600, 4100, 6000]
+    cs = g.uniform(0.02, 0.1, len(sizes))
+    pts = [W.uniform_points(n, 22, stream=200 + b) for b, n in enumerate(sizes)]
+    nrhs = 2
+    res = imq.autotune([cuda(x) for x in pts], cs, 1e-6, p_candidates=(6, 8, 10, 12, 14),
+                       leaf_candidates=(32, 64), nrhs=nrhs, domain=(0.0, 0.0, 1.0))
+    assert res["met"], res
+    assert res["sampled_rows"] == 32 * len(sizes)
+    n = sum(sizes)
+    v = splitmix_pm1(nrhs * n).reshape(nrhs, n)
+    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, res["p"], res["leaf"], domain=(0.0, 0.0, 1.0))
+    b = host(bp.matvec(cuda(v, torch.float32)))
+    worst = 0.0
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for q, (x, c) in enumerate(zip(pts, cs)):
+        rows = _rows(sizes[q], 32)
+        for r in range(nrhs):
+            vq = v[r, offs[q]:offs[q + 1]].astype(np.float64)
+            exact = dense.matvec_rows(x, c, vq, rows)
+            got = b[r, offs[q]:offs[q + 1]][rows]
+            worst = max(worst, np.linalg.norm(got - exact) / np.linalg.norm(exact))
+    assert worst == pytest.approx(res["rel_err"], rel=1e-3)
+    assert worst <= 1e-6
+    bp.close()
