@@ -16,7 +16,9 @@
 // is G_m^m times a real sequence g_n (g_m = 1) that obeys the normalised
 // three-term recurrence in n; column m contributes Re( G_m^m * sum_n g_n Mh_n^m ).
 // The recurrence coefficients live in __constant__ memory, so with P fixed
-// every coefficient is an operand of the FMA that uses it.
+// every coefficient is an operand of the FMA that uses it.  The M2P terms run
+// first, one warp per (W entry, 32 points), into per-entry partial sums that
+// the L2P kernel adds in W-list order.
 #include <cmath>
 #include <vector>
 
@@ -37,26 +39,89 @@ __constant__ float c_fm[kMaxP + 2];
 
 constexpr int kFarWarps = 4;
 
+// M2P of one W-list source S at up to 32 points of a leaf (one lane per point):
+// the value of Mh(S) at x, column by column.
 template <int P>
-__global__ void __launch_bounds__(32 * kFarWarps, 8) k_far_t(
+__device__ __forceinline__ float m2p_value(const u64 *cm, float vx, float vy, float c2, float c, float hs) {
+    const float inv = rsqrtf(vx * vx + vy * vy + c2);
+    const float a = hs * inv, t = c * inv;
+    const float ta = t * a, a2 = a * a;
+    const float zr0 = vx * inv * a, zi0 = vy * inv * a;
+    float gr = inv, gi = 0.f;   // G_m^m, from G_0^0
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            const float f = c_fm[m];
+            const float nr = (gr * zr0 - gi * zi0) * f;
+            gi = (gr * zi0 + gi * zr0) * f;
+            gr = nr;
+        }
+        const int k0 = cbase(P, m);
+        u64 sm = cm[k0];   // g_m = 1
+        float g1 = 1.f, g2 = 0.f;
+#pragma unroll
+        for (int n = m + 1; n <= P; ++n) {
+            const float g = c_rec_a[n * (kMaxP + 1) + m] * ta * g1 - c_rec_b[n * (kMaxP + 1) + m] * a2 * g2;
+            g2 = g1;
+            g1 = g;
+            if (((n + m) & 1) == 0) sm = fma2(pk2(g, g), cm[k0 + (n - m) / 2], sm);
+        }
+        float sr, si;
+        up2(sm, sr, si);
+        const float eps = m ? 2.f : 1.f;
+        acc = fmaf(eps, gr * sr - gi * si, acc);
+    }
+    return acc;
+}
+
+// M2P work items, one warp each: item = (target leaf b, W source s, first point i0,
+// offset of its 32 partial sums).  Splitting the W lists over warps keeps a leaf
+// with a long W list from becoming the kernel's critical path.
+template <int P>
+__global__ void __launch_bounds__(32 * kFarWarps, 8) k_m2p_t(
+    int nitems, const int4 *__restrict__ items, const int32_t *__restrict__ end, const int32_t *__restrict__ level,
+    const double2 *__restrict__ centre, const float2 *__restrict__ loc, const float *__restrict__ M, int K, double S,
+    ShapeC shape, float *__restrict__ wpart) {
+    constexpr int NC = ncplx(P);
+    __shared__ __align__(8) u64 s_cm[kFarWarps][NC];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * kFarWarps + wib;
+    if (warp >= nitems) return;
+    u64 *cm = s_cm[wib];
+    const int4 it = items[warp];
+    const int b = it.x, s = it.y, i = it.z + lane;
+    const float *Ms = M + (int64_t)s * K;
+    for (int k = lane; k < NC; k += 32) {
+        int m, slot;
+        decode_term<P>(k, m, slot);
+        cm[k] = pk2(Ms[slot], m ? Ms[slot + 1] : 0.f);
+    }
+    __syncwarp();
+    const float2 lp = i < end[b] ? loc[i] : make_float2(0.f, 0.f);
+    const double2 cb = centre[b], cs = centre[s];
+    const float c = (float)shape.of(b);
+    const float vx = lp.x + (float)(cb.x - cs.x), vy = lp.y + (float)(cb.y - cs.y);
+    const float hs = (float)(S / (double)(1 << level[s]));
+    wpart[it.w + lane] = m2p_value<P>(cm, vx, vy, c * c, c, hs);
+}
+
+// L2P at the points of each leaf, then the leaf's M2P partial sums added in W-list
+// order (the order of a serial loop over the list, so the sum is deterministic).
+template <int P>
+__global__ void __launch_bounds__(32 * kFarWarps, 8) k_l2p_t(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-    const int32_t *__restrict__ level, const double2 *__restrict__ centre, const float2 *__restrict__ loc,
-    const int32_t *__restrict__ woff, const int32_t *__restrict__ witems, const float *__restrict__ M,
-    const float *__restrict__ L, const float *__restrict__ coef, int K, double S, ShapeC shape,
-    float *__restrict__ bs) {
+    const int32_t *__restrict__ level, const float2 *__restrict__ loc, const int32_t *__restrict__ woff,
+    const int32_t *__restrict__ wbase, const float *__restrict__ L, const float *__restrict__ coef, int K, double S,
+    const float *__restrict__ wpart, float *__restrict__ bs) {
     constexpr int NC = ncplx(P);
     __shared__ __align__(8) u64 s_cl[kFarWarps][NC];   // per-warp L2P coefficients
-    __shared__ __align__(8) u64 s_cm[kFarWarps][NC];   // per-warp multipole of the current W source
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp = blockIdx.x * kFarWarps + wib;
     if (warp >= nleaf) return;
     u64 *cl = s_cl[wib];
-    u64 *cm = s_cm[wib];
     const int b = leaves[warp];
-    const double2 cb = centre[b];
     const float inv_h = 1.f / (float)(S / (double)(1 << level[b]));
-    const float c = (float)shape.of(b);
-    const float c2 = c * c;
     const float *Lb = L + (int64_t)b * K;
 
     // complex L2P coefficients of column m, term j: eps_m * norm * (Lr, Li)
@@ -69,79 +134,69 @@ __global__ void __launch_bounds__(32 * kFarWarps, 8) k_far_t(
     __syncwarp();
 
     const int i0 = begin[b], i1 = end[b];
-    const int we0 = woff[b], we1 = woff[b + 1];
-    for (int base = i0; base < i1; base += 32) {
+    const int nw = woff[b + 1] - woff[b], nch = (i1 - i0 + 31) >> 5;
+    const float *wp = wpart + wbase[warp];
+    for (int base = i0, ch = 0; base < i1; base += 32, ++ch) {
         const int i = base + lane;
         const bool act = i < i1;
         const float2 lp = act ? loc[i] : make_float2(0.f, 0.f);
         float phi = 0.f;
-        // ---- L2P
-        {
-            const float ux = lp.x * inv_h, uy = lp.y * inv_h;
-            const float r2 = ux * ux + uy * uy;
-            const u64 R2 = pk2(r2, r2);
-            float zr = 1.f, zi = 0.f;
+        const float ux = lp.x * inv_h, uy = lp.y * inv_h;
+        const float r2 = ux * ux + uy * uy;
+        const u64 R2 = pk2(r2, r2);
+        float zr = 1.f, zi = 0.f;
 #pragma unroll
-            for (int m = 0; m <= P; ++m) {
-                const int k0 = cbase(P, m), J = cnt_col(P, m);
-                u64 pm = cl[k0 + J - 1];
+        for (int m = 0; m <= P; ++m) {
+            const int k0 = cbase(P, m), J = cnt_col(P, m);
+            u64 pm = cl[k0 + J - 1];
 #pragma unroll
-                for (int j = J - 2; j >= 0; --j) pm = fma2(pm, R2, cl[k0 + j]);
-                float pr, pi;
-                up2(pm, pr, pi);
-                phi = fmaf(zr, pr, fmaf(-zi, pi, phi));
-                const float nr = zr * ux + zi * uy;
-                zi = zi * ux - zr * uy;
-                zr = nr;
-            }
+            for (int j = J - 2; j >= 0; --j) pm = fma2(pm, R2, cl[k0 + j]);
+            float pr, pi;
+            up2(pm, pr, pi);
+            phi = fmaf(zr, pr, fmaf(-zi, pi, phi));
+            const float nr = zr * ux + zi * uy;
+            zi = zi * ux - zr * uy;
+            zr = nr;
         }
-        // ---- M2P over the W list
-        for (int e = we0; e < we1; ++e) {
-            const int s = witems[e];
-            const float *Ms = M + (int64_t)s * K;
-            __syncwarp();
-            for (int k = lane; k < NC; k += 32) {
-                int m, slot;
-                decode_term<P>(k, m, slot);
-                cm[k] = pk2(Ms[slot], m ? Ms[slot + 1] : 0.f);
-            }
-            __syncwarp();
-            const double2 cs = centre[s];
-            const float vx = lp.x + (float)(cb.x - cs.x), vy = lp.y + (float)(cb.y - cs.y);
-            const float hs = (float)(S / (double)(1 << level[s]));
-            const float inv = rsqrtf(vx * vx + vy * vy + c2);
-            const float a = hs * inv, t = c * inv;
-            const float ta = t * a, a2 = a * a;
-            const float zr0 = vx * inv * a, zi0 = vy * inv * a;
-            float gr = inv, gi = 0.f;   // G_m^m, from G_0^0
-            float acc = 0.f;
-#pragma unroll
-            for (int m = 0; m <= P; ++m) {
-                if (m > 0) {
-                    const float f = c_fm[m];
-                    const float nr = (gr * zr0 - gi * zi0) * f;
-                    gi = (gr * zi0 + gi * zr0) * f;
-                    gr = nr;
-                }
-                const int k0 = cbase(P, m);
-                u64 sm = cm[k0];   // g_m = 1
-                float g1 = 1.f, g2 = 0.f;
-#pragma unroll
-                for (int n = m + 1; n <= P; ++n) {
-                    const float g = c_rec_a[n * (kMaxP + 1) + m] * ta * g1 - c_rec_b[n * (kMaxP + 1) + m] * a2 * g2;
-                    g2 = g1;
-                    g1 = g;
-                    if (((n + m) & 1) == 0) sm = fma2(pk2(g, g), cm[k0 + (n - m) / 2], sm);
-                }
-                float sr, si;
-                up2(sm, sr, si);
-                const float eps = m ? 2.f : 1.f;
-                acc = fmaf(eps, gr * sr - gi * si, acc);
-            }
-            phi += acc;
-        }
+        for (int e = 0; e < nw; ++e) phi += wp[((int64_t)e * nch + ch) * 32 + lane];
         if (act) bs[i] = phi;
     }
+}
+
+// Host: the M2P item table and each leaf's offset into the partial sums (once per plan).
+void ensure_m2p_items(Plan &P, cudaStream_t s) {
+    if (P.n_m2p_items >= 0) return;
+    const int nl = P.nleaf;
+    std::vector<int32_t> leaves(nl), beg(P.nbox), en(P.nbox), woff(P.nbox + 1), witems(std::max<int64_t>(1, P.W.total));
+    IMQ_CUDA(cudaMemcpyAsync(leaves.data(), P.leaves.ptr, 4 * (size_t)nl, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(beg.data(), P.begin.ptr, 4 * (size_t)P.nbox, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(en.data(), P.end.ptr, 4 * (size_t)P.nbox, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(woff.data(), P.W.off.ptr, 4 * (size_t)(P.nbox + 1), cudaMemcpyDeviceToHost, s));
+    if (P.W.total > 0)
+        IMQ_CUDA(cudaMemcpyAsync(witems.data(), P.W.items.ptr, 4 * (size_t)P.W.total, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> wbase(nl);
+    std::vector<int4> items;
+    int64_t off = 0;
+    for (int w = 0; w < nl; ++w) {
+        const int b = leaves[w];
+        const int nch = (en[b] - beg[b] + 31) / 32;
+        wbase[w] = (int32_t)off;
+        for (int e = woff[b]; e < woff[b + 1]; ++e)
+            for (int k = 0; k < nch; ++k) {
+                items.push_back(make_int4(b, witems[e], beg[b] + 32 * k, (int32_t)off));
+                off += 32;
+            }
+    }
+    if (off > 0x7FFFFFFF) fail(IMQ_UNSUPPORTED, "far field: too many M2P partial sums");
+    P.m2p_items.alloc(sizeof(int4) * std::max<size_t>(1, items.size()));
+    P.wbase.alloc(4 * (size_t)std::max(1, nl));
+    P.wpart.alloc(4 * (size_t)std::max<int64_t>(32, off));
+    if (!items.empty())
+        IMQ_CUDA(cudaMemcpyAsync(P.m2p_items.ptr, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+    if (nl > 0) IMQ_CUDA(cudaMemcpyAsync(P.wbase.ptr, wbase.data(), 4 * (size_t)nl, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    P.n_m2p_items = (int)items.size();
 }
 
 std::vector<int> g_tables_ready;   // per device
@@ -175,16 +230,22 @@ bool far_fixed_p_supported(int p) { return p >= 1 && p <= 16; }
 
 void far_fixed_p_prepare(cudaStream_t s) { upload_tables(s); }
 
-void far_fixed_p_launch(const Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s) {
-    const unsigned grid = (unsigned)((P.nleaf + kFarWarps - 1) / kFarWarps);
-    if (grid == 0) return;
-#define IMQ_FAR_CASE(PP)                                                                                        \
-    case PP:                                                                                                   \
-        k_far_t<PP><<<grid, 32 * kFarWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),    \
-                                                    P.end.as<int32_t>(), P.level.as<int32_t>(),                \
-                                                    P.centre.as<double2>(), P.loc.as<float2>(),                \
-                                                    P.W.off.as<int32_t>(), P.W.items.as<int32_t>(), M, L, coef, \
-                                                    P.layout.K, P.side, P.shape(), b);                         \
+void far_fixed_p_launch(Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s) {
+    if (P.nleaf == 0) return;
+    ensure_m2p_items(P, s);
+    const unsigned gi = (unsigned)((P.n_m2p_items + kFarWarps - 1) / kFarWarps);
+    const unsigned gl = (unsigned)((P.nleaf + kFarWarps - 1) / kFarWarps);
+#define IMQ_FAR_CASE(PP)                                                                                          \
+    case PP:                                                                                                     \
+        if (gi > 0)                                                                                              \
+            k_m2p_t<PP><<<gi, 32 * kFarWarps, 0, s>>>(P.n_m2p_items, P.m2p_items.as<int4>(), P.end.as<int32_t>(), \
+                                                      P.level.as<int32_t>(), P.centre.as<double2>(),             \
+                                                      P.loc.as<float2>(), M, P.layout.K, P.side, P.shape(),      \
+                                                      P.wpart.as<float>());                                      \
+        k_l2p_t<PP><<<gl, 32 * kFarWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),        \
+                                                  P.end.as<int32_t>(), P.level.as<int32_t>(), P.loc.as<float2>(), \
+                                                  P.W.off.as<int32_t>(), P.wbase.as<int32_t>(), L, coef,          \
+                                                  P.layout.K, P.side, P.wpart.as<float>(), b);                   \
         break;
     switch (P.p) {
         IMQ_FAR_CASE(1)

@@ -188,6 +188,11 @@ struct Plan {
     DevMem loc;        // float2[N]  offset from the leaf centre
     DevMem rec4;       // float4[N]  P2P source records (x, y, u, 0) of the current product
     DevMem leaf_of;    // int32[N]
+    // far field (FP32, fixed p): M2P items (leaf, W source, first point, partial offset)
+    DevMem m2p_items;  // int4[n_m2p_items]
+    DevMem wbase;      // int32[nleaf] offset of each leaf's M2P partial sums
+    DevMem wpart;      // float[32 * n_m2p_items] partial sums, W-entry major then 32-point chunk
+    int n_m2p_items = -1;   // -1: not built yet
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
     std::vector<double> h_m2l_odd, h_l2l_odd, h_dzc;   // derivative path ([lev][40][K][Ko], [4][Ko][Ko])
@@ -258,7 +263,7 @@ void p2l_fixed_p_launch(const Plan &P, const float *u, float *L, cudaStream_t s)
 // far.cu: L2P + M2P for a compile-time order (FP32)
 bool far_fixed_p_supported(int p);
 void far_fixed_p_prepare(cudaStream_t s);
-void far_fixed_p_launch(const Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s);
+void far_fixed_p_launch(Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s);
@@ -290,5 +295,10 @@ imq_status guarded_call(F &&f) {   // run f, translate exceptions into a status 
         return IMQ_CUDA_ERROR;
     }
 }
+
+// Measured choice of p and leaf size (autotune.cu); arguments already checked.
+void autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
+              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+              const imq_options *opt, cudaStream_t s, imq_tune_result *out);
 
 }  // namespace imq
