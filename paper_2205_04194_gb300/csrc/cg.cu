@@ -573,7 +573,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         cudaStreamDestroy(cs);
         IMQ_CUDA(ce);
     }
-    IMQ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    IMQ_CUDA(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);

@@ -290,7 +290,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
         cleanup();
         IMQ_CUDA(ce);
     }
-    ce = cudaGraphInstantiate(&exec, graph, 0);
+    ce = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     if (ce != cudaSuccess) {
         cleanup();
         IMQ_CUDA(ce);

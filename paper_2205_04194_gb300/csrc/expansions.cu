@@ -735,10 +735,108 @@ void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kou
 template void m2l_direct_launch<float>(Plan &, const float *, float *, const float *, int, int, cudaStream_t, int *);
 template void m2l_direct_launch<double>(Plan &, const double *, double *, const double *, int, int, cudaStream_t, int *);
 
+// FP32 product at a fixed order p <= 16.  The near field (P2P) and the W-list
+// M2P terms depend on the far-field chain only at its end, so without a phase
+// timer they run concurrently with the latency-bound chain
+// P2M -> M2M -> M2L -> P2L -> L2L, on the plan's two streams:
+//
+//   hi  : wait(fork), P2M, M2M, [mready], M2L, P2L, L2L, wait(join), L2P (+ W partials + near), [done]
+//   aux : wait(fork), P2P -> near, wait(mready), M2P -> W partials, [join]
+//   s   : [fork] ... wait(done)
+//
+// With a timer every phase runs on s in that order.  Either way b = L2P + the
+// W partials in list order + near, so both schedules give the same bits.
+int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStream_t s0, PhaseTimer *tm) {
+    TypedOps &O = P.ops32;
+    const int K = P.layout.K, nb = P.nbox;
+    float *M = O.M.as<float>(), *L = O.L.as<float>();
+    const float *m2m = O.m2m.as<float>(), *l2l = O.l2l.as<float>(), *m2l = O.m2l.as<float>(),
+                *coef = O.p2mc.as<float>();
+    ensure_m2p_items(P, s0);
+    if (!P.near.ptr) P.near.alloc(sizeof(float) * (size_t)P.N);
+    const bool conc = tm == nullptr;
+    if (conc) P.aux.ensure();
+    cudaStream_t sa = conc ? P.aux.s : s0, s = conc ? P.aux.hi : s0;
+    float *near = P.near.as<float>();
+    int launches = 0;
+    auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
+    auto t1 = [&]() { if (tm) tm->stop(s); };
+    for (int r = 0; r < nrhs; ++r) {
+        const float *u = us + (size_t)r * P.N;
+        float *b = bs + (size_t)r * P.N;
+        if (conc) {
+            IMQ_CUDA(cudaEventRecord(P.aux.fork, s0));
+            IMQ_CUDA(cudaStreamWaitEvent(s, P.aux.fork, 0));
+            IMQ_CUDA(cudaStreamWaitEvent(sa, P.aux.fork, 0));
+            p2p_near_f32(P, u, near, sa);
+            launches += 2;
+        }
+        IMQ_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)nb * K, s));
+        IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)nb * K, s));
+        t0(kPhP2M);
+        p2m_launch<float>(P, u, M, coef, s);
+        ++launches;
+        t1();
+        t0(kPhM2M);
+        m2m_levels<float>(P, M, m2m, s, &launches);
+        t1();
+        if (conc) {
+            IMQ_CUDA(cudaEventRecord(P.aux.mready, s));
+            IMQ_CUDA(cudaStreamWaitEvent(sa, P.aux.mready, 0));
+            far_m2p_launch(P, M, sa);
+            if (P.n_m2p_items > 0) ++launches;
+            IMQ_CUDA(cudaEventRecord(P.aux.join, sa));
+        }
+        t0(kPhM2L);
+        if (P.n_m2l_tiles > 0 && O.umma) {
+            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), K, s);
+            launches += 2;
+        } else if (P.n_m2l_tiles > 0) {
+            m2l_tiled_launch(P, M, L, m2l, s);
+            ++launches;
+        }
+        t1();
+        t0(kPhP2L);
+        if (P.X.total > 0) {
+            p2l_launch_impl<float, 0>(P, u, L, K, s);
+            ++launches;
+        }
+        t1();
+        t0(kPhL2L);
+        l2l_launch<float>(P, L, l2l, K, s, &launches);
+        t1();
+        if (!conc) {
+            t0(kPhP2P);
+            p2p_near_f32(P, u, near, s);
+            launches += 2;
+            t1();
+        }
+        t0(kPhFar);
+        if (conc) {
+            IMQ_CUDA(cudaStreamWaitEvent(s, P.aux.join, 0));
+        } else {
+            far_m2p_launch(P, M, s);
+            if (P.n_m2p_items > 0) ++launches;
+        }
+        far_l2p_launch(P, L, coef, near, b, s);
+        ++launches;
+        t1();
+        if (conc) {
+            IMQ_CUDA(cudaEventRecord(P.aux.done, s));
+            IMQ_CUDA(cudaStreamWaitEvent(s0, P.aux.done, 0));
+        }
+    }
+    if (tm) tm->launches += launches;
+    return launches;
+}
+
 template <class T>
 int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer *tm) {
     const bool f64 = std::is_same<T, double>::value;
     ensure_ops(P, f64, s);
+    if constexpr (std::is_same<T, float>::value) {
+        if (far_fixed_p_supported(P.p)) return fmm_apply_f32_fixed(P, us, bs, nrhs, s, tm);
+    }
     TypedOps &O = f64 ? P.ops64 : P.ops32;
     const int K = P.layout.K, p = P.p, nb = P.nbox;
     T *M = O.M.as<T>(), *L = O.L.as<T>();
@@ -746,7 +844,6 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
     int launches = 0;
     auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
     auto t1 = [&]() { if (tm) tm->stop(s); };
-    bool far_generic = false;
     for (int r = 0; r < nrhs; ++r) {
         const T *u = us + (size_t)r * P.N;
         T *b = bs + (size_t)r * P.N;
@@ -786,24 +883,16 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t1();
         // evaluation: L2P + M2P writes b, P2P adds the near field
         t0(kPhFar);
-        if constexpr (std::is_same<T, float>::value) {
-            if (far_fixed_p_supported(p)) far_fixed_p_launch(P, M, L, coef, b, s);
-            else far_generic = true;
-        } else {
-            far_generic = true;
-        }
-        if (far_generic) {
-            k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
-                P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
-                P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
-                P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, P.shape(), b);
-            IMQ_LAUNCH_CHECK();
-        }
+        k_far<T><<<blocks_for((int64_t)P.nleaf * 32, 128), 128, 0, s>>>(
+            P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.level.as<int32_t>(),
+            P.centre.as<double2>(), P.loc.as<float2>(), P.pos.as<double2>(), P.W.off.as<int32_t>(),
+            P.W.items.as<int32_t>(), M, L, coef, K, p, P.side, P.shape(), b);
+        IMQ_LAUNCH_CHECK();
         ++launches;
         t1();
         t0(kPhP2P);
         p2p_apply<T>(P, u, b, s);
-        ++launches;
+        launches += std::is_same<T, float>::value ? 2 : 1;
         t1();
     }
     if (tm) tm->launches += launches;

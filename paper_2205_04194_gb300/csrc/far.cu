@@ -107,13 +107,14 @@ __global__ void __launch_bounds__(32 * kFarWarps, 8) k_m2p_t(
 }
 
 // L2P at the points of each leaf, then the leaf's M2P partial sums added in W-list
-// order (the order of a serial loop over the list, so the sum is deterministic).
+// order (the order of a serial loop over the list, so the sum is deterministic),
+// then (if given) the point's near-field sum.
 template <int P>
 __global__ void __launch_bounds__(32 * kFarWarps, 8) k_l2p_t(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ level, const float2 *__restrict__ loc, const int32_t *__restrict__ woff,
     const int32_t *__restrict__ wbase, const float *__restrict__ L, const float *__restrict__ coef, int K, double S,
-    const float *__restrict__ wpart, float *__restrict__ bs) {
+    const float *__restrict__ wpart, const float *__restrict__ near, float *__restrict__ bs) {
     constexpr int NC = ncplx(P);
     __shared__ __align__(8) u64 s_cl[kFarWarps][NC];   // per-warp L2P coefficients
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -159,9 +160,11 @@ __global__ void __launch_bounds__(32 * kFarWarps, 8) k_l2p_t(
             zr = nr;
         }
         for (int e = 0; e < nw; ++e) phi += wp[((int64_t)e * nch + ch) * 32 + lane];
-        if (act) bs[i] = phi;
+        if (act) bs[i] = near ? phi + near[i] : phi;
     }
 }
+
+}  // namespace
 
 // Host: the M2P item table and each leaf's offset into the partial sums (once per plan).
 void ensure_m2p_items(Plan &P, cudaStream_t s) {
@@ -199,6 +202,8 @@ void ensure_m2p_items(Plan &P, cudaStream_t s) {
     P.n_m2p_items = (int)items.size();
 }
 
+namespace {
+
 std::vector<int> g_tables_ready;   // per device
 
 void upload_tables(cudaStream_t s) {
@@ -230,43 +235,44 @@ bool far_fixed_p_supported(int p) { return p >= 1 && p <= 16; }
 
 void far_fixed_p_prepare(cudaStream_t s) { upload_tables(s); }
 
-void far_fixed_p_launch(Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s) {
-    if (P.nleaf == 0) return;
+void far_m2p_launch(Plan &P, const float *M, cudaStream_t s) {
     ensure_m2p_items(P, s);
     const unsigned gi = (unsigned)((P.n_m2p_items + kFarWarps - 1) / kFarWarps);
-    const unsigned gl = (unsigned)((P.nleaf + kFarWarps - 1) / kFarWarps);
-#define IMQ_FAR_CASE(PP)                                                                                          \
-    case PP:                                                                                                     \
-        if (gi > 0)                                                                                              \
-            k_m2p_t<PP><<<gi, 32 * kFarWarps, 0, s>>>(P.n_m2p_items, P.m2p_items.as<int4>(), P.end.as<int32_t>(), \
-                                                      P.level.as<int32_t>(), P.centre.as<double2>(),             \
-                                                      P.loc.as<float2>(), M, P.layout.K, P.side, P.shape(),      \
-                                                      P.wpart.as<float>());                                      \
-        k_l2p_t<PP><<<gl, 32 * kFarWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),        \
-                                                  P.end.as<int32_t>(), P.level.as<int32_t>(), P.loc.as<float2>(), \
-                                                  P.W.off.as<int32_t>(), P.wbase.as<int32_t>(), L, coef,          \
-                                                  P.layout.K, P.side, P.wpart.as<float>(), b);                   \
+    if (gi == 0) return;
+#define IMQ_M2P_CASE(PP)                                                                                      \
+    case PP:                                                                                                 \
+        k_m2p_t<PP><<<gi, 32 * kFarWarps, 0, s>>>(P.n_m2p_items, P.m2p_items.as<int4>(), P.end.as<int32_t>(), \
+                                                  P.level.as<int32_t>(), P.centre.as<double2>(),             \
+                                                  P.loc.as<float2>(), M, P.layout.K, P.side, P.shape(),      \
+                                                  P.wpart.as<float>());                                      \
         break;
     switch (P.p) {
-        IMQ_FAR_CASE(1)
-        IMQ_FAR_CASE(2)
-        IMQ_FAR_CASE(3)
-        IMQ_FAR_CASE(4)
-        IMQ_FAR_CASE(5)
-        IMQ_FAR_CASE(6)
-        IMQ_FAR_CASE(7)
-        IMQ_FAR_CASE(8)
-        IMQ_FAR_CASE(9)
-        IMQ_FAR_CASE(10)
-        IMQ_FAR_CASE(11)
-        IMQ_FAR_CASE(12)
-        IMQ_FAR_CASE(13)
-        IMQ_FAR_CASE(14)
-        IMQ_FAR_CASE(15)
-        IMQ_FAR_CASE(16)
+        IMQ_M2P_CASE(1) IMQ_M2P_CASE(2) IMQ_M2P_CASE(3) IMQ_M2P_CASE(4) IMQ_M2P_CASE(5) IMQ_M2P_CASE(6)
+        IMQ_M2P_CASE(7) IMQ_M2P_CASE(8) IMQ_M2P_CASE(9) IMQ_M2P_CASE(10) IMQ_M2P_CASE(11) IMQ_M2P_CASE(12)
+        IMQ_M2P_CASE(13) IMQ_M2P_CASE(14) IMQ_M2P_CASE(15) IMQ_M2P_CASE(16)
         default: fail(IMQ_UNSUPPORTED, "far field: no fixed-order kernel for this p");
     }
-#undef IMQ_FAR_CASE
+#undef IMQ_M2P_CASE
+    IMQ_LAUNCH_CHECK();
+}
+
+void far_l2p_launch(Plan &P, const float *L, const float *coef, const float *near, float *b, cudaStream_t s) {
+    const unsigned gl = (unsigned)((P.nleaf + kFarWarps - 1) / kFarWarps);
+    if (gl == 0) return;
+#define IMQ_L2P_CASE(PP)                                                                                        \
+    case PP:                                                                                                   \
+        k_l2p_t<PP><<<gl, 32 * kFarWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),      \
+                                                  P.end.as<int32_t>(), P.level.as<int32_t>(), P.loc.as<float2>(), \
+                                                  P.W.off.as<int32_t>(), P.wbase.as<int32_t>(), L, coef,          \
+                                                  P.layout.K, P.side, P.wpart.as<float>(), near, b);             \
+        break;
+    switch (P.p) {
+        IMQ_L2P_CASE(1) IMQ_L2P_CASE(2) IMQ_L2P_CASE(3) IMQ_L2P_CASE(4) IMQ_L2P_CASE(5) IMQ_L2P_CASE(6)
+        IMQ_L2P_CASE(7) IMQ_L2P_CASE(8) IMQ_L2P_CASE(9) IMQ_L2P_CASE(10) IMQ_L2P_CASE(11) IMQ_L2P_CASE(12)
+        IMQ_L2P_CASE(13) IMQ_L2P_CASE(14) IMQ_L2P_CASE(15) IMQ_L2P_CASE(16)
+        default: fail(IMQ_UNSUPPORTED, "far field: no fixed-order kernel for this p");
+    }
+#undef IMQ_L2P_CASE
     IMQ_LAUNCH_CHECK();
 }
 

@@ -139,6 +139,19 @@ struct Schwarz {
     int64_t total_slots = 0;
 };
 
+// Streams and fork/join events of the concurrent FP32 product (per plan): the
+// far-field chain runs on a highest-priority stream, the near field on a
+// lowest-priority one, so free SM slots go to the latency-bound chain first.
+struct AuxStream {
+    cudaStream_t hi = nullptr, s = nullptr;
+    cudaEvent_t fork = nullptr, mready = nullptr, join = nullptr, done = nullptr;
+    void ensure();
+    AuxStream() = default;
+    AuxStream(const AuxStream &) = delete;
+    AuxStream &operator=(const AuxStream &) = delete;
+    ~AuxStream();
+};
+
 struct Plan {
     int device = 0;
     int64_t N = 0;
@@ -193,6 +206,8 @@ struct Plan {
     DevMem wbase;      // int32[nleaf] offset of each leaf's M2P partial sums
     DevMem wpart;      // float[32 * n_m2p_items] partial sums, W-entry major then 32-point chunk
     int n_m2p_items = -1;   // -1: not built yet
+    DevMem near;       // float[N] near-field (P2P) sums of the current FP32 product
+    AuxStream aux;     // the P2P / M2P stream of the concurrent FP32 product
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
     std::vector<double> h_m2l_odd, h_l2l_odd, h_dzc;   // derivative path ([lev][40][K][Ko], [4][Ko][Ko])
@@ -263,7 +278,12 @@ void p2l_fixed_p_launch(const Plan &P, const float *u, float *L, cudaStream_t s)
 // far.cu: L2P + M2P for a compile-time order (FP32)
 bool far_fixed_p_supported(int p);
 void far_fixed_p_prepare(cudaStream_t s);
-void far_fixed_p_launch(Plan &P, const float *M, const float *L, const float *coef, float *b, cudaStream_t s);
+void ensure_m2p_items(Plan &P, cudaStream_t s);   // host sync: call outside stream capture
+void far_m2p_launch(Plan &P, const float *M, cudaStream_t s);   // W-list M2P partial sums
+// b = L2P + the leaf's M2P partial sums (+ near[i] if near is not null)
+void far_l2p_launch(Plan &P, const float *L, const float *coef, const float *near, float *b, cudaStream_t s);
+// p2p.cu: near[i] = the P2P sum of point i (FP32, stored, not added)
+void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s);

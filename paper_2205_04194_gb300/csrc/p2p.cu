@@ -192,6 +192,8 @@ __device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase
     return lane_reduce<float, TC>(s, lane);
 }
 
+// STORE: write the near-field sum (b_near = sum); otherwise add it to bs.
+template <bool STORE>
 __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
@@ -229,7 +231,10 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
                                        udelta, loc, rec, c2, err);
             tcap = 16;
         }
-        if (lane < tcap && lane < ntc) bs[tb + tc + lane] += tot;
+        if (lane < tcap && lane < ntc) {
+            if (STORE) bs[tb + tc + lane] = tot;
+            else bs[tb + tc + lane] += tot;
+        }
     }
 }
 
@@ -284,28 +289,37 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
 
 }  // namespace
 
+template <bool STORE>
+void p2p_f32_launch(Plan &P, const float *u, float *bs, cudaStream_t s) {
+    const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
+    if (!P.rec4.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace missing");
+    k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u, P.N, P.rec4.as<float4>());
+    IMQ_LAUNCH_CHECK();
+    const size_t smem = sizeof(WarpStage) * kP2PWarps;
+    IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_p2p_f32<STORE><<<grid, 32 * kP2PWarps, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
+                                                        P.end.as<int32_t>(), P.U.off.as<int32_t>(),
+                                                        P.U.items.as<int32_t>(), P.ucum.as<int32_t>(),
+                                                        P.utot.as<int32_t>(), P.uoff.as<float2>(), P.loc.as<float2>(),
+                                                        P.rec4.as<float4>(), P.shape(), bs, device_error_word());
+    IMQ_LAUNCH_CHECK();
+}
+
 template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
-    const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
     if constexpr (std::is_same<T, float>::value) {
-        if (!P.rec4.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace missing");
-        k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u, P.N, P.rec4.as<float4>());
-        IMQ_LAUNCH_CHECK();
-        const size_t smem = sizeof(WarpStage) * kP2PWarps;
-        IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_p2p_f32<<<grid, 32 * kP2PWarps, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
-                                                     P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
-                                                     P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(),
-                                                     P.loc.as<float2>(), P.rec4.as<float4>(), P.shape(), bs,
-                                                     device_error_word());
+        p2p_f32_launch<false>(P, u, bs, s);
     } else {
+        const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
         k_p2p_f64<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
                                                   P.end.as<int32_t>(), P.U.off.as<int32_t>(), P.U.items.as<int32_t>(),
                                                   P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.pos.as<double2>(), u,
                                                   P.shape(), bs);
+        IMQ_LAUNCH_CHECK();
     }
-    IMQ_LAUNCH_CHECK();
 }
+
+void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s) { p2p_f32_launch<true>(P, u, near, s); }
 
 template void p2p_apply<float>(Plan &, const float *, float *, cudaStream_t);
 template void p2p_apply<double>(Plan &, const double *, double *, cudaStream_t);

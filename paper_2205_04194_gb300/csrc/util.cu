@@ -103,6 +103,27 @@ int *device_error_word() {
     return g_err_word[dev];
 }
 
+void AuxStream::ensure() {
+    if (s) return;
+    int least = 0, greatest = 0;
+    IMQ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    IMQ_CUDA(cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest));
+    IMQ_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least));
+    IMQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    IMQ_CUDA(cudaEventCreateWithFlags(&mready, cudaEventDisableTiming));
+    IMQ_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    IMQ_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+}
+
+AuxStream::~AuxStream() {
+    if (fork) cudaEventDestroy(fork);
+    if (mready) cudaEventDestroy(mready);
+    if (join) cudaEventDestroy(join);
+    if (done) cudaEventDestroy(done);
+    if (s) cudaStreamDestroy(s);
+    if (hi) cudaStreamDestroy(hi);
+}
+
 void check_device_errors(cudaStream_t s) {
     int *w = device_error_word();
     int h = 0;
