@@ -735,17 +735,18 @@ void m2l_direct_launch(Plan &P, const T *M, T *L, const T *ops, int Kin, int Kou
 template void m2l_direct_launch<float>(Plan &, const float *, float *, const float *, int, int, cudaStream_t, int *);
 template void m2l_direct_launch<double>(Plan &, const double *, double *, const double *, int, int, cudaStream_t, int *);
 
-// FP32 product at a fixed order p <= 16.  The near field (P2P) and the W-list
-// M2P terms depend on the far-field chain only at its end, so without a phase
-// timer they run concurrently with the latency-bound chain
-// P2M -> M2M -> M2L -> P2L -> L2L, on the plan's two streams:
+// FP32 product at a fixed order p <= 16.  P2L (X lists), the near field (P2P)
+// and the W-list M2P terms depend on the far-field chain only at its ends, so
+// without a phase timer they run concurrently with the latency-bound chain
+// P2M -> M2M -> M2L -> L2L, on the plan's two streams:
 //
-//   hi  : wait(fork), P2M, M2M, [mready], M2L, P2L, L2L, wait(join), L2P (+ W partials + near), [done]
-//   aux : wait(fork), P2P -> near, wait(mready), M2P -> W partials, [join]
-//   s   : [fork] ... wait(done)
+//   s0  : zero M and L, [fork] ... wait(done)
+//   hi  : wait(fork), P2M, M2M, [mready], wait(xready), M2L (+= L), L2L, wait(join), L2P (+ W partials + near), [done]
+//   aux : wait(fork), P2L (+= L), [xready], P2P -> near, wait(mready), M2P -> W partials, [join]
 //
-// With a timer every phase runs on s in that order.  Either way b = L2P + the
-// W partials in list order + near, so both schedules give the same bits.
+// With a timer every phase runs on s0 in the order P2M, M2M, P2L, M2L, L2L, P2P,
+// far.  Either way L = P2L terms + M2L terms, and b = L2P + the W partials in
+// list order + near, so both schedules give the same bits.
 int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStream_t s0, PhaseTimer *tm) {
     TypedOps &O = P.ops32;
     const int K = P.layout.K, nb = P.nbox;
@@ -759,20 +760,25 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     cudaStream_t sa = conc ? P.aux.s : s0, s = conc ? P.aux.hi : s0;
     float *near = P.near.as<float>();
     int launches = 0;
-    auto t0 = [&](int ph) { if (tm) tm->start(ph, s); };
-    auto t1 = [&]() { if (tm) tm->stop(s); };
+    auto t0 = [&](int ph) { if (tm) tm->start(ph, s0); };
+    auto t1 = [&]() { if (tm) tm->stop(s0); };
     for (int r = 0; r < nrhs; ++r) {
         const float *u = us + (size_t)r * P.N;
         float *b = bs + (size_t)r * P.N;
+        IMQ_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)nb * K, s0));
+        IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)nb * K, s0));
         if (conc) {
             IMQ_CUDA(cudaEventRecord(P.aux.fork, s0));
             IMQ_CUDA(cudaStreamWaitEvent(s, P.aux.fork, 0));
             IMQ_CUDA(cudaStreamWaitEvent(sa, P.aux.fork, 0));
+            if (P.X.total > 0) {
+                p2l_launch_impl<float, 0>(P, u, L, K, sa);
+                ++launches;
+            }
+            IMQ_CUDA(cudaEventRecord(P.aux.xready, sa));
             p2p_near_f32(P, u, near, sa);
             launches += 2;
         }
-        IMQ_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)nb * K, s));
-        IMQ_CUDA(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)nb * K, s));
         t0(kPhP2M);
         p2m_launch<float>(P, u, M, coef, s);
         ++launches;
@@ -786,6 +792,14 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             far_m2p_launch(P, M, sa);
             if (P.n_m2p_items > 0) ++launches;
             IMQ_CUDA(cudaEventRecord(P.aux.join, sa));
+            IMQ_CUDA(cudaStreamWaitEvent(s, P.aux.xready, 0));
+        } else {
+            t0(kPhP2L);
+            if (P.X.total > 0) {
+                p2l_launch_impl<float, 0>(P, u, L, K, s);
+                ++launches;
+            }
+            t1();
         }
         t0(kPhM2L);
         if (P.n_m2l_tiles > 0 && O.umma) {
@@ -793,12 +807,6 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             launches += 2;
         } else if (P.n_m2l_tiles > 0) {
             m2l_tiled_launch(P, M, L, m2l, s);
-            ++launches;
-        }
-        t1();
-        t0(kPhP2L);
-        if (P.X.total > 0) {
-            p2l_launch_impl<float, 0>(P, u, L, K, s);
             ++launches;
         }
         t1();

@@ -144,7 +144,7 @@ struct Schwarz {
 // lowest-priority one, so free SM slots go to the latency-bound chain first.
 struct AuxStream {
     cudaStream_t hi = nullptr, s = nullptr;
-    cudaEvent_t fork = nullptr, mready = nullptr, join = nullptr, done = nullptr;
+    cudaEvent_t fork = nullptr, xready = nullptr, mready = nullptr, join = nullptr, done = nullptr;
     void ensure();
     AuxStream() = default;
     AuxStream(const AuxStream &) = delete;

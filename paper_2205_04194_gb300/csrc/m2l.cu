@@ -5,7 +5,7 @@
 // operator depends only on the level l and the integer offset o of S
 // relative to B (40 classes).  One CTA owns a tile of up to kTB target boxes
 // of one level and accumulates, in registers, the contributions of all 40
-// classes:  L[:, tile] = sum_o T_{l,o} M[:, src(tile, o)].
+// classes:  L[:, tile] += sum_o T_{l,o} M[:, src(tile, o)]  (added to what P2L left there).
 // Per class the operator (K x Kp, input-major, zero-padded rows) and the
 // gathered source multipoles (kTB x Kpad, box-major, Kpad odd so that the
 // column reads hit distinct banks) are staged in shared memory.  Thread
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tiled(const int4 *__restrict__
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const int row = ty * RR + r;
-            if (row < Kout) Lb[row] = acc[r][c];
+            if (row < Kout) atomicAdd(Lb + row, acc[r][c]);   // one add per element: a RED, no load
         }
     }
 }

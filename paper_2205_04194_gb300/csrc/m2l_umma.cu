@@ -96,7 +96,7 @@ __global__ void k_m2l_images(const float *__restrict__ ops, int64_t nblk, int K,
 // Warp roles (288 threads):
 //   warps 0-3  drain: thread b owns target row b (TMEM lane b); after each chunk
 //              it adds the chunk's accumulator to FP32 registers, and at the end
-//              writes the target's local coefficients;
+//              adds them to the target's local coefficients;
 //   warps 4-7  producers: gather the 128 rows of A (hi and lo) by cp.async,
 //              eight threads per 128-byte row, and arrive on the stage's
 //              barrier through cp.async.mbarrier.arrive.noinc; thread 128 also
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             float *Lb = L + (int64_t)tbox[b0 + tid] * Kout;
 #pragma unroll
             for (int i = 0; i < NC * 32; ++i)
-                if (i < Kout) Lb[i] = acc[i];
+                if (i < Kout) atomicAdd(Lb + i, acc[i]);   // onto the P2L terms in L: a RED, no load
         }
     } else if (w < 8) {
         // ---------------------------------------------------------------- producers

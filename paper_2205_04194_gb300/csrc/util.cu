@@ -110,6 +110,7 @@ void AuxStream::ensure() {
     IMQ_CUDA(cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest));
     IMQ_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least));
     IMQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    IMQ_CUDA(cudaEventCreateWithFlags(&xready, cudaEventDisableTiming));
     IMQ_CUDA(cudaEventCreateWithFlags(&mready, cudaEventDisableTiming));
     IMQ_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     IMQ_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
@@ -117,6 +118,7 @@ void AuxStream::ensure() {
 
 AuxStream::~AuxStream() {
     if (fork) cudaEventDestroy(fork);
+    if (xready) cudaEventDestroy(xready);
     if (mready) cudaEventDestroy(mready);
     if (join) cudaEventDestroy(join);
     if (done) cudaEventDestroy(done);
