@@ -264,6 +264,139 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t *__restrict__ parents
     }
 }
 
+// FP32 M2M / L2L with the four quadrant operators staged in shared memory by
+// one bulk copy per CTA (for K <= kTransSmemMaxK).  Per level the kernels above
+// are bound by the latency of their K / kTransUnroll dependent operator-row
+// loads from L2; here that is one copy, and the K-long reduction runs from
+// shared memory.  CTA: 16 parents, 8 warps; warp w applies quadrant q = w & 3
+// to parents 8 (w >> 2) .. + 7.  Same FMA order and quadrant sum order as
+// k_m2m / k_l2l, so the results are bitwise equal.
+constexpr int kTransSmemMaxK = 110;
+constexpr int kTS = 16;   // parents per CTA
+
+size_t trans_s_smem(int K) {
+    return sizeof(float) * ((size_t)4 * K * K + (size_t)8 * K * kTransG) + 16;
+}
+
+// acc[g][r] = sum_{i < K} A[i][lane + 32 r] * X[i][g], A and X in shared memory
+template <int RC>
+__device__ __forceinline__ void trans_rows_smem(const float *A, const float *X, int K, int lane,
+                                                float (&acc)[kTransG][RC]) {
+#pragma unroll
+    for (int g = 0; g < kTransG; ++g)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[g][r] = 0.f;
+    for (int i = 0; i < K; ++i) {
+        float w[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) w[r] = lane + 32 * r < K ? A[i * K + lane + 32 * r] : 0.f;
+        float mv[kTransG];
+        lds8<float>(X + (size_t)i * kTransG, mv);
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) acc[g][r] += w[r] * mv[g];
+    }
+}
+
+template <int RC, bool UP>
+__global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ parents, int n,
+                                                const int32_t *__restrict__ child, float *__restrict__ X,
+                                                const float *__restrict__ op, int K, int *err) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *sop = reinterpret_cast<float *>(smraw);                 // [4][K][K]
+    float *sx = sop + (size_t)4 * K * K;                            // [8 warps][K][8]; reused as red[4][16][K]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ch[kTS * 4], s_par[kTS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, grp = w >> 2;
+    const int p0 = blockIdx.x * kTS;
+    const int ng = min(kTS, n - p0);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(sizeof(float) * 4 * K * K);
+        mbar_arrive_expect_tx(&bar, bytes);
+        bulk_g2s(sop, op, bytes, &bar);
+    }
+    if (threadIdx.x < kTS * 4) {
+        const int g = threadIdx.x >> 2;
+        const int pb = g < ng ? parents[p0 + g] : -1;
+        s_ch[threadIdx.x] = pb >= 0 ? child[4 * pb + (threadIdx.x & 3)] : -1;
+        if ((threadIdx.x & 3) == 0) s_par[g] = pb;
+    }
+    __syncthreads();
+    float *mx = sx + (size_t)w * K * kTransG;
+    {   // stage: child q of the warp's 8 parents (upward) or the parents themselves (downward)
+        float v[kTransG][RC];
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g) {
+            const int src = UP ? s_ch[4 * (grp * kTransG + g) + q] : s_par[grp * kTransG + g];
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int i = lane + 32 * r;
+                v[g][r] = (src >= 0 && i < K) ? X[(int64_t)src * K + i] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int i = lane + 32 * r;
+                if (i < K) mx[(size_t)i * kTransG + g] = v[g][r];
+            }
+    }
+    // a CTA-uniform verdict on the bounded wait, so that every thread leaves together
+    if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
+        if (threadIdx.x == 0) set_error(err, kErrWaitTimeout);
+        return;   // the results of this product are invalid; the host reads the error word
+    }
+    float acc[kTransG][RC];
+    trans_rows_smem<RC>(sop + (size_t)q * K * K, mx, K, lane, acc);
+    if (UP) {
+        __syncthreads();   // every warp is done with its staging area: reuse it for the quadrant products
+        float *red = sx;   // [4][16][K]
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g)
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int o = lane + 32 * r;
+                if (o < K) red[((size_t)q * kTS + grp * kTransG + g) * K + o] = acc[g][r];
+            }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTS * K; e += blockDim.x) {
+            const int g = e / K, o = e - g * K;
+            if (g >= ng) continue;
+            const float sum = ((red[(0 * kTS + g) * K + o] + red[(1 * kTS + g) * K + o]) + red[(2 * kTS + g) * K + o]) +
+                              red[(3 * kTS + g) * K + o];
+            X[(int64_t)s_par[g] * K + o] = sum;
+        }
+    } else {
+        float old[kTransG][RC];
+        int chs[kTransG];
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g) {
+            chs[g] = grp * kTransG + g < ng ? s_ch[4 * (grp * kTransG + g) + q] : -1;
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int o = lane + 32 * r;
+                old[g][r] = (chs[g] >= 0 && o < K) ? X[(int64_t)chs[g] * K + o] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kTransG; ++g) {
+            if (chs[g] < 0) continue;
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int o = lane + 32 * r;
+                if (o < K) X[(int64_t)chs[g] * K + o] = old[g][r] + acc[g][r];
+            }
+        }
+    }
+}
+
 // M2L for the FP64 path: one thread per (target box, output row), operators
 // read through the cache hierarchy.
 template <class T>
@@ -671,6 +804,26 @@ template <class T, bool UP>
 void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, bool downward, cudaStream_t s,
                   int *launches) {
     ensure_parents(P, s);
+    if constexpr (std::is_same<T, float>::value) {
+        if (K <= kTransSmemMaxK) {
+            const int RC = (K + 31) / 32;
+            void (*kern)(const int32_t *, int, const int32_t *, float *, const float *, int, int *) =
+                RC == 1 ? k_trans_s<1, UP> : RC == 2 ? k_trans_s<2, UP> : RC == 3 ? k_trans_s<3, UP> : k_trans_s<4, UP>;
+            const size_t smem = trans_s_smem(K);
+            IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int *err = device_error_word();
+            for (int k = 0; k <= lev_hi - lev_lo; ++k) {
+                const int lev = downward ? lev_lo + k : lev_hi - k;
+                const int pb = P.parent_start[lev], np = P.parent_start[lev + 1] - pb;
+                if (np <= 0) continue;
+                kern<<<(np + kTS - 1) / kTS, 256, smem, s>>>(P.parents.as<int32_t>() + pb, np, P.child.as<int32_t>(), X,
+                                                            op, K, err);
+                IMQ_LAUNCH_CHECK();
+                ++*launches;
+            }
+            return;
+        }
+    }
     const int RC = (K + 31) / 32;
     void (*kern)(const int32_t *, int, const int32_t *, T *, const T *, int) = nullptr;
 #define IMQ_TRANS_CASE(R)                                \
