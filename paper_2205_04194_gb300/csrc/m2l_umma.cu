@@ -223,13 +223,31 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         const int r = tid - kDrainThreads;
         const int j = r & 7;
         const unsigned char *imgb = reinterpret_cast<const unsigned char *>(img);
+        // the sources of class ci + 1 are loaded while class ci's chunks are gathered, so
+        // the table lookup is off the producer's per-chunk path
+        int src[8], nxt[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            src[k] = -1;
+            nxt[k] = (tgt[k] >= 0 && nitems > 0) ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + s_cls[0]) : -1;
+        }
         for (int it = 0; it < nitems; ++it) {
             const int st = it % S;
             if (s_abort || (it >= S && !mbar_wait(&s_empty[st], (uint32_t)((it / S) + 1) & 1u))) {
                 ok = false;
                 break;
             }
-            const int o = s_cls[it / NKC], kc = it - (it / NKC) * NKC;
+            const int ci = it / NKC, o = s_cls[ci], kc = it - ci * NKC;
+            if (kc == 0) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) src[k] = nxt[k];
+                if (ci + 1 < s_ncls) {
+                    const int o1 = s_cls[ci + 1];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        nxt[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + o1) : -1;
+                }
+            }
             const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
             if (r == 0) {
                 mbar_arrive_expect_tx(&s_full[st], img_bytes);
@@ -239,9 +257,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             }
             // 8 consecutive threads fetch the 8 16-byte chunks of one 128-byte row, so a
             // warp instruction reads 4 whole rows (full sectors) rather than 32 fragments
-            int src[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) src[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + o) : -1;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int row = (r >> 3) + 16 * k;
