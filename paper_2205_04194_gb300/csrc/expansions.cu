@@ -665,7 +665,7 @@ static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
     if (P.m2l_kernel == IMQ_M2L_TENSOR && !fits)
         fail(IMQ_UNSUPPORTED, "imq_plan: the expansion does not fit the tensor-core M2L");
     if (P.m2l_kernel == IMQ_M2L_CUDA_CORES || !fits) return;
-    m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, s);
+    m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, O.m2l_tmask, s);
     O.umma = true;
 }
 
@@ -956,7 +956,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         }
         t0(kPhM2L);
         if (P.n_m2l_tiles > 0 && O.umma) {
-            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), K, s);
+            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s);
             launches += 2;
         } else if (P.n_m2l_tiles > 0) {
             m2l_tiled_launch(P, M, L, m2l, s);
@@ -1022,7 +1022,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t0(kPhM2L);
         if constexpr (std::is_same<T, float>::value) {
             if (P.n_m2l_tiles > 0 && O.umma) {
-                m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), K, s);
+                m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s);
                 launches += 2;
             } else if (P.n_m2l_tiles > 0) {
                 m2l_tiled_launch(P, M, L, m2l, s);

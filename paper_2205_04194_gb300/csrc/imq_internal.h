@@ -118,7 +118,7 @@ struct TypedOps {        // operator set in one precision
     DevMem m2l_odd, l2l_odd, dzc, Lodd;
     bool dz_ready = false;
     // tensor-core M2L (FP32 only): swizzled tf32 hi/lo operator images, packed multipoles
-    DevMem m2l_img, Mpk;
+    DevMem m2l_img, Mpk, m2l_tmask;   // m2l_tmask: uint64 per tile, bit o = offset class o present
     bool umma = false;
 };
 
@@ -286,8 +286,10 @@ void far_l2p_launch(Plan &P, const float *L, const float *coef, const float *nea
 void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
-void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s);
-void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, int Kout, cudaStream_t s);
+void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
+                      cudaStream_t s);
+void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
+                     int Kout, cudaStream_t s);
 // batch.cu
 template <class T>
 void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,

@@ -21,6 +21,8 @@
 // stage S-1 chunks ahead; one thread issues the 12 MMAs of a chunk and commits
 // them to the stage's mbarrier, which releases the stage for reuse.  Every
 // wait is bounded and reports kErrWaitTimeout through the device error word.
+#include <algorithm>
+
 #include "imq_internal.h"
 #include "ptx.cuh"
 #include "umma.cuh"
@@ -112,15 +114,14 @@ constexpr int kThreadsWS = kDrainThreads + kProdThreads + 32;
 
 template <int S, int NC>
 __global__ void __launch_bounds__(kThreadsWS, 1)
-    k_m2l_umma(const int4 *__restrict__ tiles, const int32_t *__restrict__ tbox, const int32_t *__restrict__ vtab,
-               const float *__restrict__ Mpk, float *__restrict__ L, const float *__restrict__ img, int Kout, int Kn,
-               int NKC, int *err) {
+    k_m2l_umma(const int4 *__restrict__ tiles, const uint64_t *__restrict__ tmask, const int32_t *__restrict__ tbox,
+               const int32_t *__restrict__ vtab, const float *__restrict__ Mpk, float *__restrict__ L,
+               const float *__restrict__ img, int Kout, int Kn, int NKC, int *err) {
     constexpr uint32_t kAccCols = NC <= 2 ? 64 : NC <= 4 ? 128 : 256;   // columns per accumulator
     constexpr int NA = NC <= 4 ? 4 : 2;                                   // accumulators in rotation
     constexpr uint32_t kTCols = NA * kAccCols;                            // <= 512
     extern __shared__ unsigned char smraw[];
     __shared__ int s_cls[kOffsetClasses];
-    __shared__ int s_present[kOffsetClasses];
     __shared__ int s_ncls;
     __shared__ volatile int s_abort;
     __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_accf[4], s_acce[4];
@@ -136,7 +137,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     const int blk = tile.x, b0 = tile.y, nbt = tile.z;
 
     if (w == 0) tmem_alloc(&s_tmem, kTCols);
-    if (tid < kOffsetClasses) s_present[tid] = 0;
     if (tid == 32) {
         s_abort = 0;
         for (int i = 0; i < S; ++i) {
@@ -162,24 +162,17 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             const int row = (r >> 3) + 16 * k;
             tgt[k] = row < nbt ? tbox[b0 + row] : -1;
         }
-        if ((r & 7) == 0) {   // one thread per row marks the classes present in the tile
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (tgt[k] >= 0)
-                    for (int o = 0; o < kOffsetClasses; ++o)
-                        if (vtab[(int64_t)kOffsetClasses * tgt[k] + o] >= 0) s_present[o] = 1;
-        }
+    }
+    if (tid == 0) {   // the offset classes present in the tile (bit o of the plan's tile mask)
+        const uint64_t mk = tmask[blockIdx.x];
+        int n = 0;
+        for (int o = 0; o < kOffsetClasses; ++o)
+            if ((mk >> o) & 1ull) s_cls[n++] = o;
+        s_ncls = n;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
-        int n = 0;
-        for (int o = 0; o < kOffsetClasses; ++o)
-            if (s_present[o]) s_cls[n++] = o;
-        s_ncls = n;
-    }
-    __syncthreads();
     const uint32_t tmem = s_tmem;
     const int nitems = s_ncls * NKC;
     bool ok = true;
@@ -318,6 +311,24 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     if (w == 0) tmem_dealloc(tmem, kTCols);
 }
 
+// Bit o of mask[t] is set when some target box of tile t has a class-o V source.
+// One warp per tile, lanes over its boxes.
+__global__ void k_tile_masks(const int4 *__restrict__ tiles, int ntiles, const int32_t *__restrict__ tbox,
+                             const int32_t *__restrict__ vtab, uint64_t *__restrict__ mask) {
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    const int4 tile = tiles[t];
+    uint64_t m = 0;
+    for (int row = lane; row < tile.z; row += 32) {
+        const int b = tbox[tile.y + row];
+        for (int o = 0; o < kOffsetClasses; ++o)
+            if (vtab[(int64_t)kOffsetClasses * b + o] >= 0) m |= 1ull << o;
+    }
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) m |= __shfl_xor_sync(0xFFFFFFFFu, m, k);
+    if (lane == 0) mask[t] = m;
+}
+
 }  // namespace
 
 bool m2l_umma_supported(int K, int Kout) {
@@ -326,7 +337,8 @@ bool m2l_umma_supported(int K, int Kout) {
     return d.smem() + kStaticSmem <= 227 * 1024;
 }
 
-void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, cudaStream_t s) {
+void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
+                      cudaStream_t s) {
     const int K = P.layout.K;
     const UmmaDims d = umma_dims(K, Kout);
     const int Kp = 16 * m2l_tiled_rows(Kout);
@@ -337,9 +349,17 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
         k_m2l_images<<<blocks_for(chunks, 256), 256, 0, s>>>(ops, nblk, K, Kp, Kout, d.Kn, d.NKC, img.as<float>());
     IMQ_LAUNCH_CHECK();
     Mpk.alloc(sizeof(float) * (size_t)P.nbox * 2 * d.KP);
+    tmask.alloc(sizeof(uint64_t) * (size_t)std::max(1, P.n_m2l_tiles));
+    if (P.n_m2l_tiles > 0) {
+        k_tile_masks<<<(P.n_m2l_tiles + 3) / 4, 128, 0, s>>>(P.m2l_tiles.as<int4>(), P.n_m2l_tiles,
+                                                            P.m2l_tbox.as<int32_t>(), P.vtab.as<int32_t>(),
+                                                            tmask.as<uint64_t>());
+        IMQ_LAUNCH_CHECK();
+    }
 }
 
-void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, int Kout, cudaStream_t s) {
+void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
+                     int Kout, cudaStream_t s) {
     if (P.n_m2l_tiles == 0) return;
     const int K = P.layout.K;
     const UmmaDims d = umma_dims(K, Kout);
@@ -350,7 +370,8 @@ void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, 
 #define IMQ_UMMA_CASE(SS, NCC)                                                                                    \
     if (d.stages == SS && d.tcols == NCC) {                                                                      \
         IMQ_CUDA(cudaFuncSetAttribute(k_m2l_umma<SS, NCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_m2l_umma<SS, NCC><<<P.n_m2l_tiles, kThreadsWS, smem, s>>>(P.m2l_tiles.as<int4>(), P.m2l_tbox.as<int32_t>(), \
+        k_m2l_umma<SS, NCC><<<P.n_m2l_tiles, kThreadsWS, smem, s>>>(P.m2l_tiles.as<int4>(), tmask,              \
+                                                                 P.m2l_tbox.as<int32_t>(),                         \
                                                                  P.vtab.as<int32_t>(), Mpk, L, img, Kout, d.Kn,    \
                                                                  d.NKC, err);                                      \
         launched = true;                                                                                          \
