@@ -1,6 +1,7 @@
 // Inline-PTX helpers for sm_103a: mbarrier, 1-D TMA bulk copies, error flags.
-// Every wait is bounded: after kSpinLimit polls it reports failure instead of
-// spinning forever, and the caller records an error word the host reads back.
+// Every wait is bounded: after kSpinLimit polls or 0.5 s it reports failure
+// instead of spinning forever, and the caller records an error word the host
+// reads back.
 #pragma once
 
 #include <stdint.h>
@@ -51,10 +52,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; returns false on timeout.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait; returns false on timeout: after kSpinLimit polls, or once
+// kWaitLimitNs of wall time have passed (each try_wait may suspend the thread
+// for a while, so the poll count alone does not bound the time).
+constexpr uint64_t kWaitLimitNs = 500000000ull;   // 0.5 s
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 1; i < kSpinLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
     }
     return false;
 }
