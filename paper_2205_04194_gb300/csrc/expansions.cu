@@ -268,44 +268,49 @@ __global__ void __launch_bounds__(128) k_l2l(const int32_t *__restrict__ parents
 // one bulk copy per CTA (for K <= kTransSmemMaxK).  Per level the kernels above
 // are bound by the latency of their K / kTransUnroll dependent operator-row
 // loads from L2; here that is one copy, and the K-long reduction runs from
-// shared memory.  CTA: 16 parents, 8 warps; warp w applies quadrant q = w & 3
-// to parents 8 (w >> 2) .. + 7.  Same FMA order and quadrant sum order as
-// k_m2m / k_l2l, so the results are bitwise equal.
+// shared memory.  CTA: 16 parents, 16 warps; warp w applies quadrant q = w & 3
+// to parents 4 (w >> 2) .. + 3 (four warps per quadrant hide the shared-memory
+// latency of the reduction).  Levels are chained with programmatic dependent
+// launch, so a level's prologue overlaps the previous level.  Same FMA and
+// quadrant-sum order as k_m2m / k_l2l, so the results are bitwise equal.
 constexpr int kTransSmemMaxK = 110;
 constexpr int kTS = 16;   // parents per CTA
+constexpr int kTSG = 4;   // parents per warp
+constexpr int kTSWarps = 4 * kTS / kTSG;
 
 size_t trans_s_smem(int K) {
-    return sizeof(float) * ((size_t)4 * K * K + (size_t)8 * K * kTransG) + 16;
+    return sizeof(float) * ((size_t)4 * K * K + (size_t)kTSWarps * K * kTSG) + 16;
 }
 
 // acc[g][r] = sum_{i < K} A[i][lane + 32 r] * X[i][g], A and X in shared memory
 template <int RC>
 __device__ __forceinline__ void trans_rows_smem(const float *A, const float *X, int K, int lane,
-                                                float (&acc)[kTransG][RC]) {
+                                                float (&acc)[kTSG][RC]) {
 #pragma unroll
-    for (int g = 0; g < kTransG; ++g)
+    for (int g = 0; g < kTSG; ++g)
 #pragma unroll
         for (int r = 0; r < RC; ++r) acc[g][r] = 0.f;
+#pragma unroll 4
     for (int i = 0; i < K; ++i) {
         float w[RC];
 #pragma unroll
         for (int r = 0; r < RC; ++r) w[r] = lane + 32 * r < K ? A[i * K + lane + 32 * r] : 0.f;
-        float mv[kTransG];
-        lds8<float>(X + (size_t)i * kTransG, mv);
+        const float4 x = reinterpret_cast<const float4 *>(X)[i];
+        const float mv[kTSG] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g)
+        for (int g = 0; g < kTSG; ++g)
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[g][r] += w[r] * mv[g];
     }
 }
 
 template <int RC, bool UP>
-__global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ parents, int n,
-                                                const int32_t *__restrict__ child, float *__restrict__ X,
-                                                const float *__restrict__ op, int K, int *err) {
+__global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__restrict__ parents, int n,
+                                                           const int32_t *__restrict__ child, float *__restrict__ X,
+                                                           const float *__restrict__ op, int K, int *err) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float *sop = reinterpret_cast<float *>(smraw);                 // [4][K][K]
-    float *sx = sop + (size_t)4 * K * K;                            // [8 warps][K][8]; reused as red[4][16][K]
+    float *sx = sop + (size_t)4 * K * K;                            // [16 warps][K][4]; reused as red[4][16][K]
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_ch[kTS * 4], s_par[kTS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, grp = w >> 2;
@@ -328,12 +333,14 @@ __global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ par
         if ((threadIdx.x & 3) == 0) s_par[g] = pb;
     }
     __syncthreads();
-    float *mx = sx + (size_t)w * K * kTransG;
-    {   // stage: child q of the warp's 8 parents (upward) or the parents themselves (downward)
-        float v[kTransG][RC];
+    // everything below reads expansions the previous kernel on the stream wrote
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    float *mx = sx + (size_t)w * K * kTSG;
+    {   // stage: child q of the warp's parents (upward) or the parents themselves (downward)
+        float v[kTSG][RC];
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g) {
-            const int src = UP ? s_ch[4 * (grp * kTransG + g) + q] : s_par[grp * kTransG + g];
+        for (int g = 0; g < kTSG; ++g) {
+            const int src = UP ? s_ch[4 * (grp * kTSG + g) + q] : s_par[grp * kTSG + g];
 #pragma unroll
             for (int r = 0; r < RC; ++r) {
                 const int i = lane + 32 * r;
@@ -341,29 +348,31 @@ __global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ par
             }
         }
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g)
-#pragma unroll
-            for (int r = 0; r < RC; ++r) {
-                const int i = lane + 32 * r;
-                if (i < K) mx[(size_t)i * kTransG + g] = v[g][r];
-            }
+        for (int r = 0; r < RC; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K) reinterpret_cast<float4 *>(mx)[i] = make_float4(v[0][r], v[1][r], v[2][r], v[3][r]);
+        }
     }
     // a CTA-uniform verdict on the bounded wait, so that every thread leaves together
     if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
         if (threadIdx.x == 0) set_error(err, kErrWaitTimeout);
         return;   // the results of this product are invalid; the host reads the error word
     }
-    float acc[kTransG][RC];
+    float acc[kTSG][RC];
     trans_rows_smem<RC>(sop + (size_t)q * K * K, mx, K, lane, acc);
+    // programmatic dependent launch: once every CTA is writing its results, the next
+    // level's kernel may start its prologue (barrier set-up, operator copy, parent and
+    // child ids); triggering this late keeps waiting CTAs from holding SMs for long
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (UP) {
         __syncthreads();   // every warp is done with its staging area: reuse it for the quadrant products
         float *red = sx;   // [4][16][K]
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g)
+        for (int g = 0; g < kTSG; ++g)
 #pragma unroll
             for (int r = 0; r < RC; ++r) {
                 const int o = lane + 32 * r;
-                if (o < K) red[((size_t)q * kTS + grp * kTransG + g) * K + o] = acc[g][r];
+                if (o < K) red[((size_t)q * kTS + grp * kTSG + g) * K + o] = acc[g][r];
             }
         __syncthreads();
         for (int e = threadIdx.x; e < kTS * K; e += blockDim.x) {
@@ -374,11 +383,11 @@ __global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ par
             X[(int64_t)s_par[g] * K + o] = sum;
         }
     } else {
-        float old[kTransG][RC];
-        int chs[kTransG];
+        float old[kTSG][RC];
+        int chs[kTSG];
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g) {
-            chs[g] = grp * kTransG + g < ng ? s_ch[4 * (grp * kTransG + g) + q] : -1;
+        for (int g = 0; g < kTSG; ++g) {
+            chs[g] = grp * kTSG + g < ng ? s_ch[4 * (grp * kTSG + g) + q] : -1;
 #pragma unroll
             for (int r = 0; r < RC; ++r) {
                 const int o = lane + 32 * r;
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(256) k_trans_s(const int32_t *__restrict__ par
             }
         }
 #pragma unroll
-        for (int g = 0; g < kTransG; ++g) {
+        for (int g = 0; g < kTSG; ++g) {
             if (chs[g] < 0) continue;
 #pragma unroll
             for (int r = 0; r < RC; ++r) {
@@ -816,9 +825,18 @@ void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, boo
                 const int lev = downward ? lev_lo + k : lev_hi - k;
                 const int pb = P.parent_start[lev], np = P.parent_start[lev + 1] - pb;
                 if (np <= 0) continue;
-                kern<<<(np + kTS - 1) / kTS, 256, smem, s>>>(P.parents.as<int32_t>() + pb, np, P.child.as<int32_t>(), X,
-                                                            op, K, err);
-                IMQ_LAUNCH_CHECK();
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)((np + kTS - 1) / kTS));
+                cfg.blockDim = dim3(32 * kTSWarps);
+                cfg.dynamicSmemBytes = smem;
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                attr[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                const int32_t *par = P.parents.as<int32_t>() + pb, *ch = P.child.as<int32_t>();
+                IMQ_CUDA(cudaLaunchKernelEx(&cfg, kern, par, np, ch, (float *)X, (const float *)op, K, err));
                 ++*launches;
             }
             return;
