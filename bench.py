@@ -39,6 +39,34 @@ N_SM = 152
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
 
 
+# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum + dram__bytes_write.sum),
+# from one ncu capture of `python bench.py --steps 3 --warmup 1 --no-cpu --no-solve --p 12
+# --phase-steps 2` on the 1M clustered workload (L2 flushed between products), keyed by the
+# SHA-256 of the kernel sources at capture time: once a source changes the figure is stale
+# and the bench reports null.  Summaries: profiles/launches_fast_product_clustered_1m.md.
+TRAFFIC = {
+    # k_m2l_umma 87.47 MB read + 0.21 MB written, k_pack_m 17.19 MB read (the M2L phase times both)
+    "m2l": {"bytes": 87.47e6 + 0.21e6 + 17.19e6, "sources": {
+        "paper_2205_04194_gb300/csrc/m2l_umma.cu": "d925151ba794c28ab67f2ecafcc9f8208ea6c1de4d225e2393697c0e25ac2340",
+        "paper_2205_04194_gb300/csrc/umma.cuh": "a133f64894a1d5c359ee5202af3f44414abc786ea60768f20a375cecf456fcd6",
+        "paper_2205_04194_gb300/csrc/ptx.cuh": "9f11aae585d997f977cfb9515e1a6d3900bf168e91c1a75824dfdb29176bb76c"}},
+}
+
+
+def _traffic(kernel: str):
+    import hashlib
+    rec = TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    for rel, digest in rec["sources"].items():
+        if digest is None:
+            continue
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != digest:
+                return None
+    return rec["bytes"]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -467,7 +495,7 @@ def main():
     else:
         roof = {"kernel": "k_m2l_umma (tcgen05 kind::tf32, 3xTF32) + k_pack_m", "bound": "tensor",
                 "achieved": m2l_tf, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m2l_tf / tf32_peak,
-                "traffic": None,
+                "traffic": _traffic("m2l") if (wl.n == 1_000_000 and wl.p == 12) else None,
                 "achieved_executed": m2l_exec_tf, "frac_executed": m2l_exec_tf / tf32_peak,
                 "peak_source": f"{src} bf16 burst {bf16:.1f} TFLOP/s x nominal tf32/bf16 ratio "
                                f"{TF32_PER_BF16:.3f} (1.1 / 2.25 PFLOP/s dense)",
