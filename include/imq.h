@@ -73,8 +73,26 @@ typedef struct imq_options {
     double x0, y0, side;       /*    otherwise D is the exact bounding square          */
     int32_t check_duplicates;  /* 1: imq_plan fails with IMQ_DUPLICATE_POINTS on equal points */
     int32_t m2l_kernel;        /* imq_m2l_kernel: how the FP32 product runs M2L             */
-    int32_t reserved[6];
+    int32_t algorithm;         /* imq_algorithm: the fast multipole form (default) or the
+                                  paper's treecode, Algorithm 1                              */
+    int32_t levels;            /* IMQ_ALG_TREECODE: the paper's L (1..15): blocks of the
+                                  finest level are 2^(L+1) x 2^(L+1); `leaf` is ignored      */
+    int32_t reserved[4];
 } imq_options;
+
+/* How imq_matvec evaluates the product.
+ *   FMM      : adaptive quadtree (split while a box holds more than `leaf`
+ *              points); multipoles translated to local expansions (M2L, L2L)
+ *              and evaluated once per target; the paper's M2P only on the
+ *              W lists of the adaptive tree.
+ *   TREECODE : Algorithm 1 of Section 2.2 on a uniform partition: levels
+ *              l = 1..L of 2^(l+1) x 2^(l+1) blocks, the moments of every block
+ *              (here P2M at the finest level and M2M upward, equal to the
+ *              per-level moments up to rounding), the far-field sum of
+ *              Eq. (13) at every target for the blocks of S_p at every level
+ *              (M2P over the union of the V lists of the target block's
+ *              ancestors), and the direct sum over NS_p at level L (U lists). */
+typedef enum imq_algorithm { IMQ_ALG_FMM = 0, IMQ_ALG_TREECODE = 1 } imq_algorithm;
 
 /* M2L kernel of the FP32 product.  AUTO takes the tensor cores when the
  * expansion fits them (K, K_out <= 256 reals), else the CUDA cores.
@@ -416,7 +434,7 @@ typedef struct imq_plan_info {
     int64_t n_points;
     int64_t n_nodes;                     /* evaluation plans: nodes among n_points (else 0) */
     int32_t n_problems;                  /* batched plans: independent problems (else 1)     */
-    int32_t reserved0;
+    int32_t algorithm;                   /* imq_algorithm of the plan                        */
     int32_t n_boxes, n_leaves, max_level, p, leaf, k_real;  /* k_real: reals per expansion */
     double x0, y0, side, c;
     int64_t n_u, n_v, n_w, n_x;          /* total entries of each interaction list */

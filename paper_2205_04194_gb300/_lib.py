@@ -30,11 +30,12 @@ class ImqError(RuntimeError):
 
 class ImqOptions(ctypes.Structure):
     _fields_ = [("struct_size", I32), ("has_domain", I32), ("x0", D), ("y0", D), ("side", D),
-                ("check_duplicates", I32), ("m2l_kernel", I32), ("reserved", I32 * 6)]
+                ("check_duplicates", I32), ("m2l_kernel", I32), ("algorithm", I32), ("levels", I32),
+                ("reserved", I32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
-    _fields_ = [("n_points", I64), ("n_nodes", I64), ("n_problems", I32), ("reserved0", I32), ("n_boxes", I32), ("n_leaves", I32), ("max_level", I32), ("p", I32),
+    _fields_ = [("n_points", I64), ("n_nodes", I64), ("n_problems", I32), ("algorithm", I32), ("n_boxes", I32), ("n_leaves", I32), ("max_level", I32), ("p", I32),
                 ("leaf", I32), ("k_real", I32), ("x0", D), ("y0", D), ("side", D), ("c", D),
                 ("n_u", I64), ("n_v", I64), ("n_w", I64), ("n_x", I64), ("p2p_pairs", I64),
                 ("m2l_pairs", I64), ("device_bytes", I64)]

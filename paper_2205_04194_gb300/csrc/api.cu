@@ -140,11 +140,13 @@ const char *imq_version(void) { return "imq-gb300 0.1 (sm_103a)"; }
 namespace {
 
 void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
-                     double &side, bool &dups, int *m2l_kernel = nullptr) {
+                     double &side, bool &dups, int *m2l_kernel = nullptr, int *algorithm = nullptr,
+                     int *tc_depth = nullptr) {
     if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
     if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
     if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
-    if (leaf < 1) fail(IMQ_INVALID_ARG, "imq_plan: leaf must be >= 1");
+    if (leaf < 1 && !(opt && opt->algorithm == IMQ_ALG_TREECODE))   // the treecode ignores leaf
+        fail(IMQ_INVALID_ARG, "imq_plan: leaf must be >= 1");
     dups = false;
     x0 = 0;
     y0 = 0;
@@ -163,6 +165,12 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
         if (opt->m2l_kernel < IMQ_M2L_AUTO || opt->m2l_kernel > IMQ_M2L_TENSOR)
             fail(IMQ_INVALID_ARG, "imq_plan: unknown m2l_kernel");
         if (m2l_kernel) *m2l_kernel = opt->m2l_kernel;
+        if (opt->algorithm != IMQ_ALG_FMM && opt->algorithm != IMQ_ALG_TREECODE)
+            fail(IMQ_INVALID_ARG, "imq_plan: unknown algorithm");
+        if (opt->algorithm == IMQ_ALG_TREECODE && (opt->levels < 1 || opt->levels > IMQ_MAX_LEVEL - 1))
+            fail(IMQ_INVALID_ARG, "imq_plan: the treecode needs levels in [1, IMQ_MAX_LEVEL - 1]");
+        if (algorithm) *algorithm = opt->algorithm;
+        if (tc_depth) *tc_depth = opt->algorithm == IMQ_ALG_TREECODE ? opt->levels + 1 : 0;
     }
 }
 
@@ -170,8 +178,8 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
                         const imq_options *opt, cudaStream_t s) {
     double x0, y0, side;
     bool dups;
-    int m2lk = IMQ_M2L_AUTO;
-    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk);
+    int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM, depth = 0;
+    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth);
     check_device();
     auto *h = new imq_plan_s;
     try {
@@ -186,6 +194,8 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
         P.y0 = y0;
         P.side = side;
         P.m2l_kernel = m2lk;
+        P.algorithm = alg;
+        P.tc_depth = depth;
         P.layout.build(p, 0);
         build_tree(P, d_points, s, dups);
         ensure_ops(P, false, s);
@@ -255,8 +265,9 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
         const int64_t N = offs[nprob];
         double x0, y0, side;
         bool dups;
-        int m2lk = IMQ_M2L_AUTO;
-        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk);
+        int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM;
+        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg);
+        if (alg != IMQ_ALG_FMM) fail(IMQ_UNSUPPORTED, "imq_plan_batched: the treecode is built for single plans only");
         check_device();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
@@ -536,6 +547,7 @@ imq_status imq_plan_get_info(imq_plan_t plan, imq_plan_info *info) {
         info->n_points = P.N;
         info->n_nodes = P.n_nodes;
         info->n_problems = P.nprob;
+        info->algorithm = P.algorithm;
         info->n_boxes = P.nbox;
         info->n_leaves = P.nleaf;
         info->max_level = P.max_level;

@@ -163,6 +163,8 @@ struct Plan {
     Layout layout_odd;   // locals of the c-derivative (n+m odd)
     int64_t n_nodes = 0; // evaluation plans: the first n_nodes points are nodes, the rest targets
     int m2l_kernel = 0;  // imq_m2l_kernel
+    int algorithm = 0;   // imq_algorithm
+    int tc_depth = 0;    // IMQ_ALG_TREECODE: depth of the uniform partition (paper's L + 1)
     int nprob = 1;       // batched plans: independent problems sharing one flattened tree
     DevMem box_prob;     // int32[nbox] problem of each box (batched plans only)
     DevMem prob_c;       // double[nprob] shape of each problem (batched plans only)

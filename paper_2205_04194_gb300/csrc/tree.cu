@@ -170,7 +170,8 @@ __device__ int lower_bound_u32(const uint32_t *a, int lo, int hi, uint32_t key) 
     return lo;
 }
 
-__global__ void split_count(int lb, int nl, int lev, int leaf, const uint32_t *__restrict__ codes,
+// depth > 0: uniform partition (the paper's blocks), split every box above that depth
+__global__ void split_count(int lb, int nl, int lev, int leaf, int depth, const uint32_t *__restrict__ codes,
                             const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
                             const uint32_t *__restrict__ prefix, int32_t *__restrict__ qb, int32_t *__restrict__ nchild) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,7 +179,7 @@ __global__ void split_count(int lb, int nl, int lev, int leaf, const uint32_t *_
     const int b = lb + i;
     const int bg = begin[b], en = end[b];
     int cnt = 0;
-    if (en - bg > leaf && lev < IMQ_MAX_LEVEL) {
+    if (depth > 0 ? lev < depth : (en - bg > leaf && lev < IMQ_MAX_LEVEL)) {
         const int shift = 32 - 2 * (lev + 1);
         const uint32_t P = prefix[b];
         qb[5 * i] = bg;
@@ -534,6 +535,52 @@ void offset_of_class(int k, int *dx, int *dy) {
     *dx = *dy = 0;
 }
 
+// The paper's Algorithm 1 on the uniform partition: the far field of a target
+// block at level l comes from the blocks of S_p, the children of its parent's
+// neighbours that are not adjacent to it -- the V list of its ancestor at that
+// level -- evaluated at the targets themselves (M2P).  The W list of each leaf
+// becomes the union of the V lists of the leaf and of its ancestors (coarsest
+// level first), and the V lists are emptied so that no M2L / L2L work is done.
+void treecode_lists(Plan &P, cudaStream_t s) {
+    const int nb = P.nbox;
+    std::vector<int32_t> voff(nb + 1), par(nb), lev(nb), wcnt(nb, 0);
+    IMQ_CUDA(cudaMemcpyAsync(voff.data(), P.V.off.ptr, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(par.data(), P.parent.ptr, 4 * (size_t)nb, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaMemcpyAsync(lev.data(), P.level.ptr, 4 * (size_t)nb, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> vitems(std::max<int64_t>(1, P.V.total));
+    if (P.V.total > 0)
+        IMQ_CUDA(cudaMemcpyAsync(vitems.data(), P.V.items.ptr, 4 * (size_t)P.V.total, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> leaves(std::max(1, P.nleaf));
+    IMQ_CUDA(cudaMemcpyAsync(leaves.data(), P.leaves.ptr, 4 * (size_t)P.nleaf, cudaMemcpyDeviceToHost, s));
+    IMQ_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::vector<int32_t>> T(nb);
+    for (int k = 0; k < P.nleaf; ++k) {
+        const int b = leaves[k];
+        std::vector<int32_t> chain;
+        for (int a = b; a >= 0; a = par[a]) chain.push_back(a);
+        for (auto it = chain.rbegin(); it != chain.rend(); ++it)
+            for (int e = voff[*it]; e < voff[*it + 1]; ++e) T[b].push_back(vitems[e]);
+    }
+    std::vector<int32_t> toff(nb + 1, 0), titems;
+    for (int b = 0; b < nb; ++b) {
+        toff[b + 1] = toff[b] + (int32_t)T[b].size();
+        titems.insert(titems.end(), T[b].begin(), T[b].end());
+    }
+    P.W.off.alloc(4 * (size_t)(nb + 1));
+    P.W.items.alloc(4 * std::max<size_t>(1, titems.size()));
+    P.W.total = (int64_t)titems.size();
+    IMQ_CUDA(cudaMemcpyAsync(P.W.off.ptr, toff.data(), 4 * (size_t)(nb + 1), cudaMemcpyHostToDevice, s));
+    if (!titems.empty())
+        IMQ_CUDA(cudaMemcpyAsync(P.W.items.ptr, titems.data(), 4 * titems.size(), cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemsetAsync(P.V.off.ptr, 0, 4 * (size_t)(nb + 1), s));
+    P.V.total = 0;
+    IMQ_CUDA(cudaMemsetAsync(P.vtab.ptr, 0xFF, sizeof(int32_t) * kOffsetClasses * (size_t)nb, s));
+    P.m2l_pairs = 0;
+    P.m2l_level_lo = IMQ_MAX_LEVEL + 1;
+    P.m2l_level_hi = 0;
+    IMQ_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups) {
     const int64_t N = P.N;
     int *err = device_error_word();
@@ -621,7 +668,7 @@ void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups
         if (nl == 0) break;
         AsyncMem qb(sizeof(int32_t) * 5 * nl, s), nch(sizeof(int32_t) * nl, s), cb(sizeof(int32_t) * nl, s),
             tot(sizeof(int32_t), s);
-        split_count<<<blocks_for(nl, 256), 256, 0, s>>>(lb, nl, lev, P.leaf, P.codes.as<uint32_t>(), begin.ptr(),
+        split_count<<<blocks_for(nl, 256), 256, 0, s>>>(lb, nl, lev, P.leaf, P.tc_depth, P.codes.as<uint32_t>(), begin.ptr(),
                                                          end.ptr(), prefix.ptr(), qb.as<int32_t>(), nch.as<int32_t>());
         IMQ_LAUNCH_CHECK();
         exclusive_scan<int32_t>(nch.as<int32_t>(), cb.as<int32_t>(), nl, tot.as<int32_t>(), s);
@@ -784,6 +831,7 @@ void build_tree(Plan &P, const double *d_points, cudaStream_t s, bool check_dups
     x_aux<<<blocks_for(nb, 128), 128, 0, s>>>(nb, P.begin.as<int32_t>(), P.end.as<int32_t>(), P.X.off.as<int32_t>(),
                                               P.X.items.as<int32_t>(), P.xcum.as<int32_t>(), P.xtot.as<int32_t>());
     IMQ_LAUNCH_CHECK();
+    if (P.tc_depth > 0) treecode_lists(P, s);
     build_m2l_tiles(P, s);
     int herr = 0;
     IMQ_CUDA(cudaMemcpyAsync(&herr, lerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -57,7 +57,10 @@ def _like(v, n_total: int, code: int):
 M2L_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
 
 
-def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto"):
+ALGORITHMS = {"fmm": 0, "treecode": 1}
+
+
+def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0):
     opt = ImqOptions()
     opt.struct_size = ctypes.sizeof(ImqOptions)
     if domain is not None:
@@ -65,18 +68,24 @@ def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto"):
         opt.x0, opt.y0, opt.side = (float(v) for v in domain)
     opt.check_duplicates = 1 if check_duplicates else 0
     opt.m2l_kernel = M2L_KERNELS[m2l_kernel]
+    opt.algorithm = ALGORITHMS[algorithm]
+    opt.levels = int(levels)
     return opt
 
 
 class Plan:
-    """imq_plan: quadtree, interaction lists and operators for (points, c, p, leaf)."""
+    """imq_plan: quadtree, interaction lists and operators for (points, c, p, leaf).
+
+    algorithm="treecode" with levels=L builds the paper's Algorithm 1 on a uniform
+    partition of 2^(L+1) x 2^(L+1) blocks at the finest level (leaf is ignored)."""
 
     def __init__(self, points, c: float, p: int, leaf: int, domain=None,
-                 check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto"):
+                 check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto",
+                 algorithm: str = "fmm", levels: int = 0):
         self._h = ctypes.c_void_p(0)
         pts_ptr, keep = _buf(points, torch.float64)
         n = int(np.shape(points)[0])
-        opt = _plan_options(domain, check_duplicates, m2l_kernel)
+        opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels)
         call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
         del keep

@@ -94,3 +94,21 @@ def test_autotune_arguments_rejected_before_any_gpu_work(lib):
     assert L.imq_autotune(*args(offs=(ctypes.c_int64 * 2)(0, 0))) == 1
     assert L.imq_autotune(*args(pts=None)) == 1
     assert ctypes.sizeof(_lib.TuneResult) == 32 + 64 * 24   # the C struct (sizeof checked with gcc)
+
+
+def test_treecode_options_checked_before_any_gpu_work(lib):
+    from paper_2205_04194_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p(0)
+    pts = (ctypes.c_double * 4)(0.0, 0.0, 1.0, 1.0)
+    opt = _lib.ImqOptions()
+    opt.struct_size = ctypes.sizeof(_lib.ImqOptions)
+    opt.algorithm = 1
+    opt.levels = 0                                   # the paper's L starts at 1
+    assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    opt.levels = 16
+    assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    opt.algorithm = 7
+    assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    assert b"unknown algorithm" in L.imq_last_error()
+    assert ctypes.sizeof(_lib.ImqOptions) == 64       # the C struct: fields kept at their offsets
