@@ -427,6 +427,13 @@ imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob,
  * ------------------------------------------------------------------------- */
 imq_status imq_sync_check(void *stream);
 
+/* imq_selftest_wait_timeout -- exercise the bounded-wait path: one kernel waits
+ * on a shared-memory barrier that nothing ever completes, gives up after the
+ * wait limit (0.5 s), records the timeout in the error word, and this call
+ * reads it back (as imq_sync_check does).  Returns IMQ_TIMEOUT when the path
+ * works; the context stays usable.  (Not an operation of the paper.) */
+imq_status imq_selftest_wait_timeout(void *stream);
+
 /* ------------------------------------------------------------------------- *
  * Introspection of a plan, for tests and benchmarks.
  * ------------------------------------------------------------------------- */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
     "imq_autotune": (INT, [P, P, INT, P, D, P, INT, P, INT, INT, P, P, P]),
     "imq_sync_check": (INT, [P]),
+    "imq_selftest_wait_timeout": (INT, [P]),
     "imq_plan_get_info": (INT, [P, P]),
     "imq_plan_export_tree": (INT, [P, P, P, P, P, P, P, P, P]),
     "imq_plan_export_list": (INT, [P, CHAR, P, P]),

@@ -439,6 +439,13 @@ imq_status imq_sync_check(void *stream) {
     return guard([&] { check_device_errors(static_cast<cudaStream_t>(stream)); });
 }
 
+imq_status imq_selftest_wait_timeout(void *stream) {
+    return guard([&] {
+        check_device();
+        selftest_wait_timeout(static_cast<cudaStream_t>(stream));
+    });
+}
+
 void imq_cg_default_options(imq_cg_options *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));

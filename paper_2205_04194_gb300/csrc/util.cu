@@ -126,6 +126,26 @@ AuxStream::~AuxStream() {
     if (hi) cudaStreamDestroy(hi);
 }
 
+namespace {
+// A wait that nothing satisfies: the bounded mbarrier wait gives up after its
+// limit and reports through the error word (self-test of the timeout path).
+__global__ void k_wait_never(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0) && threadIdx.x == 0) set_error(err, kErrWaitTimeout);
+}
+}  // namespace
+
+void selftest_wait_timeout(cudaStream_t s) {
+    k_wait_never<<<1, 32, 0, s>>>(device_error_word());
+    IMQ_LAUNCH_CHECK();
+    check_device_errors(s);
+}
+
 void check_device_errors(cudaStream_t s) {
     int *w = device_error_word();
     int h = 0;

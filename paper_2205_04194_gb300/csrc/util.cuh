@@ -18,6 +18,10 @@ int *device_error_word();
 // bounded wait ran out since the last check (the affected results are invalid).
 void check_device_errors(cudaStream_t s);
 
+// Launch one kernel whose bounded wait can never complete, then check the error
+// word: throws IMQ_TIMEOUT when the timeout path works.
+void selftest_wait_timeout(cudaStream_t s);
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace imq
