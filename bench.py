@@ -129,6 +129,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over the ranks of the default process group (x itself
+    without one): the step time of a replicated run is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_rows(points, c, v, seconds: float, min_rows: int = 8):
     """Time the FP64 dense oracle (O1) on a sample of rows sized to ~`seconds`."""
     from oracle import dense
@@ -424,11 +436,7 @@ def main():
         dist.barrier()
     launches = per_product * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), dev)
     # phase breakdown (library events around each phase's kernels), outside the timed region
     phase_tot = {k: 0.0 for k in imq.Plan.PHASES}
     for k in range(args.phase_steps):
@@ -466,11 +474,7 @@ def main():
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             e2e.append(1e3 * dt)
-    e2e_ms = statistics.mean(e2e)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(statistics.mean(e2e), dev)
 
     if rank != 0:
         dist.destroy_process_group()
