@@ -18,6 +18,7 @@
 #include "fmm_common.cuh"
 #include "imq_internal.h"
 #include "ptx.cuh"
+#include "umma.cuh"
 #include "util.cuh"
 
 namespace imq {
@@ -307,7 +308,8 @@ __device__ __forceinline__ void trans_rows_smem(const float *A, const float *X, 
 template <int RC, bool UP>
 __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__restrict__ parents, int n,
                                                            const int32_t *__restrict__ child, float *__restrict__ X,
-                                                           const float *__restrict__ op, int K, int *err) {
+                                                           const float *__restrict__ op, int K, int *err,
+                                                           float *__restrict__ Xpk, int KP) {
     extern __shared__ __align__(16) unsigned char smraw[];
     float *sop = reinterpret_cast<float *>(smraw);                 // [4][K][K]
     float *sx = sop + (size_t)4 * K * K;                            // [16 warps][K][4]; reused as red[4][16][K]
@@ -381,6 +383,12 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
             const float sum = ((red[(0 * kTS + g) * K + o] + red[(1 * kTS + g) * K + o]) + red[(2 * kTS + g) * K + o]) +
                               red[(3 * kTS + g) * K + o];
             X[(int64_t)s_par[g] * K + o] = sum;
+            if (Xpk) {   // the tf32 hi / lo rows the tensor-core M2L gathers
+                float *pk = Xpk + (int64_t)s_par[g] * 2 * KP;
+                const float hi = tf32_round(sum);
+                pk[o] = hi;
+                pk[KP + o] = tf32_round(sum - hi);
+            }
         }
     } else {
         float old[kTSG][RC];
@@ -763,14 +771,14 @@ template void p2l_odd_launch<float>(Plan &, const float *, float *, cudaStream_t
 template void p2l_odd_launch<double>(Plan &, const double *, double *, cudaStream_t);
 
 template <class T>
-void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches);
+void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches, float *Mpk = nullptr, int KP = 0);
 
 // P2M: the fixed-order FP32 kernel where one is compiled, else the generic one
 template <class T>
-void p2m_launch(Plan &P, const T *u, T *M, const T *coef, cudaStream_t s) {
+void p2m_launch(Plan &P, const T *u, T *M, const T *coef, cudaStream_t s, float *Mpk = nullptr, int KP = 0) {
     if constexpr (std::is_same<T, float>::value) {
         if (p2m_fixed_p_supported(P.p)) {
-            p2m_fixed_p_launch(P, u, M, coef, s);
+            p2m_fixed_p_launch(P, u, M, coef, s, Mpk, KP);
             return;
         }
     }
@@ -809,14 +817,15 @@ void ensure_parents(Plan &P, cudaStream_t s) {
     IMQ_CUDA(cudaStreamSynchronize(s));
 }
 
+// Xpk (upward, shared-memory kernel only): also write the tf32 hi / lo rows of the parents
 template <class T, bool UP>
 void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, bool downward, cudaStream_t s,
-                  int *launches) {
+                  int *launches, float *Xpk = nullptr, int KP = 0) {
     ensure_parents(P, s);
     if constexpr (std::is_same<T, float>::value) {
         if (K <= kTransSmemMaxK) {
             const int RC = (K + 31) / 32;
-            void (*kern)(const int32_t *, int, const int32_t *, float *, const float *, int, int *) =
+            void (*kern)(const int32_t *, int, const int32_t *, float *, const float *, int, int *, float *, int) =
                 RC == 1 ? k_trans_s<1, UP> : RC == 2 ? k_trans_s<2, UP> : RC == 3 ? k_trans_s<3, UP> : k_trans_s<4, UP>;
             const size_t smem = trans_s_smem(K);
             IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -836,7 +845,7 @@ void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, boo
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
                 const int32_t *par = P.parents.as<int32_t>() + pb, *ch = P.child.as<int32_t>();
-                IMQ_CUDA(cudaLaunchKernelEx(&cfg, kern, par, np, ch, (float *)X, (const float *)op, K, err));
+                IMQ_CUDA(cudaLaunchKernelEx(&cfg, kern, par, np, ch, (float *)X, (const float *)op, K, err, Xpk, KP));
                 ++*launches;
             }
             return;
@@ -872,11 +881,11 @@ void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, boo
 }
 
 template <class T>
-void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches) {
-    trans_launch<T, true>(P, M, m2m, P.layout.K, 2, P.max_level - 1, false, s, launches);
+void m2m_levels(Plan &P, T *M, const T *m2m, cudaStream_t s, int *launches, float *Mpk, int KP) {
+    trans_launch<T, true>(P, M, m2m, P.layout.K, 2, P.max_level - 1, false, s, launches, Mpk, KP);
 }
-template void m2m_levels<float>(Plan &, float *, const float *, cudaStream_t, int *);
-template void m2m_levels<double>(Plan &, double *, const double *, cudaStream_t, int *);
+template void m2m_levels<float>(Plan &, float *, const float *, cudaStream_t, int *, float *, int);
+template void m2m_levels<double>(Plan &, double *, const double *, cudaStream_t, int *, float *, int);
 template void upward_launch<float>(Plan &, const float *, float *, const float *, const float *, cudaStream_t, int *);
 template void upward_launch<double>(Plan &, const double *, double *, const double *, const double *, cudaStream_t, int *);
 
@@ -926,6 +935,10 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
                 *coef = O.p2mc.as<float>();
     ensure_m2p_items(P, s0);
     if (!P.near.ptr) P.near.alloc(sizeof(float) * (size_t)P.N);
+    // the tensor-core M2L's tf32 hi / lo rows are written by P2M and M2M themselves
+    // (both fixed-order / shared-memory kernels), so no packing pass sits on the chain
+    const bool fuse_pack = O.umma && P.n_m2l_tiles > 0 && p2m_fixed_p_supported(P.p) && K <= kTransSmemMaxK;
+    const int kp_pack = m2l_umma_kp(K);
     const bool conc = tm == nullptr;
     if (conc) P.aux.ensure();
     cudaStream_t sa = conc ? P.aux.s : s0, s = conc ? P.aux.hi : s0;
@@ -951,11 +964,11 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             launches += 2;
         }
         t0(kPhP2M);
-        p2m_launch<float>(P, u, M, coef, s);
+        p2m_launch<float>(P, u, M, coef, s, fuse_pack ? O.Mpk.as<float>() : nullptr, kp_pack);
         ++launches;
         t1();
         t0(kPhM2M);
-        m2m_levels<float>(P, M, m2m, s, &launches);
+        m2m_levels<float>(P, M, m2m, s, &launches, fuse_pack ? O.Mpk.as<float>() : nullptr, kp_pack);
         t1();
         if (conc) {
             IMQ_CUDA(cudaEventRecord(P.aux.mready, s));
@@ -974,8 +987,9 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         }
         t0(kPhM2L);
         if (P.n_m2l_tiles > 0 && O.umma) {
-            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s);
-            launches += 2;
+            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s,
+                            fuse_pack);
+            launches += fuse_pack ? 1 : 2;
         } else if (P.n_m2l_tiles > 0) {
             m2l_tiled_launch(P, M, L, m2l, s);
             ++launches;

@@ -274,7 +274,9 @@ int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t
 void build_m2l_tiles(Plan &P, cudaStream_t s);
 // p2m.cu: P2M for a compile-time order (FP32)
 bool p2m_fixed_p_supported(int p);
-void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s);
+// Mpk (may be null): also write the tf32 hi / lo rows [hi | pad to KP | lo | pad] of the tensor-core M2L
+void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s,
+                        float *Mpk = nullptr, int KP = 0);
 void p2l_fixed_p_prepare(cudaStream_t s);
 void p2l_fixed_p_launch(const Plan &P, const float *u, float *L, cudaStream_t s);
 // far.cu: L2P + M2P for a compile-time order (FP32)
@@ -290,8 +292,10 @@ void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s);
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
                       cudaStream_t s);
+// packed: Mpk already holds the hi / lo rows of every box (written by P2M and M2M)
 void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
-                     int Kout, cudaStream_t s);
+                     int Kout, cudaStream_t s, bool packed = false);
+int m2l_umma_kp(int K);   // padded row length KP of the hi / lo rows
 // batch.cu
 template <class T>
 void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,

@@ -349,6 +349,8 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
         k_m2l_images<<<blocks_for(chunks, 256), 256, 0, s>>>(ops, nblk, K, Kp, Kout, d.Kn, d.NKC, img.as<float>());
     IMQ_LAUNCH_CHECK();
     Mpk.alloc(sizeof(float) * (size_t)P.nbox * 2 * d.KP);
+    // the pads past K stay zero: the fused writers (P2M, M2M) store only the first K of each half
+    IMQ_CUDA(cudaMemsetAsync(Mpk.ptr, 0, sizeof(float) * (size_t)P.nbox * 2 * d.KP, s));
     tmask.alloc(sizeof(uint64_t) * (size_t)std::max(1, P.n_m2l_tiles));
     if (P.n_m2l_tiles > 0) {
         k_tile_masks<<<(P.n_m2l_tiles + 3) / 4, 128, 0, s>>>(P.m2l_tiles.as<int4>(), P.n_m2l_tiles,
@@ -358,13 +360,17 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
     }
 }
 
+int m2l_umma_kp(int K) { return 32 * ((K + 31) / 32); }
+
 void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
-                     int Kout, cudaStream_t s) {
+                     int Kout, cudaStream_t s, bool packed) {
     if (P.n_m2l_tiles == 0) return;
     const int K = P.layout.K;
     const UmmaDims d = umma_dims(K, Kout);
-    k_pack_m<<<blocks_for((int64_t)P.nbox * d.KP, 256), 256, 0, s>>>(M, P.nbox, K, d.KP, Mpk);
-    IMQ_LAUNCH_CHECK();
+    if (!packed) {
+        k_pack_m<<<blocks_for((int64_t)P.nbox * d.KP, 256), 256, 0, s>>>(M, P.nbox, K, d.KP, Mpk);
+        IMQ_LAUNCH_CHECK();
+    }
     const size_t smem = d.smem();
     int *err = device_error_word();
 #define IMQ_UMMA_CASE(SS, NCC)                                                                                    \

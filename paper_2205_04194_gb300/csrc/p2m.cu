@@ -24,6 +24,7 @@
 #include "fixed_order.cuh"
 #include "fmm_common.cuh"
 #include "imq_internal.h"
+#include "umma.cuh"
 #include "util.cuh"
 
 namespace imq {
@@ -56,7 +57,8 @@ __global__ void __launch_bounds__(32 * kP2MWarps) k_p2m_t(int nleaf, const int32
                                                           const int32_t *__restrict__ level,
                                                           const float2 *__restrict__ loc, const float *__restrict__ u,
                                                           float *__restrict__ M, int K,
-                                                          const float *__restrict__ coef, double S) {
+                                                          const float *__restrict__ coef, double S,
+                                                          float *__restrict__ Mpk, int KP) {
     constexpr int NC = ncplx(P);
     constexpr int NP = (NC + 31) / 32 * 32;
     constexpr int Q = NP / 32;
@@ -101,8 +103,20 @@ __global__ void __launch_bounds__(32 * kP2MWarps) k_p2m_t(int nleaf, const int32
         float re, im;
         up2(acc[k], re, im);
         const float cc = coef[slot];
-        Mb[slot] = cc * re;
-        if (m > 0) Mb[slot + 1] = cc * im;
+        const float vr = cc * re, vi = cc * im;
+        Mb[slot] = vr;
+        if (m > 0) Mb[slot + 1] = vi;
+        if (Mpk) {   // the tf32 hi / lo rows the tensor-core M2L gathers
+            float *pk = Mpk + (int64_t)b * 2 * KP;
+            const float hr = tf32_round(vr);
+            pk[slot] = hr;
+            pk[KP + slot] = tf32_round(vr - hr);
+            if (m > 0) {
+                const float hi = tf32_round(vi);
+                pk[slot + 1] = hi;
+                pk[KP + slot + 1] = tf32_round(vi - hi);
+            }
+        }
     }
 }
 
@@ -249,14 +263,15 @@ void p2l_fixed_p_launch(const Plan &P, const float *u, float *L, cudaStream_t s)
     IMQ_LAUNCH_CHECK();
 }
 
-void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s) {
+void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s, float *Mpk,
+                        int KP) {
     const unsigned grid = (unsigned)((P.nleaf + kP2MWarps - 1) / kP2MWarps);
     if (grid == 0) return;
 #define IMQ_P2M_CASE(PP)                                                                                          \
     case PP:                                                                                                     \
         k_p2m_t<PP><<<grid, 32 * kP2MWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),      \
                                                     P.end.as<int32_t>(), P.level.as<int32_t>(),                  \
-                                                    P.loc.as<float2>(), u, M, P.layout.K, coef, P.side);         \
+                                                    P.loc.as<float2>(), u, M, P.layout.K, coef, P.side, Mpk, KP); \
         break;
     switch (P.p) {
         IMQ_P2M_CASE(1)
