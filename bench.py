@@ -45,9 +45,9 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
 # SHA-256 of the kernel sources at capture time: once a source changes the figure is stale
 # and the bench reports null.  Summaries: profiles/launches_fast_product_clustered_1m.md.
 TRAFFIC = {
-    # k_m2l_umma 87.47 MB read + 0.21 MB written, k_pack_m 17.19 MB read (the M2L phase times both)
-    "m2l": {"bytes": 87.47e6 + 0.21e6 + 17.19e6, "sources": {
-        "paper_2205_04194_gb300/csrc/m2l_umma.cu": "d925151ba794c28ab67f2ecafcc9f8208ea6c1de4d225e2393697c0e25ac2340",
+    # k_m2l_umma: 87.44 MB read + 0.28 MB written per launch (its tf32 rows come from P2M / M2M)
+    "m2l": {"bytes": 87.44e6 + 0.28e6, "sources": {
+        "paper_2205_04194_gb300/csrc/m2l_umma.cu": "9e188a398c2404daff8adacc4ba048cec2aff56d02309329976aeda8ede08319",
         "paper_2205_04194_gb300/csrc/umma.cuh": "a133f64894a1d5c359ee5202af3f44414abc786ea60768f20a375cecf456fcd6",
         "paper_2205_04194_gb300/csrc/ptx.cuh": "9f11aae585d997f977cfb9515e1a6d3900bf168e91c1a75824dfdb29176bb76c"}},
 }
@@ -519,7 +519,7 @@ def main():
                 "peak_source": f"derived: {N_SM} SMs x {MUFU_PER_CLK_SM} MUFU rsqrt/clk x {mhz:.0f} MHz "
                                f"({src} sm_max_mhz)"}
     else:
-        roof = {"kernel": "k_m2l_umma (tcgen05 kind::tf32, 3xTF32) + k_pack_m", "bound": "tensor",
+        roof = {"kernel": "k_m2l_umma (tcgen05 kind::tf32, 3xTF32)", "bound": "tensor",
                 "achieved": m2l_tf, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m2l_tf / tf32_peak,
                 "traffic": _traffic("m2l") if (wl.n == 1_000_000 and wl.p == 12) else None,
                 "achieved_executed": m2l_exec_tf, "frac_executed": m2l_exec_tf / tf32_peak,
