@@ -166,7 +166,17 @@ void imq_plan_destroy(imq_plan_t plan);
  *   out : [nrhs][N] of dtype, host or device, in the caller's point order.
  *   dt  : IMQ_F32 -- every kernel in FP32 except the FP64 operator set-up;
  *         IMQ_F64 -- every kernel in FP64.
- *   Errors: IMQ_INVALID_ARG (nrhs < 1, NULL pointers), IMQ_OOM, IMQ_CUDA_ERROR.
+ *   Streams: with device buffers the call only enqueues work.  The FP32
+ *   product forks from `stream` onto two streams the plan owns (the far-field
+ *   chain at the highest priority, P2L / P2P / M2P at the lowest) and joins
+ *   them back into `stream` before its last kernel, so later work on `stream`
+ *   is ordered after the product.  A plan serves one call at a time: calls on
+ *   the same plan from several host threads, or on streams that overlap, must
+ *   be serialised by the caller.  With host buffers the call synchronises.
+ *   A kernel's bounded wait that ran out is reported by the next call that
+ *   synchronises, or by imq_sync_check.
+ *   Errors: IMQ_INVALID_ARG (nrhs < 1, NULL pointers), IMQ_OOM, IMQ_CUDA_ERROR,
+ *   IMQ_TIMEOUT (host buffers only, see above).
  * ------------------------------------------------------------------------- */
 imq_status imq_matvec(imq_plan_t plan, const void *v, void *out, int nrhs,
                       imq_dtype dt, void *stream);
