@@ -106,13 +106,13 @@ __global__ void __launch_bounds__(32 * kFarWarps, 8) k_m2p_t(
     wpart[it.w + lane] = m2p_value<P>(cm, vx, vy, c * c, c, hs);
 }
 
-// (At most 4 CTAs of 4 warps per SM: the unrolled evaluation keeps the leaf's
+// (At most 4 CTAs of 4 warps per SM, 2 from P = 13 on: the unrolled evaluation keeps the leaf's
 // coefficients in registers, and a tighter bound spills them to local memory.)
 // L2P at the points of each leaf, then the leaf's M2P partial sums added in W-list
 // order (the order of a serial loop over the list, so the sum is deterministic),
 // then (if given) the point's near-field sum.
 template <int P>
-__global__ void __launch_bounds__(32 * kFarWarps, 4) k_l2p_t(
+__global__ void __launch_bounds__(32 * kFarWarps, (P <= 12 ? 4 : 2)) k_l2p_t(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ level, const float2 *__restrict__ loc, const int32_t *__restrict__ woff,
     const int32_t *__restrict__ wbase, const float *__restrict__ L, const float *__restrict__ coef, int K, double S,
