@@ -160,3 +160,42 @@ def test_fixed_order_far_field_every_p(p):
     ofmm = fmm.fmm_matvec(pts, c, v, p, 24, (0.0, 0.0, 1.0))
     assert rel2(b32, ofmm) < 1e-6
     plan.close()
+
+
+def test_fast_full_size_uniform_100k_sampled_rows():
+    """The 100k configuration at its own p and leaf (12, 64), c = 2 x mean NN spacing."""
+    import torch
+    imq = _imq()
+    wl = W.uniform_100k()
+    v = W.random_vector(wl.n, 2)
+    plan = imq.Plan(cuda(wl.points), wl.c, wl.p, wl.leaf, domain=wl.domain)
+    b = host(plan.matvec(cuda(v, torch.float32)))
+    rows = np.random.default_rng(1).choice(wl.n, 2048, replace=False)
+    ref = dense.matvec_rows(wl.points, wl.c, v, rows)
+    assert rel2(b[rows], ref) < 1e-6
+    plan.close()
+
+
+def test_batched_256_full_size_sampled_rows():
+    """All 256 problems (3.7M points) in one batched plan at the bench's autotuned (p, leaf),
+    4 right-hand sides; 64 sampled rows of 16 problems against the FP64 oracle.  The
+    Franke data (positive, no cancellation) meets 1e-6; the trig sums cancel, so FP32
+    rounding of the sums leaves them near 1e-6 and they are held to 2e-6."""
+    import torch
+    imq = _imq()
+    probs = W.batched_256()
+    pts = [cuda(x) for x, _, _ in probs]
+    cs = [c for _, c, _ in probs]
+    f = np.concatenate([r for _, _, r in probs], axis=1)
+    bp = imq.BatchedPlan(pts, cs, 14, 128, domain=(0.0, 0.0, 1.0))
+    b = host(bp.matvec(cuda(f, torch.float32)))
+    offs = bp.offsets
+    g = np.random.default_rng(3)
+    for q in np.linspace(0, len(probs) - 1, 16).astype(int):
+        x, c, rhs = probs[q]
+        rows = g.choice(x.shape[0], min(64, x.shape[0]), replace=False)
+        for r in range(4):
+            ref = dense.matvec_rows(x, c, rhs[r], rows)
+            got = b[r, offs[q]:offs[q + 1]][rows]
+            assert rel2(got, ref) < (1e-6 if r == 0 else 2e-6), (q, r, rel2(got, ref))
+    bp.close()
