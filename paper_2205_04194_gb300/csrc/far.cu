@@ -20,6 +20,7 @@
 // first, one warp per (W entry, 32 points), into per-entry partial sums that
 // the L2P kernel adds in W-list order.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "f32x2.cuh"
@@ -207,10 +208,12 @@ void ensure_m2p_items(Plan &P, cudaStream_t s) {
 namespace {
 
 std::vector<int> g_tables_ready;   // per device
+std::mutex g_tables_mu;            // plans may be built from several host threads
 
 void upload_tables(cudaStream_t s) {
     int dev = 0;
     IMQ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tables_mu);
     if ((int)g_tables_ready.size() <= dev) g_tables_ready.resize(dev + 1, 0);
     if (g_tables_ready[dev]) return;
     std::vector<float> A((kMaxP + 1) * (kMaxP + 1), 0.f), B(A.size(), 0.f), F(kMaxP + 2, 0.f);

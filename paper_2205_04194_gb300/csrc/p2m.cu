@@ -18,6 +18,7 @@
 // the concatenated source points of the X entries and the same butterfly
 // reduction closes the warp.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "f32x2.cuh"
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(32 * kP2LWarps) k_p2l_t(
 }
 
 std::vector<int> g_p2l_tables;   // per device
+std::mutex g_p2l_mu;             // plans may be built from several host threads
 
 }  // namespace
 
@@ -209,6 +211,7 @@ bool p2m_fixed_p_supported(int p) { return p >= 1 && p <= 16; }
 void p2l_fixed_p_prepare(cudaStream_t s) {
     int dev = 0;
     IMQ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_p2l_mu);
     if ((int)g_p2l_tables.size() <= dev) g_p2l_tables.resize(dev + 1, 0);
     if (g_p2l_tables[dev]) return;
     std::vector<float> A((kMaxPT + 1) * (kMaxPT + 1), 0.f), B(A.size(), 0.f), F(kMaxPT + 2, 0.f);
