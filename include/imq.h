@@ -78,6 +78,16 @@ typedef struct imq_options {
     int32_t levels;            /* IMQ_ALG_TREECODE: the paper's L (1..15): blocks of the
                                   finest level are 2^(L+1) x 2^(L+1); `leaf` is ignored      */
     int32_t reserved[4];
+    /* Optional allocator of the plan's own device buffers (tree, lists, operators,
+     * expansions, solver work arrays), e.g. a framework's caching allocator.  Both
+     * NULL: cudaMalloc / cudaFree.  alloc returns device memory of at least `bytes`
+     * (16-byte aligned) or NULL (the call then fails with IMQ_OOM); free receives
+     * each such block once, when the plan is destroyed or the buffer is replaced,
+     * after the device has finished with it.  Per-call temporaries stay
+     * stream-ordered (cudaMallocAsync).  Read only when struct_size covers them. */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *ctx);
+    void *alloc_ctx;
 } imq_options;
 
 /* How imq_matvec evaluates the product.

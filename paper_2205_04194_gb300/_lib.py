@@ -28,10 +28,15 @@ class ImqError(RuntimeError):
         super().__init__(f"{func}: {status_name(status)}: {msg}")
 
 
+# caller-supplied allocator of a plan's device buffers (imq_options.alloc / free)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
 class ImqOptions(ctypes.Structure):
     _fields_ = [("struct_size", I32), ("has_domain", I32), ("x0", D), ("y0", D), ("side", D),
                 ("check_duplicates", I32), ("m2l_kernel", I32), ("algorithm", I32), ("levels", I32),
-                ("reserved", I32 * 4)]
+                ("reserved", I32 * 4), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", P)]
 
 
 class PlanInfo(ctypes.Structure):

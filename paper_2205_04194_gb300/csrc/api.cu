@@ -139,6 +139,18 @@ const char *imq_version(void) { return "imq-gb300 0.1 (sm_103a)"; }
 
 namespace {
 
+Allocator plan_allocator(const imq_options *opt) {
+    Allocator a;
+    if (opt && opt->struct_size >= (int)(offsetof(imq_options, alloc_ctx) + sizeof(void *))) {
+        if ((opt->alloc == nullptr) != (opt->free == nullptr))
+            fail(IMQ_INVALID_ARG, "imq_plan: imq_options.alloc and free must be given together");
+        a.alloc = opt->alloc;
+        a.free = opt->free;
+        a.ctx = opt->alloc_ctx;
+    }
+    return a;
+}
+
 void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
                      double &side, bool &dups, int *m2l_kernel = nullptr, int *algorithm = nullptr,
                      int *tc_depth = nullptr) {
@@ -180,8 +192,11 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
     bool dups;
     int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM, depth = 0;
     parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth);
+    const Allocator al = plan_allocator(opt);
     check_device();
     auto *h = new imq_plan_s;
+    h->P.allocator = al;
+    UseAllocator use(&h->P.allocator);
     try {
         Plan &P = h->P;
         IMQ_CUDA(cudaGetDevice(&P.device));
@@ -219,6 +234,7 @@ imq_status imq_plan(const double *points, int64_t N, double c, int p, int leaf, 
         double x0, y0, side;
         bool dups;
         parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups);   // argument errors before any GPU work
+        (void)plan_allocator(opt);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         check_device();
         DevIn pts(points, sizeof(double) * 2 * (size_t)N, s);
@@ -237,6 +253,7 @@ imq_status imq_plan_eval(const double *nodes, int64_t n_nodes, const double *tar
         double x0, y0, side;
         bool dups;
         parse_plan_args(n_nodes + n_targets, c, p, leaf, opt, x0, y0, side, dups);
+        (void)plan_allocator(opt);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         check_device();
         const int64_t N = n_nodes + n_targets;
@@ -267,6 +284,7 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
         bool dups;
         int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM;
         parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg);
+        (void)plan_allocator(opt);
         if (alg != IMQ_ALG_FMM) fail(IMQ_UNSUPPORTED, "imq_plan_batched: the treecode is built for single plans only");
         check_device();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -288,6 +306,8 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
             if (!(side > 0)) side = 1.0;
         }
         auto *hp = new imq_plan_s;
+        hp->P.allocator = plan_allocator(opt);
+        UseAllocator use(&hp->P.allocator);
         try {
             Plan &P = hp->P;
             IMQ_CUDA(cudaGetDevice(&P.device));
@@ -323,6 +343,7 @@ static void matvec_impl(imq_plan_t plan, const void *v, void *out, int nrhs, imq
     if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_matvec: nrhs must be >= 1");
     if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_matvec: unknown dtype");
     Plan &P = plan->P;
+    UseAllocator use(&P.allocator);   // buffers the plan creates lazily
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t es = dt == IMQ_F32 ? 4 : 8;
     const size_t bytes = es * (size_t)nrhs * P.N;
@@ -362,6 +383,7 @@ static void eval_impl(imq_plan_t plan, const void *in, void *out, int nrhs, imq_
     if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_evaluate: nrhs must be >= 1");
     if (dt != IMQ_F32 && dt != IMQ_F64) fail(IMQ_INVALID_ARG, "imq_evaluate: unknown dtype");
     Plan &P = plan->P;
+    UseAllocator use(&P.allocator);
     if (P.n_nodes <= 0) fail(IMQ_INVALID_ARG, "imq_evaluate: the plan was not made by imq_plan_eval");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t N = P.N, Nn = P.n_nodes, Nt = N - Nn;
@@ -471,6 +493,7 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
     const imq_status st = guard([&] {
         if (!plan || !f || !coef) fail(IMQ_INVALID_ARG, "imq_cg_solve: NULL pointer");
         if (nrhs < 1) fail(IMQ_INVALID_ARG, "imq_cg_solve: nrhs must be >= 1");
+        UseAllocator use(&plan->P.allocator);   // preconditioner factors and solver work arrays
         imq_cg_options o;
         imq_cg_default_options(&o);
         if (opt) {

@@ -40,16 +40,33 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 #define IMQ_LAUNCH_CHECK() ::imq::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
 
 // ---------------------------------------------------------------- device memory
+// Caller-supplied allocator of plan-owned buffers (imq_options.alloc / free).
+struct Allocator {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free)(void *, size_t, void *) = nullptr;
+    void *ctx = nullptr;
+};
+
+// While alive, DevMem::alloc on this thread uses `a` (if it has an alloc function).
+struct UseAllocator {
+    const Allocator *prev;
+    explicit UseAllocator(const Allocator *a);
+    ~UseAllocator();
+    UseAllocator(const UseAllocator &) = delete;
+    UseAllocator &operator=(const UseAllocator &) = delete;
+};
+
 struct DevMem {
     void *ptr = nullptr;
     size_t bytes = 0;
+    Allocator by;   // who allocated ptr (free == nullptr: cudaMalloc)
     DevMem() = default;
     DevMem(const DevMem &) = delete;
     DevMem &operator=(const DevMem &) = delete;
-    DevMem(DevMem &&o) noexcept : ptr(o.ptr), bytes(o.bytes) { o.ptr = nullptr; o.bytes = 0; }
+    DevMem(DevMem &&o) noexcept : ptr(o.ptr), bytes(o.bytes), by(o.by) { o.ptr = nullptr; o.bytes = 0; }
     DevMem &operator=(DevMem &&o) noexcept {
         release();
-        ptr = o.ptr; bytes = o.bytes; o.ptr = nullptr; o.bytes = 0;
+        ptr = o.ptr; bytes = o.bytes; by = o.by; o.ptr = nullptr; o.bytes = 0;
         return *this;
     }
     ~DevMem() { release(); }
@@ -153,6 +170,7 @@ struct AuxStream {
 };
 
 struct Plan {
+    Allocator allocator;   // the caller's allocator of this plan's buffers (empty: cudaMalloc)
     int device = 0;
     int64_t N = 0;
     double c = 0, x0 = 0, y0 = 0, side = 1;

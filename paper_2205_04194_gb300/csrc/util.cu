@@ -23,9 +23,24 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     fail(IMQ_CUDA_ERROR, buf);
 }
 
+namespace {
+thread_local const Allocator *t_alloc = nullptr;
+}
+
+UseAllocator::UseAllocator(const Allocator *a) : prev(t_alloc) { t_alloc = (a && a->alloc) ? a : nullptr; }
+UseAllocator::~UseAllocator() { t_alloc = prev; }
+
 void DevMem::alloc(size_t n) {
     release();
     if (n == 0) n = 16;
+    if (t_alloc) {
+        ptr = t_alloc->alloc(n, t_alloc->ctx);
+        if (!ptr) fail(IMQ_OOM, "the caller's allocator returned NULL for " + std::to_string(n) + " bytes");
+        by = *t_alloc;
+        bytes = n;
+        return;
+    }
+    by = Allocator{};
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -37,9 +52,13 @@ void DevMem::alloc(size_t n) {
 }
 
 void DevMem::release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) {
+        if (by.free) by.free(ptr, bytes, by.ctx);
+        else cudaFree(ptr);
+    }
     ptr = nullptr;
     bytes = 0;
+    by = Allocator{};
 }
 
 AsyncMem::AsyncMem(size_t bytes, cudaStream_t s) : stream(s) {

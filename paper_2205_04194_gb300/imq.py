@@ -60,9 +60,27 @@ M2L_KERNELS = {"auto": 0, "cuda_cores": 1, "tensor": 2}
 ALGORITHMS = {"fmm": 0, "treecode": 1}
 
 
-def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0):
+def _torch_allocator():
+    """(alloc, free) callbacks that serve a plan's device buffers from torch's caching
+    allocator on the current device; keep them alive as long as the plan."""
+    def _alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:   # noqa: BLE001 - reported to the library as an allocation failure
+            return None
+
+    def _free(ptr, nbytes, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+
+
+def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0,
+                  allocator=None):
     opt = ImqOptions()
     opt.struct_size = ctypes.sizeof(ImqOptions)
+    if allocator is not None:
+        opt.alloc, opt.free = allocator
     if domain is not None:
         opt.has_domain = 1
         opt.x0, opt.y0, opt.side = (float(v) for v in domain)
@@ -81,11 +99,13 @@ class Plan:
 
     def __init__(self, points, c: float, p: int, leaf: int, domain=None,
                  check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto",
-                 algorithm: str = "fmm", levels: int = 0):
+                 algorithm: str = "fmm", levels: int = 0, allocator: str | None = None):
         self._h = ctypes.c_void_p(0)
+        # allocator="torch": the plan's own buffers come from torch's caching allocator
+        self._alloc_cbs = _torch_allocator() if allocator == "torch" else None
         pts_ptr, keep = _buf(points, torch.float64)
         n = int(np.shape(points)[0])
-        opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels)
+        opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels, self._alloc_cbs)
         call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
         del keep

@@ -111,4 +111,17 @@ def test_treecode_options_checked_before_any_gpu_work(lib):
     opt.algorithm = 7
     assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
     assert b"unknown algorithm" in L.imq_last_error()
-    assert ctypes.sizeof(_lib.ImqOptions) == 64       # the C struct: fields kept at their offsets
+    assert ctypes.sizeof(_lib.ImqOptions) == 88       # the C struct (sizeof checked with gcc)
+
+
+def test_allocator_needs_both_functions(lib):
+    from paper_2205_04194_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p(0)
+    pts = (ctypes.c_double * 4)(0.0, 0.0, 1.0, 1.0)
+    opt = _lib.ImqOptions()
+    opt.struct_size = ctypes.sizeof(_lib.ImqOptions)
+    keep = _lib.ALLOC_FN(lambda n, ctx: None)
+    opt.alloc = keep                                  # free missing
+    assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    assert b"together" in L.imq_last_error()
