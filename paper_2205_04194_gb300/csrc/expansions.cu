@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
             if (i < K) reinterpret_cast<float4 *>(mx)[i] = make_float4(v[0][r], v[1][r], v[2][r], v[3][r]);
         }
     }
-    // a CTA-uniform verdict on the bounded wait, so that every thread leaves together
+    // a CTA-uniform outcome of the bounded wait, so that every thread leaves together
     if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
         if (threadIdx.x == 0) set_error(err, kErrWaitTimeout);
         return;   // the results of this product are invalid; the host reads the error word
