@@ -201,6 +201,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     out->rel_err = out->tried[best].rel_err;
     out->matvec_ms = out->tried[best].matvec_ms;
     out->sampled_rows = S;
+    check_device_errors(s);   // a bounded wait that ran out would invalidate the measured errors
 }
 
 }  // namespace imq
