@@ -366,11 +366,15 @@ imq_status imq_dense_matvec(const double *points, int64_t N, double c, const voi
  *            are rejected, since staging them would need an allocation).
  *   N      : 1 <= N <= IMQ_NOALLOC_MAX_N; larger N fails with IMQ_INVALID_ARG.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   All calls share the one array, which keeps the previous call's contents
- *   (each call clears its error word and rewrites the records it uses): calls
- *   that overlap on the GPU race and must be serialised by the caller, e.g.
- *   on one stream.  Work is enqueued on `stream`; the call does not wait.
+ *   (cudaGetSymbolAddress) and clears its error word; make that first call
+ *   before any stream capture.  All calls share the one array, which keeps the
+ *   previous call's contents (each call rewrites the records it uses): calls
+ *   that overlap on the GPU race and must be serialised by the caller, e.g. on
+ *   one stream.  Work is enqueued on `stream`; the call does not wait.
+ *   A tile wait in the kernel is bounded; one that runs out sets the array's
+ *   error word, which stays set until imq_sync_check reads and clears it
+ *   (IMQ_TIMEOUT, `out` of the affected calls invalid).  imq_sync_check
+ *   allocates nothing either.
  *   Errors: IMQ_INVALID_ARG, IMQ_UNSUPPORTED, IMQ_CUDA_ERROR.
  * ------------------------------------------------------------------------- */
 #define IMQ_NOALLOC_MAX_N 262144
@@ -435,13 +439,16 @@ imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob,
 /* ------------------------------------------------------------------------- *
  * imq_sync_check -- synchronise `stream` and report a failed bounded wait.
  *
- *   The kernels that wait on shared-memory barriers or on a grid barrier (the
- *   tensor-core M2L, the P2P source staging, the one-launch M2M/L2L) give up
- *   after a fixed number of polls instead of hanging, and record that in a
- *   per-device error word.  Calls that synchronise anyway (host output
- *   buffers, imq_matvec_timed, imq_cg_solve) check it themselves; after
- *   asynchronous imq_matvec calls on device buffers, call this before using
- *   the results.  Clears the word.  (Not an operation of the paper.)
+ *   The kernels that wait on shared-memory barriers (the tensor-core M2L
+ *   pipeline, the P2P source staging, the M2M/L2L operator copy, the dense
+ *   product's source tiles) give up after a bounded number of polls or 0.5 s
+ *   instead of hanging, and record that in a per-device error word (the
+ *   allocation-free dense product in the word of its own scratch array).
+ *   Calls that synchronise anyway (host output buffers, imq_matvec_timed,
+ *   imq_cg_solve, imq_dense_matvec) check it themselves; after asynchronous
+ *   imq_matvec or imq_dense_matvec_noalloc calls on device buffers, call this
+ *   before using the results.  Reads and clears both words; allocates no
+ *   device memory.  (Not an operation of the paper.)
  *   Errors: IMQ_TIMEOUT (a wait ran out since the last check: the results of
  *   the products in between are invalid), IMQ_CUDA_ERROR.
  * ------------------------------------------------------------------------- */

@@ -539,11 +539,8 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
     IMQ_CUDA(cudaStreamSynchronize(s));
 
     // ---- capture kIterPerGraph PCG iterations on a private stream
-    cudaStream_t cs;
-    IMQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    IMQ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    GraphCapture cap;
+    cudaStream_t cs = cap.begin();
     for (int it = 0; it < kIterPerGraph; ++it) {
         if (op == IMQ_OPERATOR_FAST_F32) {
             k_p_to_f32<<<gr, kRedThreads, 0, cs>>>(p, w.u32.as<float>(), n, S);
@@ -568,22 +565,11 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         k_update_p<<<gr, kRedThreads, 0, cs>>>(p, z, n, S);
         k_commit<<<1, 1, 0, cs>>>(S);
     }
-    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-    if (ce != cudaSuccess) {
-        cudaStreamDestroy(cs);
-        IMQ_CUDA(ce);
-    }
-    IMQ_CUDA(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
-    auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-    };
-
+    cudaGraphExec_t exec = cap.instantiate();
     const auto t0 = std::chrono::steady_clock::now();
     int total_iter = 0, outer_done = 0, final_status = kConverged;
     double worst_rel = 0;
-    try {
+    {
         for (int rhs = 0; rhs < nrhs; ++rhs) {
             const double *f = f_dev + (size_t)rhs * n;
             double *xo = x_dev + (size_t)rhs * n;
@@ -691,11 +677,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
             if (status != kConverged) final_status = status == kNumerical ? kNumerical : kMaxIter;
             if (info && rhs < IMQ_CG_MAX_RHS_INFO) info->rel_residual[rhs] = rel;
         }
-    } catch (...) {
-        cleanup();
-        throw;
     }
-    cleanup();
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
         info->iterations = total_iter;

@@ -255,17 +255,9 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     else fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, s);
     IMQ_CUDA(cudaStreamSynchronize(s));
 
-    cudaStream_t cs;
-    IMQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-    };
-    IMQ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    try {
+    GraphCapture cap;
+    cudaStream_t cs = cap.begin();
+    {
         for (int it = 0; it < kIterPerGraph; ++it) {
             if (f64op) {
                 fmm_apply<double>(P, p.as<double>(), q.as<double>(), 1, cs);
@@ -280,27 +272,14 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             if (pre) schwarz_apply(P, P.schwarz, r.as<double>(), zp, P.c, n, nullptr, cs);
             k_beta<<<B, kThreads, 0, cs>>>(r.as<double>(), zp, p.as<double>(), doff, S);
         }
-    } catch (...) {
-        cudaStreamEndCapture(cs, &graph);
-        cleanup();
-        throw;
     }
-    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-    if (ce != cudaSuccess) {
-        cleanup();
-        IMQ_CUDA(ce);
-    }
-    ce = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
-    if (ce != cudaSuccess) {
-        cleanup();
-        IMQ_CUDA(ce);
-    }
+    cudaGraphExec_t exec = cap.instantiate();
 
     const auto t0 = std::chrono::steady_clock::now();
     int total_iter = 0, outer_done = 0, final_status = kConverged;
     double worst_rel = 0;
     std::vector<BScalars> h(B);
-    try {
+    {
         for (int rhs = 0; rhs < nrhs; ++rhs) {
             const double *f = f_dev + (size_t)rhs * n;
             double *xo = x_dev + (size_t)rhs * n;
@@ -409,11 +388,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             worst_rel = std::max(worst_rel, rhs_worst);
             if (info && rhs < IMQ_CG_MAX_RHS_INFO) info->rel_residual[rhs] = rhs_worst;
         }
-    } catch (...) {
-        cleanup();
-        throw;
     }
-    cleanup();
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
         info->iterations = total_iter;

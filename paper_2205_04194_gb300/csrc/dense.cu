@@ -14,6 +14,7 @@
 
 #include "imq_internal.h"
 #include "ptx.cuh"
+#include "util.cuh"
 
 namespace imq {
 namespace {
@@ -177,8 +178,11 @@ static __device__ __align__(256) float4 g_noalloc_scratch[IMQ_NOALLOC_MAX_N + 1]
 std::mutex g_noalloc_mu;
 float4 *g_noalloc_addr[64] = {nullptr};
 
-// Device address of the scratch array on the current device, resolved once per device.
-float4 *noalloc_scratch() {
+// Device address of the scratch array on the current device, resolved once per
+// device.  The first resolution on a device also clears the error word (the
+// last record), enqueued on `s`; from then on the word collects the timeouts
+// of every call until imq_sync_check reads and clears it.
+float4 *noalloc_scratch(cudaStream_t s) {
     int dev = 0;
     IMQ_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) fail(IMQ_UNSUPPORTED, "imq_dense_matvec_noalloc: device index out of range");
@@ -191,6 +195,7 @@ float4 *noalloc_scratch() {
             fail(IMQ_CUDA_ERROR, std::string("imq_dense_matvec_noalloc: cudaGetSymbolAddress failed: ") +
                                      cudaGetErrorString(e));
         }
+        IMQ_CUDA(cudaMemsetAsync(static_cast<float4 *>(p) + IMQ_NOALLOC_MAX_N, 0, sizeof(float4), s));
         g_noalloc_addr[dev] = static_cast<float4 *>(p);
     }
     return g_noalloc_addr[dev];
@@ -207,6 +212,16 @@ bool is_device_memory(const void *p) {
 
 }  // namespace
 
+int *noalloc_error_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    return g_noalloc_addr[dev] ? reinterpret_cast<int *>(g_noalloc_addr[dev] + IMQ_NOALLOC_MAX_N) : nullptr;
+}
+
 void dense_matvec_noalloc(const double *points, int64_t N, double c, const float *v, float *out, cudaStream_t s) {
     if (!points || !v || !out) fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: NULL pointer");
     if (N < 1) fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: N must be >= 1");
@@ -218,9 +233,9 @@ void dense_matvec_noalloc(const double *points, int64_t N, double c, const float
     if (!is_device_memory(points) || !is_device_memory(v) || !is_device_memory(out))
         fail(IMQ_INVALID_ARG, "imq_dense_matvec_noalloc: points, v and out must be device memory");
     check_device();
-    float4 *src = noalloc_scratch();
+    float4 *src = noalloc_scratch(s);
+    // a bounded tile wait that runs out sets a bit here; imq_sync_check reports it
     int *err = reinterpret_cast<int *>(src + IMQ_NOALLOC_MAX_N);
-    IMQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     pack_sources<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(points, v, N, src);
     IMQ_LAUNCH_CHECK();
     const unsigned grid = (unsigned)((N + kThreads * kTPT - 1) / (kThreads * kTPT));

@@ -156,6 +156,24 @@ struct Schwarz {
     int64_t total_slots = 0;
 };
 
+// A CUDA graph captured on a private stream.  begin() creates the stream and
+// starts a thread-local capture; instantiate() ends it and returns the
+// executable graph.  If anything throws in between, the destructor ends a
+// capture still open and destroys the partial graph, the executable graph and
+// the stream, so no capture is left active and nothing leaks.
+struct GraphCapture {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capturing = false;
+    cudaStream_t begin();
+    cudaGraphExec_t instantiate();
+    GraphCapture() = default;
+    GraphCapture(const GraphCapture &) = delete;
+    GraphCapture &operator=(const GraphCapture &) = delete;
+    ~GraphCapture();
+};
+
 // Streams and fork/join events of the concurrent FP32 product (per plan): the
 // far-field chain runs on a highest-priority stream, the near field on a
 // lowest-priority one, so free SM slots go to the latency-bound chain first.

@@ -106,20 +106,51 @@ PhaseTimer::~PhaseTimer() {
 }
 
 // ------------------------------------------------------------------ device error word
-static std::mutex g_err_mu;
-static int *g_err_word[64] = {nullptr};
+// One int per device, a file-scope device variable: resolving its address
+// (cudaGetSymbolAddress, once per device) allocates nothing, so checking for a
+// failed bounded wait never needs device memory of its own.
+namespace {
+__device__ int g_err_word_dev;
+std::mutex g_err_mu;
+int *g_err_word[64] = {nullptr};
+}  // namespace
 
 int *device_error_word() {
     int dev = 0;
     IMQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(IMQ_UNSUPPORTED, "device index out of range");
     std::lock_guard<std::mutex> lk(g_err_mu);
     if (!g_err_word[dev]) {
-        int *p = nullptr;
-        IMQ_CUDA(cudaMalloc(&p, sizeof(int)));
-        IMQ_CUDA(cudaMemset(p, 0, sizeof(int)));
-        g_err_word[dev] = p;
+        void *p = nullptr;
+        IMQ_CUDA(cudaGetSymbolAddress(&p, g_err_word_dev));
+        g_err_word[dev] = static_cast<int *>(p);
     }
     return g_err_word[dev];
+}
+
+cudaStream_t GraphCapture::begin() {
+    IMQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    IMQ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+    return cs;
+}
+
+cudaGraphExec_t GraphCapture::instantiate() {
+    capturing = false;
+    IMQ_CUDA(cudaStreamEndCapture(cs, &graph));
+    IMQ_CUDA(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
+    return exec;
+}
+
+GraphCapture::~GraphCapture() {
+    if (capturing) {
+        cudaGraph_t partial = nullptr;
+        if (cudaStreamEndCapture(cs, &partial) == cudaSuccess && partial) cudaGraphDestroy(partial);
+        (void)cudaGetLastError();
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
 }
 
 void AuxStream::ensure() {
@@ -166,15 +197,20 @@ void selftest_wait_timeout(cudaStream_t s) {
 }
 
 void check_device_errors(cudaStream_t s) {
-    int *w = device_error_word();
-    int h = 0;
-    IMQ_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the shared word, and the allocation-free dense product's own word if that
+    // entry point has run on this device
+    int *w[2] = {device_error_word(), noalloc_error_word()};
+    int h[2] = {0, 0};
+    for (int k = 0; k < 2; ++k)
+        if (w[k]) IMQ_CUDA(cudaMemcpyAsync(&h[k], w[k], sizeof(int), cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaStreamSynchronize(s));
-    if (h) {
-        IMQ_CUDA(cudaMemsetAsync(w, 0, sizeof(int), s));
+    const int any = h[0] | h[1];
+    if (any) {
+        for (int k = 0; k < 2; ++k)
+            if (h[k]) IMQ_CUDA(cudaMemsetAsync(w[k], 0, sizeof(int), s));
         IMQ_CUDA(cudaStreamSynchronize(s));
-        if (h & kErrWaitTimeout) fail(IMQ_TIMEOUT, "a bounded wait in a kernel ran out; results are invalid");
-        fail(IMQ_CUDA_ERROR, "a kernel reported error flags " + std::to_string(h));
+        if (any & kErrWaitTimeout) fail(IMQ_TIMEOUT, "a bounded wait in a kernel ran out; results are invalid");
+        fail(IMQ_CUDA_ERROR, "a kernel reported error flags " + std::to_string(any));
     }
 }
 

@@ -14,8 +14,13 @@ void exclusive_scan(const T *d_in, T *d_out, int64_t n, T *d_total, cudaStream_t
 // Per-device error word that kernels OR their DeviceError codes into.
 int *device_error_word();
 
-// Synchronise `s`, read and clear the device error word; throws IMQ_TIMEOUT if a
-// bounded wait ran out since the last check (the affected results are invalid).
+// Error word of imq_dense_matvec_noalloc on the current device (inside its fixed
+// scratch array), or nullptr if that entry point has not run on this device.
+int *noalloc_error_word();
+
+// Synchronise `s`, read and clear the device error words (the shared one and
+// the allocation-free dense product's); throws IMQ_TIMEOUT if a bounded wait
+// ran out since the last check (the affected results are invalid).
 void check_device_errors(cudaStream_t s);
 
 // Launch one kernel whose bounded wait can never complete, then check the error
