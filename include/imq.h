@@ -77,7 +77,13 @@ typedef struct imq_options {
                                   paper's treecode, Algorithm 1                              */
     int32_t levels;            /* IMQ_ALG_TREECODE: the paper's L (1..15): blocks of the
                                   finest level are 2^(L+1) x 2^(L+1); `leaf` is ignored      */
-    int32_t reserved[4];
+    int32_t translations;      /* imq_translations: precision of M2M / M2L / L2L in the FP32
+                                  product (IMQ_ALG_FMM, p <= 16)                             */
+    /* Tile shapes of the FP32 product (0: the default; imq_autotune measures them):        */
+    int32_t p2p_warps;         /* target leaves (warps) per P2P CTA: 2, 4 (default) or 8    */
+    int32_t p2p_chunk;         /* targets per P2P register tile: 8, 16 (default) or 32      */
+    int32_t m2l_stages;        /* tensor-core M2L pipeline stages: 2..4 (default: as many as
+                                  fit in shared memory; more than fit is clamped)            */
     /* Optional allocator of the plan's own device buffers (tree, lists, operators,
      * expansions, solver work arrays), e.g. a framework's caching allocator.  Both
      * NULL: cudaMalloc / cudaFree.  alloc returns device memory of at least `bytes`
@@ -103,6 +109,18 @@ typedef struct imq_options {
  *              (M2P over the union of the V lists of the target block's
  *              ancestors), and the direct sum over NS_p at level L (U lists). */
 typedef enum imq_algorithm { IMQ_ALG_FMM = 0, IMQ_ALG_TREECODE = 1 } imq_algorithm;
+
+/* Precision of the translations (M2M, M2L, L2L) inside the FP32 product of
+ * imq_matvec and of the CG inner iterations.  P2M, P2L, P2P, M2P and L2P stay
+ * FP32 either way.
+ *   FP32 : every kernel in FP32, M2L on the tensor cores (fastest).
+ *   FP64 : the multipoles are widened after P2M and translated in FP64, the
+ *          locals narrowed before L2P.  When the data make the far-field sums
+ *          cancel (oscillating vectors, flat shapes), the FP32 rounding of the
+ *          translated coefficients sets the error floor of the product
+ *          (relative 2-norm error ~1e-6 at c ~ 0.15-0.2 on trig-sum vectors);
+ *          FP64 translations remove that term at the cost of FP64 M2L. */
+typedef enum imq_translations { IMQ_TRANS_FP32 = 0, IMQ_TRANS_FP64 = 1 } imq_translations;
 
 /* M2L kernel of the FP32 product.  AUTO takes the tensor cores when the
  * expansion fits them (K, K_out <= 256 reals), else the CUDA cores.
@@ -302,16 +320,18 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
  *
  *   f, coef      : double[nrhs][N_total], problems in the plan's order.
  *   rel_residual : host double[nrhs][nprob] or NULL: true relative residual
- *                  ||f_b - A_b coef_b|| / ||f_b|| of each problem (FP64 fast
- *                  product of the plan).
+ *                  ||f_b - A_b coef_b|| / ||f_b|| of each problem, computed with
+ *                  the FP64 product opt->residual selects (the plan's fast
+ *                  product, or the dense product of each problem with itself).
  *   iterations   : host int32[nrhs][nprob] or NULL: inner iterations of each
  *                  problem.
  *   info         : iterations = sum over right-hand sides of the largest
  *                  per-problem count; rel_residual[r] and max_rel_residual
  *                  are maxima over the problems.
+ *   The dense inner operator and the dense residual are block diagonal: each
+ *   problem's points only with each other (O(sum N_b^2) FP64 work).
  *   Errors: as imq_cg_solve; IMQ_INVALID_ARG if the plan is not batched;
- *   IMQ_UNSUPPORTED for the dense inner operator or residual (they would
- *   couple the problems) and for residual_plan.
+ *   IMQ_UNSUPPORTED for residual_plan.
  * ------------------------------------------------------------------------- */
 imq_status imq_cg_solve_batched(imq_plan_t plan, const double *f, double *coef, int nrhs,
                                 const imq_cg_options *opt, imq_cg_info *info, double *rel_residual,
@@ -382,14 +402,23 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
                                     float *out, void *stream);
 
 /* ------------------------------------------------------------------------- *
- * imq_autotune -- choose the truncation order p and the leaf size.
+ * imq_autotune -- choose the truncation order p, the leaf size, the precision
+ * of the translations and the tile shapes of the FP32 product.
  *
  *   The paper fixes M (= p) from the a-priori bound of Theorem 2.1 (worked
  *   example, Section 2.2) and the number of levels L by balancing the far-
- *   and near-field multiplication counts (Section 2.3).  Here both are
- *   measured: for each leaf size in leaf_cand, the smallest p in p_cand whose
- *   FP32 fast product meets `target` (relative 2-norm error on sampled rows,
- *   worst over problems and right-hand sides), then the fastest of those.
+ *   and near-field multiplication counts (Section 2.3).  Here everything is
+ *   measured:
+ *     1. for each leaf size in leaf_cand, the smallest p in p_cand whose FP32
+ *        fast product meets `target` (relative 2-norm error on sampled rows,
+ *        worst over problems and right-hand sides), then the fastest of those;
+ *     2. if no candidate meets the target with FP32 translations, step 1 again
+ *        with FP64 translations (IMQ_TRANS_FP64), whose error floor is lower;
+ *     3. on the chosen (p, leaf, translations), the P2P tile shape (p2p_warps x
+ *        p2p_chunk in {2, 4, 8} x {8, 16, 32}), then the tensor-core M2L
+ *        pipeline depth (m2l_stages 2..4, as far as they fit): the fastest
+ *        shape whose error still meets the target (else whose error does not
+ *        grow by more than 1 %).
  *   If no candidate meets the target, the most accurate one is returned and
  *   met = 0.
  *
@@ -402,7 +431,8 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  *   p_cand  : HOST int32[n_p], 1 <= n_p <= 16, each in [1, IMQ_MAX_P].
  *   leaf_cand : HOST int32[n_leaf], 1 <= n_leaf <= 16, each >= 1.
  *   nrhs    : right-hand sides of the timed product, 1..16.
- *   opt     : plan options (domain, M2L kernel), may be NULL.
+ *   opt     : plan options (domain, M2L kernel), may be NULL; its translations
+ *             and tile fields are ignored (they are what is tuned).
  *   out     : HOST result; out->tried lists every configuration measured.
  *
  *   Sample: 2048 rows (single problem) or 32 rows per problem, evenly spaced
@@ -418,6 +448,8 @@ typedef struct imq_tune_entry {
     int32_t p, leaf;
     double rel_err;          /* sampled relative 2-norm error of the FP32 product */
     float matvec_ms;         /* best of the timed products                         */
+    int32_t translations;    /* imq_translations                                   */
+    int32_t p2p_warps, p2p_chunk, m2l_stages;   /* tile shape (0: default)         */
     int32_t reserved;
 } imq_tune_entry;
 
@@ -428,6 +460,8 @@ typedef struct imq_tune_result {
     int32_t met;             /* 1 if rel_err <= target                             */
     int32_t n_tried;
     int32_t sampled_rows;
+    int32_t translations;    /* the choice's imq_translations                      */
+    int32_t p2p_warps, p2p_chunk, m2l_stages;   /* the choice's tile shape         */
     imq_tune_entry tried[IMQ_TUNE_MAX_TRIED];
 } imq_tune_result;
 

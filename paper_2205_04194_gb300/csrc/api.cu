@@ -153,7 +153,7 @@ Allocator plan_allocator(const imq_options *opt) {
 
 void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
                      double &side, bool &dups, int *m2l_kernel = nullptr, int *algorithm = nullptr,
-                     int *tc_depth = nullptr) {
+                     int *tc_depth = nullptr, bool *trans64 = nullptr) {
     if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
     if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
     if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
@@ -164,7 +164,7 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
     y0 = 0;
     side = -1;
     if (opt) {
-        if (opt->struct_size < (int)offsetof(imq_options, reserved))
+        if (opt->struct_size < (int)offsetof(imq_options, translations))
             fail(IMQ_INVALID_ARG, "imq_plan: imq_options.struct_size too small");
         if (opt->has_domain) {
             if (!std::isfinite(opt->x0) || !std::isfinite(opt->y0) || !std::isfinite(opt->side) || opt->side <= 0)
@@ -183,6 +183,30 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
             fail(IMQ_INVALID_ARG, "imq_plan: the treecode needs levels in [1, IMQ_MAX_LEVEL - 1]");
         if (algorithm) *algorithm = opt->algorithm;
         if (tc_depth) *tc_depth = opt->algorithm == IMQ_ALG_TREECODE ? opt->levels + 1 : 0;
+        if (opt->struct_size >= (int)(offsetof(imq_options, translations) + sizeof(int32_t))) {
+            if (opt->translations != IMQ_TRANS_FP32 && opt->translations != IMQ_TRANS_FP64)
+                fail(IMQ_INVALID_ARG, "imq_plan: unknown translations precision");
+            if (opt->translations == IMQ_TRANS_FP64 && (p > 16 || opt->algorithm != IMQ_ALG_FMM))
+                fail(IMQ_UNSUPPORTED, "imq_plan: FP64 translations need the fast multipole form and p <= 16");
+            if (trans64) *trans64 = opt->translations == IMQ_TRANS_FP64;
+        }
+        if (opt->struct_size >= (int)(offsetof(imq_options, m2l_stages) + sizeof(int32_t))) {
+            if (opt->p2p_warps != 0 && opt->p2p_warps != 2 && opt->p2p_warps != 4 && opt->p2p_warps != 8)
+                fail(IMQ_INVALID_ARG, "imq_plan: p2p_warps must be 0, 2, 4 or 8");
+            if (opt->p2p_chunk != 0 && opt->p2p_chunk != 8 && opt->p2p_chunk != 16 && opt->p2p_chunk != 32)
+                fail(IMQ_INVALID_ARG, "imq_plan: p2p_chunk must be 0, 8, 16 or 32");
+            if (opt->m2l_stages != 0 && (opt->m2l_stages < 2 || opt->m2l_stages > 4))
+                fail(IMQ_INVALID_ARG, "imq_plan: m2l_stages must be 0 or 2..4");
+        }
+    }
+}
+
+// tile shapes of the FP32 product from the options (0: default)
+void plan_tiles(Plan &P, const imq_options *opt) {
+    if (opt && opt->struct_size >= (int)(offsetof(imq_options, m2l_stages) + sizeof(int32_t))) {
+        P.p2p_warps = opt->p2p_warps;
+        P.p2p_chunk = opt->p2p_chunk;
+        P.m2l_stages = opt->m2l_stages;
     }
 }
 
@@ -191,7 +215,8 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
     double x0, y0, side;
     bool dups;
     int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM, depth = 0;
-    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth);
+    bool t64 = false;
+    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth, &t64);
     const Allocator al = plan_allocator(opt);
     check_device();
     auto *h = new imq_plan_s;
@@ -211,9 +236,12 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
         P.m2l_kernel = m2lk;
         P.algorithm = alg;
         P.tc_depth = depth;
+        P.trans64 = t64;
+        plan_tiles(P, opt);
         P.layout.build(p, 0);
         build_tree(P, d_points, s, dups);
         ensure_ops(P, false, s);
+        if (t64) ensure_ops(P, true, s);
         IMQ_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
         delete h;
@@ -283,7 +311,8 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
         double x0, y0, side;
         bool dups;
         int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM;
-        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg);
+        bool t64 = false;
+        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, nullptr, &t64);
         (void)plan_allocator(opt);
         if (alg != IMQ_ALG_FMM) fail(IMQ_UNSUPPORTED, "imq_plan_batched: the treecode is built for single plans only");
         check_device();
@@ -319,9 +348,12 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
             P.y0 = y0;
             P.side = side;
             P.m2l_kernel = m2lk;
+            P.trans64 = t64;
+            plan_tiles(P, opt);
             P.layout.build(p, 0);
             build_batched_plan(P, static_cast<const double *>(pts.ptr), offs, cs, dups, s);
             ensure_ops(P, false, s);
+            if (t64) ensure_ops(P, true, s);
             IMQ_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
             delete hp;

@@ -1,4 +1,5 @@
-// Autotuner: choose the truncation order p and the leaf size for a point set.
+// Autotuner: choose the truncation order p, the leaf size, the precision of
+// the translations and the tile shapes of the FP32 product for a point set.
 //
 // The paper fixes M (= p) from its a-priori bound (Theorem 2.1 and the worked
 // example of Section 2.2) and picks the number of levels L by balancing the
@@ -6,7 +7,11 @@
 // tree the leaf size plays the role of L, and the bound is pessimistic for the
 // M2L-based product, so both are chosen here by measurement: for each leaf
 // size the smallest p whose FP32 product meets the target relative 2-norm
-// error on a sample of exactly computed rows, then the fastest of those.
+// error on a sample of exactly computed rows, then the fastest of those (with
+// FP64 translations when no FP32 configuration meets the target); finally the
+// tile shapes (P2P warps and target chunk, M2L pipeline depth) of the choice,
+// with the paper's cost split (Section 2.3: near field against far field) as
+// the reason the leaf size and the P2P tile come first.
 //
 // Everything runs through the public entry points (imq_plan, imq_plan_batched,
 // imq_matvec, imq_plan_destroy); the exact rows are an FP64 direct sum over
@@ -142,64 +147,124 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     } ev{e0, e1};
     std::vector<float> picked((size_t)S * nrhs);
     std::memset(out, 0, sizeof(*out));
-    for (int li = 0; li < n_leaf; ++li) {
-        for (int p : ps) {
-            PlanHolder plan;
-            if (nprob == 1)
-                check(imq_plan(d_pts.as<double>(), N, cvals[0], p, leaf_cand[li], opt, s, &plan.h));
-            else
-                check(imq_plan_batched(d_pts.as<double>(), offsets, nprob, cvals, p, leaf_cand[li], opt, s, &plan.h));
-            check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));   // warm-up, and the error sample
-            k_pick_rows<<<blocks_for((int64_t)S * nrhs, 256), 256, 0, s>>>(d_b.as<float>(), N, nrhs,
-                                                                           d_row.as<int64_t>(), S, d_pick.as<float>());
-            IMQ_LAUNCH_CHECK();
-            IMQ_CUDA(cudaMemcpyAsync(picked.data(), d_pick.ptr, 4 * picked.size(), cudaMemcpyDeviceToHost, s));
-            float best_ms = INFINITY;
-            for (int rep = 0; rep < kTimedReps; ++rep) {
-                IMQ_CUDA(cudaEventRecord(e0, s));
-                check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));
-                IMQ_CUDA(cudaEventRecord(e1, s));
-                IMQ_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                IMQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                best_ms = std::min(best_ms, ms);
-            }
-            // relative 2-norm error over the sampled rows, per problem and right-hand side; the worst
-            std::vector<double> num((size_t)nprob * nrhs, 0.0), den((size_t)nprob * nrhs, 0.0);
-            for (int r = 0; r < nrhs; ++r)
-                for (int k = 0; k < S; ++k) {
-                    const double e = exact[(size_t)r * S + k], d = (double)picked[(size_t)r * S + k] - e;
-                    num[(size_t)r * nprob + prob_of[k]] += d * d;
-                    den[(size_t)r * nprob + prob_of[k]] += e * e;
-                }
-            double err = 0;
-            for (size_t k = 0; k < num.size(); ++k)
-                err = std::max(err, den[k] > 0 ? std::sqrt(num[k] / den[k]) : std::sqrt(num[k]));
-            if (out->n_tried < IMQ_TUNE_MAX_TRIED) {
-                imq_tune_entry &t = out->tried[out->n_tried++];
-                t.p = p;
-                t.leaf = leaf_cand[li];
-                t.rel_err = err;
-                t.matvec_ms = best_ms;
-            }
-            if (err <= target) break;   // the smallest p that meets the target at this leaf size
+    imq_options base{};
+    if (opt) std::memcpy(&base, opt, std::min(sizeof(base), (size_t)std::max(0, opt->struct_size)));
+    base.struct_size = sizeof(imq_options);
+    // build one configuration, measure its sampled error and best-of-3 time, record it
+    auto measure = [&](int p, int leaf, int trans, int warps, int chunk, int stages) -> int {
+        imq_options o = base;
+        o.translations = trans;
+        o.p2p_warps = warps;
+        o.p2p_chunk = chunk;
+        o.m2l_stages = stages;
+        PlanHolder plan;
+        if (nprob == 1)
+            check(imq_plan(d_pts.as<double>(), N, cvals[0], p, leaf, &o, s, &plan.h));
+        else
+            check(imq_plan_batched(d_pts.as<double>(), offsets, nprob, cvals, p, leaf, &o, s, &plan.h));
+        check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));   // warm-up, and the error sample
+        k_pick_rows<<<blocks_for((int64_t)S * nrhs, 256), 256, 0, s>>>(d_b.as<float>(), N, nrhs,
+                                                                       d_row.as<int64_t>(), S, d_pick.as<float>());
+        IMQ_LAUNCH_CHECK();
+        IMQ_CUDA(cudaMemcpyAsync(picked.data(), d_pick.ptr, 4 * picked.size(), cudaMemcpyDeviceToHost, s));
+        float best_ms = INFINITY;
+        for (int rep = 0; rep < kTimedReps; ++rep) {
+            IMQ_CUDA(cudaEventRecord(e0, s));
+            check(imq_matvec(plan.h, d_v.ptr, d_b.ptr, nrhs, IMQ_F32, s));
+            IMQ_CUDA(cudaEventRecord(e1, s));
+            IMQ_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            IMQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best_ms = std::min(best_ms, ms);
         }
-    }
+        // relative 2-norm error over the sampled rows, per problem and right-hand side; the worst
+        std::vector<double> num((size_t)nprob * nrhs, 0.0), den((size_t)nprob * nrhs, 0.0);
+        for (int r = 0; r < nrhs; ++r)
+            for (int k = 0; k < S; ++k) {
+                const double e = exact[(size_t)r * S + k], d = (double)picked[(size_t)r * S + k] - e;
+                num[(size_t)r * nprob + prob_of[k]] += d * d;
+                den[(size_t)r * nprob + prob_of[k]] += e * e;
+            }
+        double err = 0;
+        for (size_t k = 0; k < num.size(); ++k)
+            err = std::max(err, den[k] > 0 ? std::sqrt(num[k] / den[k]) : std::sqrt(num[k]));
+        if (out->n_tried >= IMQ_TUNE_MAX_TRIED) return -1;
+        imq_tune_entry &t = out->tried[out->n_tried];
+        t = imq_tune_entry{};
+        t.p = p;
+        t.leaf = leaf;
+        t.rel_err = err;
+        t.matvec_ms = best_ms;
+        t.translations = trans;
+        t.p2p_warps = warps;
+        t.p2p_chunk = chunk;
+        t.m2l_stages = stages;
+        return out->n_tried++;
+    };
+    // 1-2: the smallest p meeting the target per leaf size, FP32 translations first
+    auto search = [&](int trans) {
+        bool any = false;
+        for (int li = 0; li < n_leaf; ++li)
+            for (int p : ps) {
+                if (trans == IMQ_TRANS_FP64 && p > 16) continue;
+                const int k = measure(p, leaf_cand[li], trans, 0, 0, 0);
+                if (k < 0) return any;
+                if (out->tried[k].rel_err <= target) {
+                    any = true;
+                    break;
+                }
+            }
+        return any;
+    };
+    bool met = search(IMQ_TRANS_FP32);
+    if (!met && ps.front() <= 16) met = search(IMQ_TRANS_FP64);
     // the fastest configuration that meets the target, else the most accurate one
-    int best = -1;
-    for (int k = 0; k < out->n_tried; ++k) {
-        const imq_tune_entry &t = out->tried[k];
-        if (t.rel_err > target) continue;
-        if (best < 0 || t.matvec_ms < out->tried[best].matvec_ms) best = k;
-    }
+    auto pick = [&](int from) {
+        int best = -1;
+        for (int k = from; k < out->n_tried; ++k) {
+            const imq_tune_entry &t = out->tried[k];
+            if (t.rel_err > target) continue;
+            if (best < 0 || t.matvec_ms < out->tried[best].matvec_ms) best = k;
+        }
+        return best;
+    };
+    int best = pick(0);
     out->met = best >= 0 ? 1 : 0;
     if (best < 0)
         for (int k = 0; k < out->n_tried; ++k)
             if (best < 0 || out->tried[k].rel_err < out->tried[best].rel_err) best = k;
-    out->p = out->tried[best].p;
-    out->leaf = out->tried[best].leaf;
-    out->rel_err = out->tried[best].rel_err;
-    out->matvec_ms = out->tried[best].matvec_ms;
+    // 3: tile shapes of the chosen configuration, P2P first, then the M2L pipeline depth
+    const imq_tune_entry chosen = out->tried[best];
+    const double err_cap = out->met ? target : chosen.rel_err * 1.01;
+    auto better = [&](int k, int cur) {
+        return k >= 0 && out->tried[k].rel_err <= err_cap && out->tried[k].matvec_ms < out->tried[cur].matvec_ms;
+    };
+    int cur = best;
+    for (int warps : {2, 4, 8})
+        for (int chunk : {8, 16, 32}) {
+            const int k = measure(chosen.p, chosen.leaf, chosen.translations, warps, chunk, 0);
+            if (better(k, cur)) cur = k;
+        }
+    const int K = (chosen.p + 1) * (chosen.p + 2) / 2;   // reals of the parity-reduced expansion
+    const bool tensor = !chosen.translations && (!opt || opt->m2l_kernel != IMQ_M2L_CUDA_CORES) &&
+                        m2l_umma_supported(K, K);
+    if (tensor) {
+        const int smax = m2l_umma_max_stages(K, K);
+        const imq_tune_entry tp = out->tried[cur];
+        for (int stages = 2; stages <= smax; ++stages) {
+            const int k = measure(chosen.p, chosen.leaf, chosen.translations, tp.p2p_warps, tp.p2p_chunk, stages);
+            if (better(k, cur)) cur = k;
+        }
+    }
+    const imq_tune_entry &w = out->tried[cur];
+    out->p = w.p;
+    out->leaf = w.leaf;
+    out->rel_err = w.rel_err;
+    out->matvec_ms = w.matvec_ms;
+    out->translations = w.translations;
+    out->p2p_warps = w.p2p_warps;
+    out->p2p_chunk = w.p2p_chunk;
+    out->m2l_stages = w.m2l_stages;
     out->sampled_rows = S;
     check_device_errors(s);   // a bounded wait that ran out would invalidate the measured errors
 }

@@ -652,11 +652,15 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                     numerical = true;
                     break;
                 }
-                // without refinement steps, a pass that broke down after improving on its start is
-                // restarted from the true residual of its best iterate while iterations are left;
+                // without refinement steps, a pass that improved on its start and either broke down
+                // or met its target on the recursive residual is restarted from the true residual of
+                // its best iterate while iterations are left (the recursive residual of the FP32
+                // operator can drift below the true one, so only the true residual certifies);
                 // otherwise the next round only computes the final true residual
                 if (max_outer == 0) {
-                    if (hs.status == kBreakdown && hs.rr_best < hs.rr0 && restarts < kMaxRestarts) ++restarts;
+                    if ((hs.status == kBreakdown || hs.status == kConverged) && hs.rr_best < hs.rr0 &&
+                        restarts < kMaxRestarts)
+                        ++restarts;
                     else restarts = -1;
                 }
             }

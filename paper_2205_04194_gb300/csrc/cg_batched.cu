@@ -224,15 +224,17 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                       imq_cg_info *info, double *rel_out, int32_t *iters_out, cudaStream_t s) {
     const int64_t n = P.N;
     const int B = P.nprob;
-    if (o.inner_operator == IMQ_OPERATOR_DENSE_F64 || o.residual == IMQ_RESIDUAL_DENSE_F64)
-        fail(IMQ_UNSUPPORTED, "imq_cg_solve: the dense product couples the problems of a batched plan");
     if (o.residual_plan) fail(IMQ_UNSUPPORTED, "imq_cg_solve: residual_plan is not supported on batched plans");
+    // the dense FP64 products of a batched plan are block diagonal: each problem only with itself
+    const bool dense_res = o.residual == IMQ_RESIDUAL_DENSE_F64;
+    const bool dense_op = o.inner_operator == IMQ_OPERATOR_DENSE_F64;
     ensure_ops(P, false, s);
-    ensure_ops(P, true, s);   // the FP64 residual product
+    if (!dense_res || o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);   // FP64 fast product
     if (o.precond == IMQ_PRECOND_SCHWARZ)
         schwarz_setup(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
     const bool pre = o.precond == IMQ_PRECOND_SCHWARZ;
     const bool f64op = o.inner_operator == IMQ_OPERATOR_FAST_F64;
+    const double *dpos = P.pos.as<double>(), *dprob_c = P.prob_c.as<double>();
 
     DevMem x, xb, r, p, q, z, u32, b32, St, tmp, off, xs, fs, ax;
     for (DevMem *d : {&x, &xb, &r, &p, &q, &xs, &fs, &ax}) d->alloc(8 * n);
@@ -252,14 +254,17 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     IMQ_CUDA(cudaMemsetAsync(u32.ptr, 0, 4 * n, s));
     IMQ_CUDA(cudaMemsetAsync(p.ptr, 0, 8 * n, s));
     if (f64op) fmm_apply<double>(P, p.as<double>(), q.as<double>(), 1, s);
-    else fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, s);
+    else if (!dense_op) fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, s);
     IMQ_CUDA(cudaStreamSynchronize(s));
 
     GraphCapture cap;
     cudaStream_t cs = cap.begin();
     {
         for (int it = 0; it < kIterPerGraph; ++it) {
-            if (f64op) {
+            if (dense_op) {
+                dense_f64_seg_async(dpos, doff, B, dprob_c, p.as<double>(), q.as<double>(), n, cs);
+                k_alpha<<<B, kThreads, 0, cs>>>(nullptr, p.as<double>(), q.as<double>(), doff, S);
+            } else if (f64op) {
                 fmm_apply<double>(P, p.as<double>(), q.as<double>(), 1, cs);
                 k_alpha<<<B, kThreads, 0, cs>>>(nullptr, p.as<double>(), q.as<double>(), doff, S);
             } else {
@@ -293,7 +298,8 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             const int max_outer = std::max(0, o.refine_steps);
             int restarts = 0;
             auto true_residual = [&]() {
-                fmm_apply<double>(P, xs.as<double>(), ax.as<double>(), 1, s);
+                if (dense_res) dense_f64_seg_async(dpos, doff, B, dprob_c, xs.as<double>(), ax.as<double>(), n, s);
+                else fmm_apply<double>(P, xs.as<double>(), ax.as<double>(), 1, s);
                 k_sub<<<gs, 256, 0, s>>>(r.as<double>(), fs.as<double>(), ax.as<double>(), n);
                 IMQ_LAUNCH_CHECK();
                 return read_seg_dots(r.as<double>(), r.as<double>(), doff, B, tmp, s);
@@ -360,13 +366,15 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                     if (h[b].status == kNumerical) status[b] = kNumerical;
                 }
                 if (max_outer == 0) {
-                    // restart the problems whose pass broke down after improving on its start,
-                    // from the true residual of their best iterate; otherwise the next round only
+                    // restart the problems whose pass improved on its start and broke down or met
+                    // its target on the recursive residual, from the true residual of their best
+                    // iterate (only the true residual certifies); otherwise the next round only
                     // computes the final true residuals
                     bool restart = false;
                     for (int b = 0; b < B; ++b)
-                        restart |= status[b] != kNumerical && h[b].status == kBreakdown && h[b].rr_best < h[b].rr0 &&
-                                   iters[b] < o.maxit;
+                        restart |= status[b] != kNumerical &&
+                                   (h[b].status == kBreakdown || h[b].status == kConverged) &&
+                                   h[b].rr_best < h[b].rr0 && iters[b] < o.maxit;
                     if (restart && restarts < kMaxRestarts) ++restarts;
                     else restarts = -1;
                 }

@@ -126,10 +126,45 @@ __global__ void __launch_bounds__(256) dense_f64(const double *__restrict__ pts,
     if (t < n) out[t] = (Tout)acc;
 }
 
+// Block-diagonal FP64 dense product of a batched plan: points of problem b
+// occupy [off[b], off[b+1]) (Morton order); target i sums over the sources of
+// its own problem only, with that problem's shape.  One thread per target, the
+// problem found by binary search; sources are read through L1 (the threads of
+// a warp share one problem almost always, so their loads coincide).
+__global__ void __launch_bounds__(256) dense_f64_seg(const double2 *__restrict__ pos, const int64_t *__restrict__ off,
+                                                     int nprob, const double *__restrict__ prob_c,
+                                                     const double *__restrict__ v, int64_t n,
+                                                     double *__restrict__ out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int lo = 0, hi = nprob;   // off[lo] <= t < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const double c = prob_c[lo], c2 = c * c;
+    const double2 xt = pos[t];
+    double acc = 0.0;
+    for (int64_t j = off[lo]; j < off[lo + 1]; ++j) {
+        const double2 xs = pos[j];
+        const double dx = xt.x - xs.x, dy = xt.y - xs.y;
+        acc += v[j] / sqrt(fma(dx, dx, fma(dy, dy, c2)));
+    }
+    out[t] = acc;
+}
+
 }  // namespace
 
 void dense_f64_async(const double *d_points, int64_t N, double c, const double *d_v, double *d_out, cudaStream_t s) {
     dense_f64<double, double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(d_points, d_v, N, c * c, d_out);
+    IMQ_LAUNCH_CHECK();
+}
+
+void dense_f64_seg_async(const double *d_points, const int64_t *d_off, int nprob, const double *d_prob_c,
+                         const double *d_v, double *d_out, int64_t N, cudaStream_t s) {
+    dense_f64_seg<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(d_points), d_off,
+                                                               nprob, d_prob_c, d_v, N, d_out);
     IMQ_LAUNCH_CHECK();
 }
 

@@ -37,6 +37,17 @@ __global__ void k_scatter(const T *__restrict__ bs, const int32_t *__restrict__ 
     if (i < n) out[perm[i]] = (Tout)bs[i];
 }
 
+// ------------------------------------------------------------------ FP32 <-> FP64 expansion copies
+// (the FP32 product with FP64 translations: P2M / P2L / L2P in FP32, M2M / M2L / L2L in FP64)
+__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, int64_t n, int add) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = add ? b[i] + (double)a[i] : (double)a[i];
+}
+__global__ void k_narrow(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
 // ------------------------------------------------------------------ P2M
 // Mh_n^m = Ptilde_n^m(0) sum_j u_j conj(w_j)^m |w_j|^{n-m},  w_j = (y_j - z_B)/h_B.
 template <class T>
@@ -937,7 +948,14 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     if (!P.near.ptr) P.near.alloc(sizeof(float) * (size_t)P.N);
     // the tensor-core M2L's tf32 hi / lo rows are written by P2M and M2M themselves
     // (both fixed-order / shared-memory kernels), so no packing pass sits on the chain
-    const bool fuse_pack = O.umma && P.n_m2l_tiles > 0 && p2m_fixed_p_supported(P.p) && K <= kTransSmemMaxK;
+    // FP64 translations: the multipoles are widened after P2M, translated (M2M, M2L, L2L) in FP64
+    // and narrowed for M2P and L2P; the FP32 M2L path and its packed rows are not used
+    const bool t64 = P.trans64;
+    if (t64 && !P.ops64.ready) fail(IMQ_CUDA_ERROR, "FP64 translation operators missing");
+    double *Md = t64 ? P.ops64.M.as<double>() : nullptr, *Ld = t64 ? P.ops64.L.as<double>() : nullptr;
+    const int64_t nK = (int64_t)nb * K;
+    const unsigned gw = (unsigned)std::min<int64_t>(blocks_for(nK, 256), 4 * 152);
+    const bool fuse_pack = !t64 && O.umma && P.n_m2l_tiles > 0 && p2m_fixed_p_supported(P.p) && K <= kTransSmemMaxK;
     const int kp_pack = m2l_umma_kp(K);
     const bool conc = tm == nullptr;
     if (conc) P.aux.ensure();
@@ -968,7 +986,15 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         ++launches;
         t1();
         t0(kPhM2M);
-        m2m_levels<float>(P, M, m2m, s, &launches, fuse_pack ? O.Mpk.as<float>() : nullptr, kp_pack);
+        if (t64) {
+            k_widen<<<gw, 256, 0, s>>>(M, Md, nK, 0);
+            m2m_levels<double>(P, Md, P.ops64.m2m.as<double>(), s, &launches);
+            k_narrow<<<gw, 256, 0, s>>>(Md, M, nK);
+            IMQ_LAUNCH_CHECK();
+            launches += 2;
+        } else {
+            m2m_levels<float>(P, M, m2m, s, &launches, fuse_pack ? O.Mpk.as<float>() : nullptr, kp_pack);
+        }
         t1();
         if (conc) {
             IMQ_CUDA(cudaEventRecord(P.aux.mready, s));
@@ -986,7 +1012,14 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             t1();
         }
         t0(kPhM2L);
-        if (P.n_m2l_tiles > 0 && O.umma) {
+        if (t64) {
+            // M2L stores every box of its levels; then the P2L terms (in L) are added
+            IMQ_CUDA(cudaMemsetAsync(Ld, 0, sizeof(double) * (size_t)nK, s));
+            m2l_direct_launch<double>(P, Md, Ld, P.ops64.m2l.as<double>(), K, K, s, &launches);
+            k_widen<<<gw, 256, 0, s>>>(L, Ld, nK, 1);
+            IMQ_LAUNCH_CHECK();
+            ++launches;
+        } else if (P.n_m2l_tiles > 0 && O.umma) {
             m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s,
                             fuse_pack);
             launches += fuse_pack ? 1 : 2;
@@ -996,7 +1029,14 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         }
         t1();
         t0(kPhL2L);
-        l2l_launch<float>(P, L, l2l, K, s, &launches);
+        if (t64) {
+            l2l_launch<double>(P, Ld, P.ops64.l2l.as<double>(), K, s, &launches);
+            k_narrow<<<gw, 256, 0, s>>>(Ld, L, nK);
+            IMQ_LAUNCH_CHECK();
+            ++launches;
+        } else {
+            l2l_launch<float>(P, L, l2l, K, s, &launches);
+        }
         t1();
         if (!conc) {
             t0(kPhP2P);

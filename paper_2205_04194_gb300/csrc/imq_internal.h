@@ -200,6 +200,10 @@ struct Plan {
     int64_t n_nodes = 0; // evaluation plans: the first n_nodes points are nodes, the rest targets
     int m2l_kernel = 0;  // imq_m2l_kernel
     int algorithm = 0;   // imq_algorithm
+    bool trans64 = false; // FP32 product with M2M / M2L / L2L in FP64 (imq_options.translations)
+    // tile shapes of the FP32 product (imq_options; 0 = default): P2P warps per CTA and
+    // target chunk, tensor-core M2L pipeline stages
+    int p2p_warps = 0, p2p_chunk = 0, m2l_stages = 0;
     int tc_depth = 0;    // IMQ_ALG_TREECODE: depth of the uniform partition (paper's L + 1)
     int nprob = 1;       // batched plans: independent problems sharing one flattened tree
     DevMem box_prob;     // int32[nbox] problem of each box (batched plans only)
@@ -332,6 +336,7 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
 void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
                      int Kout, cudaStream_t s, bool packed = false);
 int m2l_umma_kp(int K);   // padded row length KP of the hi / lo rows
+int m2l_umma_max_stages(int K, int Kout);   // pipeline stages that fit in shared memory
 // batch.cu
 template <class T>
 void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,
@@ -343,6 +348,10 @@ void dense_matvec_dev(const double *d_points, int64_t N, double c, const void *d
                       int nrhs, imq_dtype dt, cudaStream_t s);
 // FP64 dense product, kernel launch only (no host synchronisation; graph-capturable)
 void dense_f64_async(const double *d_points, int64_t N, double c, const double *d_v, double *d_out, cudaStream_t s);
+// FP64 dense product of a batched plan's block-diagonal matrix, in Morton order:
+// problem b owns [d_off[b], d_off[b+1]) with shape d_prob_c[b] (kernel launch only)
+void dense_f64_seg_async(const double *d_points, const int64_t *d_off, int nprob, const double *d_prob_c,
+                         const double *d_v, double *d_out, int64_t N, cudaStream_t s);
 // api.cu helpers
 void check_device();
 template <class F>

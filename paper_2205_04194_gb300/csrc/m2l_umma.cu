@@ -362,11 +362,15 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
 
 int m2l_umma_kp(int K) { return 32 * ((K + 31) / 32); }
 
+int m2l_umma_max_stages(int K, int Kout) { return umma_dims(K, Kout).stages; }
+
 void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
                      int Kout, cudaStream_t s, bool packed) {
     if (P.n_m2l_tiles == 0) return;
     const int K = P.layout.K;
-    const UmmaDims d = umma_dims(K, Kout);
+    UmmaDims d = umma_dims(K, Kout);
+    // the plan's tile choice: fewer pipeline stages than fit (never more)
+    if (P.m2l_stages >= 2 && P.m2l_stages < d.stages) d.stages = P.m2l_stages;
     if (!packed) {
         k_pack_m<<<blocks_for((int64_t)P.nbox * d.KP, 256), 256, 0, s>>>(M, P.nbox, K, d.KP, Mpk);
         IMQ_LAUNCH_CHECK();
@@ -383,6 +387,10 @@ void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, 
         launched = true;                                                                                          \
     }
     bool launched = false;
+    IMQ_UMMA_CASE(2, 1)
+    IMQ_UMMA_CASE(2, 2)
+    IMQ_UMMA_CASE(2, 3)
+    IMQ_UMMA_CASE(2, 4)
     IMQ_UMMA_CASE(4, 1)
     IMQ_UMMA_CASE(4, 2)
     IMQ_UMMA_CASE(4, 3)

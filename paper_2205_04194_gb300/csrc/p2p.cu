@@ -193,8 +193,9 @@ __device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase
 }
 
 // STORE: write the near-field sum (b_near = sum); otherwise add it to bs.
-template <bool STORE>
-__global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
+// W warps per CTA (one target leaf each); targets in chunks of at most TCMAX.
+template <bool STORE, int W, int TCMAX>
+__global__ void __launch_bounds__(32 * W) k_p2p_f32(
     int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
     const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
     const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
         fence_mbar_init();
     }
     __syncwarp();
-    const int widx = blockIdx.x * kP2PWarps + w;
+    const int widx = blockIdx.x * W + w;
     if (widx >= nleaf) return;
     const int b = leaves[widx];
     const int tb = begin[b], nt = end[b] - tb;
@@ -218,18 +219,22 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f32(
     uint32_t phase = 0;
     const bool staged_all = St <= kStageCap;
     if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, St, begin, uitems, ucum, udelta, rec, lane, err)) return;
-    for (int tc = 0; tc < nt; tc += 16) {
-        const int ntc = min(16, nt - tc);
+    for (int tc = 0; tc < nt; tc += TCMAX) {
+        const int ntc = min(TCMAX, nt - tc);
         float tot;
         int tcap;
         if (ntc <= 8) {
             tot = p2p_chunk_staged<8>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
                                       udelta, loc, rec, c2, err);
             tcap = 8;
-        } else {
+        } else if (TCMAX == 16 || ntc <= 16) {
             tot = p2p_chunk_staged<16>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
                                        udelta, loc, rec, c2, err);
             tcap = 16;
+        } else {
+            tot = p2p_chunk_staged<(TCMAX > 16 ? 32 : 16)>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St,
+                                                           begin, uitems, ucum, udelta, loc, rec, c2, err);
+            tcap = TCMAX > 16 ? 32 : 16;
         }
         if (lane < tcap && lane < ntc) {
             if (STORE) bs[tb + tc + lane] = tot;
@@ -289,20 +294,38 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
 
 }  // namespace
 
+template <bool STORE, int W, int TCMAX>
+void p2p_f32_launch_t(Plan &P, float *bs, cudaStream_t s) {
+    const unsigned grid = (unsigned)((P.nleaf + W - 1) / W);
+    const size_t smem = sizeof(WarpStage) * W;
+    IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32<STORE, W, TCMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_p2p_f32<STORE, W, TCMAX><<<grid, 32 * W, smem, s>>>(
+        P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.U.off.as<int32_t>(),
+        P.U.items.as<int32_t>(), P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(), P.loc.as<float2>(),
+        P.rec4.as<float4>(), P.shape(), bs, device_error_word());
+    IMQ_LAUNCH_CHECK();
+}
+
+// The plan's P2P tile shape (warps per CTA, target chunk) selects the instance.
+template <bool STORE, int W>
+void p2p_f32_launch_w(Plan &P, float *bs, cudaStream_t s) {
+    switch (P.p2p_chunk) {
+        case 8: p2p_f32_launch_t<STORE, W, 8>(P, bs, s); break;
+        case 32: p2p_f32_launch_t<STORE, W, 32>(P, bs, s); break;
+        default: p2p_f32_launch_t<STORE, W, 16>(P, bs, s); break;
+    }
+}
+
 template <bool STORE>
 void p2p_f32_launch(Plan &P, const float *u, float *bs, cudaStream_t s) {
-    const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
     if (!P.rec4.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace missing");
     k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u, P.N, P.rec4.as<float4>());
     IMQ_LAUNCH_CHECK();
-    const size_t smem = sizeof(WarpStage) * kP2PWarps;
-    IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_p2p_f32<STORE><<<grid, 32 * kP2PWarps, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
-                                                        P.end.as<int32_t>(), P.U.off.as<int32_t>(),
-                                                        P.U.items.as<int32_t>(), P.ucum.as<int32_t>(),
-                                                        P.utot.as<int32_t>(), P.uoff.as<float2>(), P.loc.as<float2>(),
-                                                        P.rec4.as<float4>(), P.shape(), bs, device_error_word());
-    IMQ_LAUNCH_CHECK();
+    switch (P.p2p_warps) {
+        case 2: p2p_f32_launch_w<STORE, 2>(P, bs, s); break;
+        case 8: p2p_f32_launch_w<STORE, 8>(P, bs, s); break;
+        default: p2p_f32_launch_w<STORE, 4>(P, bs, s); break;
+    }
 }
 
 template <class T>

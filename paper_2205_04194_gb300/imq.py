@@ -75,8 +75,11 @@ def _torch_allocator():
     return _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
 
 
+TRANSLATIONS = {"fp32": 0, "fp64": 1}
+
+
 def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0,
-                  allocator=None):
+                  allocator=None, translations="fp32", p2p_warps=0, p2p_chunk=0, m2l_stages=0):
     opt = ImqOptions()
     opt.struct_size = ctypes.sizeof(ImqOptions)
     if allocator is not None:
@@ -88,6 +91,8 @@ def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algori
     opt.m2l_kernel = M2L_KERNELS[m2l_kernel]
     opt.algorithm = ALGORITHMS[algorithm]
     opt.levels = int(levels)
+    opt.translations = TRANSLATIONS[translations]
+    opt.p2p_warps, opt.p2p_chunk, opt.m2l_stages = int(p2p_warps), int(p2p_chunk), int(m2l_stages)
     return opt
 
 
@@ -99,13 +104,15 @@ class Plan:
 
     def __init__(self, points, c: float, p: int, leaf: int, domain=None,
                  check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto",
-                 algorithm: str = "fmm", levels: int = 0, allocator: str | None = None):
+                 algorithm: str = "fmm", levels: int = 0, allocator: str | None = None,
+                 translations: str = "fp32", p2p_warps: int = 0, p2p_chunk: int = 0, m2l_stages: int = 0):
         self._h = ctypes.c_void_p(0)
         # allocator="torch": the plan's own buffers come from torch's caching allocator
         self._alloc_cbs = _torch_allocator() if allocator == "torch" else None
         pts_ptr, keep = _buf(points, torch.float64)
         n = int(np.shape(points)[0])
-        opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels, self._alloc_cbs)
+        opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels, self._alloc_cbs,
+                            translations, p2p_warps, p2p_chunk, m2l_stages)
         call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
         del keep
@@ -295,7 +302,8 @@ class BatchedPlan(Plan):
     """imq_plan_batched: independent problems (points_b, c_b) in one flattened tree."""
 
     def __init__(self, points_list, c_list, p: int, leaf: int, domain=None, stream=None,
-                 m2l_kernel: str = "auto"):
+                 m2l_kernel: str = "auto", translations: str = "fp32", p2p_warps: int = 0, p2p_chunk: int = 0,
+                 m2l_stages: int = 0):
         self._h = ctypes.c_void_p(0)
         sizes = [int(np.shape(x)[0]) for x in points_list]
         offs = np.zeros(len(sizes) + 1, dtype=np.int64)
@@ -306,7 +314,8 @@ class BatchedPlan(Plan):
             pts = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in points_list]))
         cs = np.ascontiguousarray(np.asarray(c_list, dtype=np.float64))
         pp, kp = _buf(pts, torch.float64)
-        opt = _plan_options(domain, False, m2l_kernel)
+        opt = _plan_options(domain, False, m2l_kernel, translations=translations, p2p_warps=p2p_warps,
+                            p2p_chunk=p2p_chunk, m2l_stages=m2l_stages)
         call("imq_plan_batched", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes),
              ctypes.c_void_p(cs.ctypes.data), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
@@ -322,12 +331,13 @@ class BatchedPlan(Plan):
 
     def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, x0=None, operator="fast_f32",
-              schwarz_fp64=False, stream=None, raise_on_failure=False):
+              schwarz_fp64=False, residual="plan", stream=None, raise_on_failure=False):
         """imq_cg_solve_batched: every problem's system at once, per-problem CG scalars.
+        residual="dense" certifies each problem with its own dense FP64 product.
         info adds "problem_rel_residual" and "problem_iterations" ([nrhs, n_problems])."""
         return self._solve("imq_cg_solve_batched", f, coef, x0, stream, raise_on_failure, self.n_problems, dict(
             rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
-            refine_steps=refine_steps, inner_rtol=inner_rtol, residual="plan", residual_plan=None,
+            refine_steps=refine_steps, inner_rtol=inner_rtol, residual=residual, residual_plan=None,
             operator=operator, schwarz_fp64=schwarz_fp64))
 
 
@@ -392,10 +402,22 @@ def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
     call("imq_autotune", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes), ctypes.c_void_p(cs.ctypes.data),
          float(target), ctypes.c_void_p(pc.ctypes.data), len(pc), ctypes.c_void_p(lc.ctypes.data), len(lc),
          int(nrhs), ctypes.byref(opt), _stream(stream), ctypes.byref(res))
-    tried = [{"p": res.tried[k].p, "leaf": res.tried[k].leaf, "rel_err": res.tried[k].rel_err,
-              "matvec_ms": res.tried[k].matvec_ms} for k in range(res.n_tried)]
-    return {"p": res.p, "leaf": res.leaf, "rel_err": res.rel_err, "matvec_ms": res.matvec_ms,
-            "met": bool(res.met), "sampled_rows": res.sampled_rows, "tried": tried}
+    names = {v: k for k, v in TRANSLATIONS.items()}
+
+    def entry(t):
+        return {"p": t.p, "leaf": t.leaf, "rel_err": t.rel_err, "matvec_ms": t.matvec_ms,
+                "translations": names[t.translations], "p2p_warps": t.p2p_warps, "p2p_chunk": t.p2p_chunk,
+                "m2l_stages": t.m2l_stages}
+
+    tried = [entry(res.tried[k]) for k in range(res.n_tried)]
+    out = entry(res)
+    out.update({"met": bool(res.met), "sampled_rows": res.sampled_rows, "tried": tried})
+    return out
+
+
+def tiles_of(tune: dict) -> dict:
+    """Plan keyword arguments (translations and tile shapes) of an autotune result."""
+    return {k: tune[k] for k in ("translations", "p2p_warps", "p2p_chunk", "m2l_stages")}
 
 
 def sync_check(stream=None) -> None:
@@ -407,4 +429,4 @@ def version() -> str:
     return _lib.load().imq_version().decode()
 
 
-__all__ = ["Plan", "EvalPlan", "BatchedPlan", "autotune", "sync_check", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]
+__all__ = ["Plan", "EvalPlan", "BatchedPlan", "autotune", "tiles_of", "sync_check", "dense_matvec", "dense_matvec_noalloc", "version", "ImqError", "F32", "F64"]

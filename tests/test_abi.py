@@ -93,7 +93,35 @@ def test_autotune_arguments_rejected_before_any_gpu_work(lib):
     assert L.imq_autotune(*args(cs=(ctypes.c_double * 1)(-1.0))) == 1
     assert L.imq_autotune(*args(offs=(ctypes.c_int64 * 2)(0, 0))) == 1
     assert L.imq_autotune(*args(pts=None)) == 1
-    assert ctypes.sizeof(_lib.TuneResult) == 32 + 64 * 24   # the C struct (sizeof checked with gcc)
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Every struct of include/imq.h has the size and field offsets of its ctypes mirror
+    (a C program compiled with gcc prints them)."""
+    import subprocess
+    from paper_2205_04194_gb300 import _lib
+    mirrors = {"imq_options": _lib.ImqOptions, "imq_cg_options": _lib.CgOptions, "imq_cg_info": _lib.CgInfo,
+               "imq_tune_entry": _lib.TuneEntry, "imq_tune_result": _lib.TuneResult,
+               "imq_plan_info": _lib.PlanInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "imq.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
 
 
 def test_treecode_options_checked_before_any_gpu_work(lib):

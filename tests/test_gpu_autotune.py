@@ -1,4 +1,4 @@
-"""imq_autotune: the measured choice of (p, leaf).
+"""imq_autotune: the measured choice of (p, leaf), the translation precision and the tile shapes.
 
 The autotuner's test vectors are SplitMix64 values (Steele, Lea and Flood,
 OOPSLA 2014), re-generated here from that published definition, so every
@@ -36,6 +36,12 @@ def _imq():
     return imq
 
 
+def _phase1(res, translations="fp32"):
+    """Entries of the (p, leaf) search: default tile shapes."""
+    return [t for t in res["tried"] if t["translations"] == translations and t["p2p_warps"] == 0
+            and t["p2p_chunk"] == 0 and t["m2l_stages"] == 0]
+
+
 def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
     import torch
     imq = _imq()
@@ -45,23 +51,33 @@ def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
     res = imq.autotune(cuda(pts), c, target, p_candidates=(4, 6, 8, 10, 12, 14), leaf_candidates=(32, 64))
     assert res["met"] and res["rel_err"] <= target, res
     assert res["sampled_rows"] == 2048
+    # FP32 translations meet the target here, so no FP64 configuration is tried
+    assert res["translations"] == "fp32" and not _phase1(res, "fp64")
     v = splitmix_pm1(pts.shape[0])
     rows = _rows(pts.shape[0], 2048)
     exact = dense.matvec_rows(pts, c, v.astype(np.float64), rows)
     for leaf in (32, 64):
-        tried = [t for t in res["tried"] if t["leaf"] == leaf]
+        tried = [t for t in _phase1(res) if t["leaf"] == leaf]
         ps = [t["p"] for t in tried]
         assert ps == sorted(ps) and ps[0] == 4
         # ascending p until the first that meets the target
         assert all(t["rel_err"] > target for t in tried[:-1]) and tried[-1]["rel_err"] <= target
-        for t in tried:
-            plan = imq.Plan(cuda(pts), c, t["p"], leaf)
-            b = host(plan.matvec(cuda(v, torch.float32)))
-            err = np.linalg.norm(b[rows] - exact) / np.linalg.norm(exact)
-            assert err == pytest.approx(t["rel_err"], rel=1e-3), (t, err)
-            plan.close()
-    chosen = [t for t in res["tried"] if t["p"] == res["p"] and t["leaf"] == res["leaf"]]
-    assert chosen and all(chosen[0]["matvec_ms"] <= t["matvec_ms"] for t in res["tried"] if t["rel_err"] <= target)
+    # every measured configuration, tile shapes included, reproduced against the oracle rows
+    for t in res["tried"]:
+        plan = imq.Plan(cuda(pts), c, t["p"], t["leaf"], **imq.tiles_of(t))
+        b = host(plan.matvec(cuda(v, torch.float32)))
+        err = np.linalg.norm(b[rows] - exact) / np.linalg.norm(exact)
+        assert err == pytest.approx(t["rel_err"], rel=1e-3), (t, err)
+        plan.close()
+    # the tile sweep ran on the (p, leaf) choice: 9 P2P shapes, then the M2L pipeline depths
+    tiles = [t for t in res["tried"] if t not in _phase1(res)]
+    assert len([t for t in tiles if t["m2l_stages"] == 0]) == 9
+    assert all(t["p"] == res["p"] and t["leaf"] == res["leaf"] for t in tiles)
+    # the result is the fastest measured configuration of that choice that meets the target
+    same = [t for t in res["tried"] if t["p"] == res["p"] and t["leaf"] == res["leaf"] and t["rel_err"] <= target]
+    assert res["matvec_ms"] == min(t["matvec_ms"] for t in same)
+    best1 = min((t for t in _phase1(res) if t["rel_err"] <= target), key=lambda t: t["matvec_ms"])
+    assert (best1["p"], best1["leaf"]) == (res["p"], res["leaf"])
 
 
 def test_batched_choice_meets_the_target_on_every_problem():
@@ -78,7 +94,8 @@ def test_batched_choice_meets_the_target_on_every_problem():
     assert res["sampled_rows"] == 32 * len(sizes)
     n = sum(sizes)
     v = splitmix_pm1(nrhs * n).reshape(nrhs, n)
-    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, res["p"], res["leaf"], domain=(0.0, 0.0, 1.0))
+    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, res["p"], res["leaf"], domain=(0.0, 0.0, 1.0),
+                         **imq.tiles_of(res))
     b = host(bp.matvec(cuda(v, torch.float32)))
     worst = 0.0
     offs = np.concatenate([[0], np.cumsum(sizes)])

@@ -32,10 +32,10 @@ def test_cg_unpreconditioned_fp32_operator():
     imq = _imq()
     pts, c, f = _well_conditioned()
     plan = imq.Plan(cuda(pts), c, 12, 32)
-    coef, info = plan.solve(cuda(f), rtol=1e-6, maxit=20000, precond="none")
+    coef, info = plan.solve(cuda(f), rtol=1e-6, maxit=20000, precond="none", residual="dense")
     assert info["status"] == "IMQ_OK", info
     x = host(coef)
-    assert OS.true_relres(pts, c, x, f) < 2e-6
+    assert OS.true_relres(pts, c, x, f) <= 1e-6
     assert info["max_rel_residual"] <= 1e-6
 
 
@@ -44,10 +44,11 @@ def test_schwarz_pcg_needs_far_fewer_iterations():
     pts, c, f = _well_conditioned()
     plan = imq.Plan(cuda(pts), c, 12, 32)
     _, i0 = plan.solve(cuda(f), rtol=1e-6, maxit=20000, precond="none")
-    coef, i1 = plan.solve(cuda(f), rtol=1e-6, maxit=20000, precond="schwarz", schwarz_nmax=128)
+    coef, i1 = plan.solve(cuda(f), rtol=1e-6, maxit=20000, precond="schwarz", schwarz_nmax=128,
+                          residual="dense")
     assert i1["status"] == "IMQ_OK", i1
     assert i1["iterations"] * 5 < i0["iterations"]
-    assert OS.true_relres(pts, c, host(coef), f) < 2e-6
+    assert OS.true_relres(pts, c, host(coef), f) <= 1e-6
 
 
 def test_plain_2k_fp64_to_1e10():
@@ -57,7 +58,7 @@ def test_plain_2k_fp64_to_1e10():
     coef, info = plan.solve(cuda(wl.f), rtol=1e-10, maxit=3000, precond="schwarz", schwarz_nmax=160,
                             schwarz_fp64=True, operator="dense_f64", residual="dense")
     assert info["status"] == "IMQ_OK", info
-    assert OS.true_relres(wl.points, wl.c, host(coef), wl.f) < 1.5e-10
+    assert OS.true_relres(wl.points, wl.c, host(coef), wl.f) <= 1e-10
 
 
 def test_refinement_fp32_inner_fp64_residual():
@@ -69,7 +70,7 @@ def test_refinement_fp32_inner_fp64_residual():
                             inner_rtol=1e-5, residual="dense")
     assert info["status"] == "IMQ_OK", info
     assert info["outer_steps"] >= 2
-    assert OS.true_relres(pts, c, host(coef), f) < 1.5e-8
+    assert OS.true_relres(pts, c, host(coef), f) <= 1e-8
 
 
 def test_not_converged_returns_best_iterate_and_info():
@@ -95,7 +96,7 @@ def test_multiple_rhs_host_buffers_and_determinism():
     assert ia["status"] == "IMQ_OK" and isinstance(a, np.ndarray), ia
     assert np.array_equal(a, host(b))                        # bit-reproducible
     for r in range(2):
-        assert OS.true_relres(pts, c, a[r], F[r]) < 2e-7
+        assert OS.true_relres(pts, c, a[r], F[r]) <= 1e-7
 
 
 def test_flat_shape_breakdown_returns_best_iterate():

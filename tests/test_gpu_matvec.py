@@ -177,19 +177,26 @@ def test_fast_full_size_uniform_100k_sampled_rows():
 
 
 def test_batched_256_full_size_sampled_rows():
-    """All 256 problems (3.7M points) in one batched plan at the bench's autotuned (p, leaf),
-    4 right-hand sides; 64 sampled rows of 16 problems against the FP64 oracle.  The
-    Franke data (positive, no cancellation) meets 1e-6; the trig sums cancel, so FP32
-    rounding of the sums leaves them near 1e-6 and they are held to 2e-6."""
+    """All 256 problems (3.7M points) in one batched plan at p = 14, leaf 128, 4 right-hand
+    sides; 64 sampled rows of 16 problems against the FP64 oracle, 1e-6 for every
+    right-hand side.  The trig sums cancel in the far field (c up to 0.2, several sign
+    changes over the square), so the FP32 rounding of the translated coefficients is above
+    1e-6 there: the plan translates in FP64 (P2M, P2P, M2P and L2P stay FP32).  With FP32
+    translations the Franke data (no cancellation) still meet 1e-6."""
     import torch
     imq = _imq()
     probs = W.batched_256()
     pts = [cuda(x) for x, _, _ in probs]
     cs = [c for _, c, _ in probs]
     f = np.concatenate([r for _, _, r in probs], axis=1)
-    bp = imq.BatchedPlan(pts, cs, 14, 128, domain=(0.0, 0.0, 1.0))
-    b = host(bp.matvec(cuda(f, torch.float32)))
-    offs = bp.offsets
+    d_f = cuda(f, torch.float32)
+    bp = imq.BatchedPlan(pts, cs, 14, 128, domain=(0.0, 0.0, 1.0), translations="fp64")
+    b = host(bp.matvec(d_f))
+    bp.close()
+    b32 = imq.BatchedPlan(pts, cs, 14, 128, domain=(0.0, 0.0, 1.0))
+    bf = host(b32.matvec(d_f))
+    offs = b32.offsets
+    b32.close()
     g = np.random.default_rng(3)
     for q in np.linspace(0, len(probs) - 1, 16).astype(int):
         x, c, rhs = probs[q]
@@ -197,5 +204,28 @@ def test_batched_256_full_size_sampled_rows():
         for r in range(4):
             ref = dense.matvec_rows(x, c, rhs[r], rows)
             got = b[r, offs[q]:offs[q + 1]][rows]
-            assert rel2(got, ref) < (1e-6 if r == 0 else 2e-6), (q, r, rel2(got, ref))
-    bp.close()
+            assert rel2(got, ref) <= 1e-6, (q, r, rel2(got, ref))
+        ref = dense.matvec_rows(x, c, rhs[0], rows)
+        assert rel2(bf[0, offs[q]:offs[q + 1]][rows], ref) <= 1e-6, q
+
+
+def test_fp64_translations_remove_the_fp32_cancellation_floor():
+    """One of the batched workload's largest problems (N = 46,994, c = 0.18) with a trig-sum
+    vector: the FP32 product stays above 1e-6, the same plan with FP64 translations meets it,
+    and both agree with the all-FP64 product to their own error."""
+    import torch
+    imq = _imq()
+    x, c, rhs = W.batched_256()[14]
+    rows = np.random.default_rng(5).choice(x.shape[0], 512, replace=False)
+    v = rhs[3]
+    ref = dense.matvec_rows(x, c, v, rows)
+    p32 = imq.Plan(cuda(x), c, 14, 128, domain=(0.0, 0.0, 1.0))
+    p64t = imq.Plan(cuda(x), c, 14, 128, domain=(0.0, 0.0, 1.0), translations="fp64")
+    e32 = rel2(host(p32.matvec(cuda(v, torch.float32)))[rows], ref)
+    e64t = rel2(host(p64t.matvec(cuda(v, torch.float32)))[rows], ref)
+    e64 = rel2(host(p32.matvec(cuda(v)))[rows], ref)
+    assert e64 < 1e-7
+    assert e64t <= 1e-6 < e32, (e64t, e32)
+    assert e64t < 0.5 * e32
+    p32.close()
+    p64t.close()
