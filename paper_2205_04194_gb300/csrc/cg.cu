@@ -188,16 +188,18 @@ __global__ void __launch_bounds__(kRedThreads) k_finish_beta(const double *__res
     }
 }
 
-__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ z, int64_t n, CGScalars *S) {
+// p = z + beta p; also u = (float) p, the next product's input (u may be null), and
+// rz = rz_new (one thread; the other blocks read only beta)
+__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ z, float *__restrict__ u, int64_t n,
+                           CGScalars *S) {
     if (S->done) return;
     const double bt = S->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = z[i] + bt * p[i];
-}
-
-__global__ void k_commit(CGScalars *S) {
-    if (S->done) return;
-    S->rz = S->rz_new;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double pi = z[i] + bt * p[i];
+        p[i] = pi;
+        if (u) u[i] = (float)pi;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->rz = S->rz_new;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_sum_to(const double *__restrict__ part, double *out) {
@@ -231,8 +233,15 @@ __global__ void k_scatter_f64(const double *__restrict__ v, const int32_t *__res
 // Factor one patch: A_b + shift*I assembled in FP32 from FP64 coordinate
 // differences, right-looking Cholesky in shared memory; pivots below
 // dmin are raised to dmin (the patch matrices of flat shapes are numerically
-// singular).  Output: n x n column-major lower factor.
-template <class T>
+// singular).  Output (INV = false): the n x n column-major lower factor L.
+// INV = true: the explicit inverse (A_b + shift I)^{-1} = L^{-T} L^{-1}, so that
+// the apply is one dense matrix-vector product per patch (bandwidth-bound)
+// instead of two sequential triangular solves (latency-bound).  L^{-1} is
+// formed column by column (thread t solves L y = e_t) in a second shared
+// buffer Y, row-major with a padded stride (Y[k][t] at k * (n + 1) + t), then
+// the inverse by 4 x 4 register tiles of Y^T Y on and below the diagonal,
+// mirrored.
+template <class T, bool INV>
 __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
                                  const int64_t *__restrict__ foff, const double2 *__restrict__ pos,
                                  const int32_t *__restrict__ leaves, ShapeC shape, double shift_rel,
@@ -275,9 +284,56 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
         __syncthreads();
     }
     T *F = factor + foff[b];
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int j = e / n, i = e - j * n;
-        F[e] = i >= j ? A[e] : (T)0;
+    if constexpr (!INV) {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int j = e / n, i = e - j * n;
+            F[e] = i >= j ? A[e] : (T)0;
+        }
+    } else {
+        const int n4 = (n + 3) & ~3, ld = n4 + 1;
+        T *Y = A + (size_t)n * n;   // [n4][ld], rows k >= n and columns t >= n stay zero
+        for (int e = threadIdx.x; e < n4 * ld; e += blockDim.x) Y[e] = (T)0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {   // column t of L^{-1}
+            for (int i = t; i < n; ++i) {
+                T sum = i == t ? (T)1 : (T)0;
+                for (int k = t; k < i; ++k) sum -= A[(size_t)k * n + i] * Y[(size_t)k * ld + t];
+                Y[(size_t)i * ld + t] = sum / A[(size_t)i * n + i];
+            }
+        }
+        __syncthreads();
+        const int nt = n4 / 4, ntiles = nt * (nt + 1) / 2;
+        for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
+            int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);   // tile = ti (ti + 1) / 2 + tj, tj <= ti
+            while (ti * (ti + 1) / 2 > tile) --ti;
+            while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+            const int tj = tile - ti * (ti + 1) / 2;
+            const int i0 = 4 * ti, j0 = 4 * tj;
+            T acc[4][4] = {};
+            for (int k = i0; k < n4; ++k) {   // Y[k][i] = 0 for k < i, and i0 >= j0
+                const T *yk = Y + (size_t)k * ld;
+                T a[4], bb[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = yk[i0 + q];
+                    bb[q] = yk[j0 + q];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * bb[r];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int i = i0 + q, j = j0 + r;
+                    if (i < n && j < n) {
+                        F[(size_t)j * n + i] = acc[q][r];
+                        F[(size_t)i * n + j] = acc[q][r];
+                    }
+                }
+        }
     }
 }
 
@@ -333,6 +389,51 @@ __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, co
     for (int t = 0; t < kSchwarzRowsPerLane; ++t) {
         const int i = lane + 32 * t;
         if (i < n) ypatch[o + i] = (double)v[t];
+    }
+}
+
+// One warp per patch: y = Ainv r_patch with the explicit FP32 inverse (column-major
+// n x n, n <= 32 * kInvRowsPerLane); r_j is broadcast from the lane holding it, and
+// lane l accumulates rows l, l + 32, ... (coalesced column reads).
+constexpr int kInvRowsPerLane = 5;   // patches up to 160 points
+__global__ void __launch_bounds__(128) k_schwarz_inv_apply(int npatch, const int32_t *__restrict__ poff,
+                                                           const int32_t *__restrict__ ppts,
+                                                           const int64_t *__restrict__ foff,
+                                                           const float *__restrict__ inv, const double *__restrict__ r,
+                                                           double *__restrict__ ypatch, const CGScalars *S) {
+    if (S && S->done) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= npatch) return;
+    const int o = poff[warp], n = poff[warp + 1] - o;
+    const float *Ai = inv + foff[warp];
+    float rv[kInvRowsPerLane], acc[kInvRowsPerLane];
+#pragma unroll
+    for (int t = 0; t < kInvRowsPerLane; ++t) {
+        const int i = lane + 32 * t;
+        rv[t] = i < n ? (float)r[ppts[o + i]] : 0.f;
+        acc[t] = 0.f;
+    }
+#pragma unroll
+    for (int jt = 0; jt < kInvRowsPerLane; ++jt) {
+        if (32 * jt >= n) break;
+        const int jn = min(32, n - 32 * jt);
+        const float *col0 = Ai + (size_t)(32 * jt) * n;
+#pragma unroll 4
+        for (int jl = 0; jl < jn; ++jl) {
+            const float rj = __shfl_sync(0xFFFFFFFFu, rv[jt], jl);
+            const float *col = col0 + (size_t)jl * n;
+#pragma unroll
+            for (int t = 0; t < kInvRowsPerLane; ++t) {
+                const int i = lane + 32 * t;
+                if (i < n) acc[t] = fmaf(__ldg(col + i), rj, acc[t]);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kInvRowsPerLane; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) ypatch[o + i] = (double)acc[t];
     }
 }
 
@@ -417,19 +518,23 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     Z.ypatch.alloc(sizeof(double) * std::max<int64_t>(1, Z.total_slots));
     AsyncMem ncl(sizeof(int), s);
     IMQ_CUDA(cudaMemsetAsync(ncl.ptr, 0, sizeof(int), s));
-    const size_t smem = es * (size_t)maxn * maxn;
+    // FP32 patches of at most 32 * kInvRowsPerLane points are applied through their explicit inverse
+    Z.inverse = !fp64 && maxn <= 32 * kInvRowsPerLane;
+    const int n4 = (maxn + 3) & ~3;
+    const size_t smem = es * (size_t)maxn * maxn + (Z.inverse ? es * (size_t)n4 * (n4 + 1) : 0);
     if (fp64) {
-        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_schwarz_factor<double><<<Z.npatch, 256, smem, s>>>(
+        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        k_schwarz_factor<double, false><<<Z.npatch, 256, smem, s>>>(
             Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
             P.pos.as<double2>(), P.leaves.as<int32_t>(), P.shape(), shift, 1e-14, Z.factor.as<double>(),
             ncl.as<int>());
     } else {
-        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_schwarz_factor<float><<<Z.npatch, 256, smem, s>>>(
-            Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
-            P.pos.as<double2>(), P.leaves.as<int32_t>(), P.shape(), shift, 1e-6, Z.factor.as<float>(),
-            ncl.as<int>());
+        auto kern = Z.inverse ? k_schwarz_factor<float, true> : k_schwarz_factor<float, false>;
+        IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<Z.npatch, 256, smem, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
+                                         Z.fac_off.as<int64_t>(), P.pos.as<double2>(), P.leaves.as<int32_t>(),
+                                         P.shape(), shift, 1e-6, Z.factor.as<float>(), ncl.as<int>());
     }
     IMQ_LAUNCH_CHECK();
     IMQ_CUDA(cudaStreamSynchronize(s));
@@ -445,7 +550,11 @@ void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, 
                    cudaStream_t s) {
     const CGScalars *S = static_cast<const CGScalars *>(Sv);
     const unsigned g = blocks_for((int64_t)Z.npatch * 32, 128);
-    if (Z.fp64)
+    if (Z.inverse)
+        k_schwarz_inv_apply<<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
+                                              Z.fac_off.as<int64_t>(), Z.factor.as<float>(), r, Z.ypatch.as<double>(),
+                                              S);
+    else if (Z.fp64)
         k_schwarz_solve<double><<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
                                                   Z.fac_off.as<int64_t>(), Z.factor.as<double>(), r,
                                                   Z.ypatch.as<double>(), S);
@@ -542,8 +651,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
     GraphCapture cap;
     cudaStream_t cs = cap.begin();
     for (int it = 0; it < kIterPerGraph; ++it) {
-        if (op == IMQ_OPERATOR_FAST_F32) {
-            k_p_to_f32<<<gr, kRedThreads, 0, cs>>>(p, w.u32.as<float>(), n, S);
+        if (op == IMQ_OPERATOR_FAST_F32) {   // u32 = (float) p, written by the previous k_update_p
             fmm_apply<float>(P, w.u32.as<float>(), w.b32.as<float>(), 1, cs);
             k_q_dot<<<gr, kRedThreads, 0, cs>>>(w.b32.as<float>(), p, q, n, w.part.as<double>(), S);
         } else {
@@ -562,8 +670,8 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         } else {
             k_finish_beta<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S, 1);
         }
-        k_update_p<<<gr, kRedThreads, 0, cs>>>(p, z, n, S);
-        k_commit<<<1, 1, 0, cs>>>(S);
+        k_update_p<<<gr, kRedThreads, 0, cs>>>(p, z, op == IMQ_OPERATOR_FAST_F32 ? w.u32.as<float>() : nullptr, n,
+                                               S);
     }
     cudaGraphExec_t exec = cap.instantiate();
     const auto t0 = std::chrono::steady_clock::now();
@@ -636,6 +744,10 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                 if (!(h.rz > 0)) break;   // the preconditioner is not positive on r: keep x
                 IMQ_CUDA(cudaMemcpyAsync(p, z, 8 * n, cudaMemcpyDeviceToDevice, s));
                 IMQ_CUDA(cudaMemcpyAsync(S, &h, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+                if (op == IMQ_OPERATOR_FAST_F32) {   // the first product's input; the graph writes the rest
+                    k_p_to_f32<<<gr, kRedThreads, 0, s>>>(p, w.u32.as<float>(), n, S);
+                    IMQ_LAUNCH_CHECK();
+                }
                 CGScalars hs{};
                 for (;;) {
                     IMQ_CUDA(cudaGraphLaunch(exec, s));

@@ -148,8 +148,9 @@ struct Schwarz {
     DevMem patch_off;    // int32[npatch+1] offsets into patch_pts
     DevMem patch_pts;    // int32[] sorted point indices of each patch
     DevMem fac_off;      // int64[npatch] offset of each patch's n*n factor
-    DevMem factor;       // float[] or double[] column-major Cholesky factors
+    DevMem factor;       // float[] or double[] column-major Cholesky factors (or explicit inverses)
     bool fp64 = false;
+    bool inverse = false; // factor holds each patch's explicit inverse (FP32, n <= 160)
     DevMem pt_off;       // int32[N+1] reverse map: point -> patch slots
     DevMem pt_slot;      // int32[] patch slot (patch_off[b] + local index)
     DevMem ypatch;       // double[total slots] per-patch solutions
