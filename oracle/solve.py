@@ -13,6 +13,8 @@ solver to future work (Section 4).  The oracle therefore offers:
 * ``schwarz``: the symmetric additive Schwarz preconditioner
   z = sum_b R_b^T (A_{N(b)} + delta I)^{-1} R_b r, where N(b) is the set of
   points of leaf b and of the leaves adjacent to it (its U list);
+* ``two_level``: ``schwarz`` plus a Galerkin coarse space of leaf indicators,
+  in the balancing form z = (I - QA) M1 (I - AQ) r + Q r, Q = Z (Z^T A Z)^{-1} Z^T;
 * ``true_relres``: ||f - A coef||_2 / ||f||_2 with the dense FP64 product.
 """
 from __future__ import annotations
@@ -83,3 +85,61 @@ def schwarz(points, c: float, leaf: int, delta: float = 0.0, domain=None, tree=N
         return z
 
     return apply
+
+
+def two_level(points, c: float, leaf: int, coarse_leaf: int | None = None, delta: float = 1e-9, domain=None):
+    """Two-level additive Schwarz in its balancing (deflated) form; returns (r -> z, Z, E).
+
+    The paper leaves the preconditioner to future work (Section 4) and names
+    preconditioned iterative solvers (Section 1, Beatson et al.).  The one-level
+    method is ``schwarz``: local solves on leaf neighbourhood patches.  The
+    second level adds a Galerkin coarse space: Z holds the indicator vector of
+    every leaf of the tree with ``coarse_leaf`` points per leaf (default: the
+    fine leaves), E = Z^T A Z, Q = Z E^{-1} Z^T, and
+
+        z = (I - Q A) M1 (I - A Q) r + Q r
+
+    with M1 the one-level operator.  This is symmetric, and exact on the
+    coarse space (z = Z y whenever r = A Z y).  Patch and coarse matrices are
+    inverted through their eigendecomposition with eigenvalues clamped below
+    at ``delta`` (relative to 1/c for the patches, to the largest eigenvalue for
+    E), because both are numerically singular for flat shapes.
+    """
+    pts = np.asarray(points, dtype=np.float64)
+    n = pts.shape[0]
+    t = build_tree(pts, leaf, domain)
+    A = dense.assemble(pts, c)
+    patches = []
+    for b in range(t.nbox):
+        if not t.is_leaf[b] or t.end[b] == t.begin[b]:
+            continue
+        idx = np.concatenate([t.perm[int(t.begin[s]):int(t.end[s])] for s in t.U[b]])
+        w, V = np.linalg.eigh(A[np.ix_(idx, idx)])
+        patches.append((idx, np.maximum(w, delta / c), V))
+    tc = t if coarse_leaf is None else build_tree(pts, coarse_leaf, domain)
+    cols = []
+    for b in range(tc.nbox):
+        if tc.is_leaf[b] and tc.end[b] > tc.begin[b]:
+            v = np.zeros(n)
+            v[tc.perm[int(tc.begin[b]):int(tc.end[b])]] = 1.0
+            cols.append(v)
+    Z = np.stack(cols, axis=1)
+    E = Z.T @ (A @ Z)
+    we, Ve = np.linalg.eigh(E)
+    we = np.maximum(we, delta * we.max())
+
+    def M1(r):
+        z = np.zeros_like(r)
+        for idx, w, V in patches:
+            z[idx] += V @ ((V.T @ r[idx]) / w)
+        return z
+
+    def Q(r):
+        return Z @ (Ve @ ((Ve.T @ (Z.T @ r)) / we))
+
+    def apply(r):
+        y = Q(r)
+        z = M1(r - A @ y)
+        return z - Q(A @ z) + y
+
+    return apply, Z, E
