@@ -269,7 +269,17 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
  *   maxit / refine_steps), IMQ_NUMERICAL (NaN/Inf or breakdown), IMQ_OOM,
  *   IMQ_CUDA_ERROR.
  * ------------------------------------------------------------------------- */
-typedef enum imq_precond { IMQ_PRECOND_NONE = 0, IMQ_PRECOND_SCHWARZ = 1 } imq_precond;
+/* Preconditioners.  SCHWARZ: symmetric additive Schwarz over leaf neighbourhood
+ * patches (each patch factored once, FP32 patches applied through their
+ * explicit inverse).  SCHWARZ_2L: the same plus a Galerkin coarse space, one
+ * indicator vector per coarse box (the largest tree boxes holding at most
+ * coarse_points points), E = Z^T A Z assembled exactly over every pair and
+ * inverted in FP64 once; applied in the deflated form z = y + Q (r - A y),
+ * y the patch solves, Q = Z E^{-1} Z^T, each inner pass started from Q r.
+ * One extra FP32 fast product per iteration; single plans only, at most
+ * 16384 coarse boxes.  (Section 4 leaves the preconditioner to future work;
+ * Section 1 cites preconditioned iterations.) */
+typedef enum imq_precond { IMQ_PRECOND_NONE = 0, IMQ_PRECOND_SCHWARZ = 1, IMQ_PRECOND_SCHWARZ_2L = 2 } imq_precond;
 typedef enum imq_operator {
     IMQ_OPERATOR_FAST_F32 = 0,   /* inner iterations on the FP32 fast product (default)   */
     IMQ_OPERATOR_FAST_F64 = 1,   /* inner iterations on the FP64 fast product              */
@@ -295,7 +305,10 @@ typedef struct imq_cg_options {
     imq_plan_t residual_plan;/* optional plan on the same points (e.g. larger p), or NULL      */
     int32_t inner_operator;  /* imq_operator                                                   */
     int32_t schwarz_fp64;    /* 1: factor and apply the Schwarz patches in FP64 (nmax <= 160)   */
-    int32_t reserved[6];
+    int32_t coarse_points;   /* SCHWARZ_2L: max points per coarse box, 1..1024 (0: the leaf size) */
+    int32_t coarse_gram;     /* SCHWARZ_2L: pairs of E = Z^T A Z in 0: FP64 if N^2 <= 4e10, else
+                                FP32 with FP64 partial sums; 1: FP64; 2: FP32                   */
+    int32_t reserved[4];
 } imq_cg_options;
 
 typedef struct imq_cg_info {

@@ -529,14 +529,17 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         imq_cg_options o;
         imq_cg_default_options(&o);
         if (opt) {
-            if (opt->struct_size < (int)offsetof(imq_cg_options, reserved))
+            if (opt->struct_size < (int)offsetof(imq_cg_options, coarse_points))
                 fail(IMQ_INVALID_ARG, "imq_cg_solve: imq_cg_options.struct_size too small");
             std::memcpy(&o, opt, std::min(sizeof(o), (size_t)opt->struct_size));
         }
         if (!(o.rtol > 0) || !std::isfinite(o.rtol)) fail(IMQ_INVALID_ARG, "imq_cg_solve: rtol must be > 0");
         if (o.maxit < 1) fail(IMQ_INVALID_ARG, "imq_cg_solve: maxit must be >= 1");
-        if (o.precond != IMQ_PRECOND_NONE && o.precond != IMQ_PRECOND_SCHWARZ)
+        if (o.precond != IMQ_PRECOND_NONE && o.precond != IMQ_PRECOND_SCHWARZ && o.precond != IMQ_PRECOND_SCHWARZ_2L)
             fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown preconditioner");
+        if (o.coarse_points < 0 || o.coarse_points > 1024)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: coarse_points must be in [0, 1024]");
+        if (o.coarse_gram < 0 || o.coarse_gram > 2) fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown coarse_gram");
         if (o.schwarz_nmax < 0 || o.schwarz_nmax > 224) fail(IMQ_INVALID_ARG, "imq_cg_solve: schwarz_nmax must be in [0, 224]");
         if (o.inner_operator < IMQ_OPERATOR_FAST_F32 || o.inner_operator > IMQ_OPERATOR_DENSE_F64)
             fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown inner operator");
@@ -555,6 +558,8 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         DevOut dx(coef, bytes, s);
         if (o.x0_given && dx.tmp) IMQ_CUDA(cudaMemcpyAsync(dx.ptr, coef, bytes, cudaMemcpyHostToDevice, s));
         try {
+            if (!P.prob_off.empty() && o.precond == IMQ_PRECOND_SCHWARZ_2L)
+                fail(IMQ_UNSUPPORTED, "imq_cg_solve: the two-level preconditioner is built for single plans");
             if (!P.prob_off.empty())
                 cg_solve_batched(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o,
                                  info, rel_out, iters_out, s);

@@ -71,7 +71,7 @@ __device__ __forceinline__ double final_sum(const double *part) {
 
 __global__ void __launch_bounds__(kRedThreads) k_p_to_f32(const double *__restrict__ p, float *__restrict__ u,
                                                           int64_t n, const CGScalars *S) {
-    if (S->done) return;
+    if (S && S->done) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         u[i] = (float)p[i];
 }
@@ -212,6 +212,18 @@ __global__ void k_axpby(double *__restrict__ y, const double *__restrict__ x, do
         y[i] = a * x[i] + b * y[i];
 }
 
+// r -= (double) b
+__global__ void k_sub_f32(double *__restrict__ r, const float *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] -= (double)b[i];
+}
+
+// r -= b
+__global__ void k_sub_f64(double *__restrict__ r, const double *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] -= b[i];
+}
+
 __global__ void k_sub(double *__restrict__ r, const double *__restrict__ f, const double *__restrict__ ax, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         r[i] = f[i] - ax[i];
@@ -248,91 +260,116 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
                                  double dmin_rel, T *__restrict__ factor, int *nclamped) {
     extern __shared__ __align__(16) unsigned char smraw_f[];
     T *A = reinterpret_cast<T *>(smraw_f);   // n x n, column-major
+    __shared__ int s_bad;
     const int b = blockIdx.x;
     if (b >= npatch) return;
     const int o = poff[b], n = poff[b + 1] - o;
     const double cb = shape.of(leaves[b]);
-    const T c2 = (T)(cb * cb), shift = (T)(shift_rel / cb), dmin = (T)(dmin_rel / cb);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int j = e / n, i = e - j * n;   // column j, row i
-        const double2 pi = pos[ppts[o + i]], pj = pos[ppts[o + j]];
-        const T dx = (T)(pi.x - pj.x), dy = (T)(pi.y - pj.y);
-        T a = (T)1 / sqrt(dx * dx + dy * dy + c2);
-        if (i == j) a += shift;
-        A[e] = a;
-    }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        if (threadIdx.x == 0) {
-            T d = A[k * n + k];
-            if (!(d > dmin)) {
-                d = dmin;
-                atomicAdd(nclamped, 1);
-            }
-            A[k * n + k] = sqrt(d);
-        }
-        __syncthreads();
-        const T piv = A[k * n + k];
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[k * n + i] /= piv;
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            const int jj = e / m, ii = e - jj * m;
-            const int j = k + 1 + jj, i = k + 1 + ii;
-            if (i >= j) A[j * n + i] -= A[k * n + i] * A[k * n + j];
-        }
-        __syncthreads();
-    }
+    const T c2 = (T)(cb * cb), shift = (T)(shift_rel / cb);
     T *F = factor + foff[b];
-    if constexpr (!INV) {
+    // INV: an inverse that overflows (pivots at the clamp, L^{-1} growing beyond the FP32
+    // range) is recomputed with the clamp raised 1000-fold, up to three times
+    for (int attempt = 0; attempt < (INV ? 4 : 1); ++attempt) {
+        const T dmin = (T)(dmin_rel / cb * pow(1e3, (double)attempt));
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int j = e / n, i = e - j * n;
-            F[e] = i >= j ? A[e] : (T)0;
+            const int j = e / n, i = e - j * n;   // column j, row i
+            const double2 pi = pos[ppts[o + i]], pj = pos[ppts[o + j]];
+            const T dx = (T)(pi.x - pj.x), dy = (T)(pi.y - pj.y);
+            T a = (T)1 / sqrt(dx * dx + dy * dy + c2);
+            if (i == j) a += shift;
+            A[e] = a;
         }
-    } else {
-        const int n4 = (n + 3) & ~3, ld = n4 + 1;
-        T *Y = A + (size_t)n * n;   // [n4][ld], rows k >= n and columns t >= n stay zero
-        for (int e = threadIdx.x; e < n4 * ld; e += blockDim.x) Y[e] = (T)0;
+        if (threadIdx.x == 0) s_bad = 0;
         __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {   // column t of L^{-1}
-            for (int i = t; i < n; ++i) {
-                T sum = i == t ? (T)1 : (T)0;
-                for (int k = t; k < i; ++k) sum -= A[(size_t)k * n + i] * Y[(size_t)k * ld + t];
-                Y[(size_t)i * ld + t] = sum / A[(size_t)i * n + i];
-            }
-        }
-        __syncthreads();
-        const int nt = n4 / 4, ntiles = nt * (nt + 1) / 2;
-        for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
-            int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);   // tile = ti (ti + 1) / 2 + tj, tj <= ti
-            while (ti * (ti + 1) / 2 > tile) --ti;
-            while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-            const int tj = tile - ti * (ti + 1) / 2;
-            const int i0 = 4 * ti, j0 = 4 * tj;
-            T acc[4][4] = {};
-            for (int k = i0; k < n4; ++k) {   // Y[k][i] = 0 for k < i, and i0 >= j0
-                const T *yk = Y + (size_t)k * ld;
-                T a[4], bb[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = yk[i0 + q];
-                    bb[q] = yk[j0 + q];
+        for (int k = 0; k < n; ++k) {
+            if (threadIdx.x == 0) {
+                T d = A[k * n + k];
+                if (!(d > dmin)) {
+                    d = dmin;
+                    if (attempt == 0) atomicAdd(nclamped, 1);
                 }
+                A[k * n + k] = sqrt(d);
+            }
+            __syncthreads();
+            const T piv = A[k * n + k];
+            for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[k * n + i] /= piv;
+            __syncthreads();
+            const int m = n - k - 1;
+            for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+                const int jj = e / m, ii = e - jj * m;
+                const int j = k + 1 + jj, i = k + 1 + ii;
+                if (i >= j) A[j * n + i] -= A[k * n + i] * A[k * n + j];
+            }
+            __syncthreads();
+        }
+        if constexpr (!INV) {
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                const int j = e / n, i = e - j * n;
+                F[e] = i >= j ? A[e] : (T)0;
+            }
+            return;
+        } else {
+            const int n4 = (n + 3) & ~3, ld = n4 + 1;
+            T *Y = A + (size_t)n * n;   // [n4][ld], rows k >= n and columns t >= n stay zero
+            for (int e = threadIdx.x; e < n4 * ld; e += blockDim.x) Y[e] = (T)0;
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {   // column t of L^{-1}
+                bool fin = true;
+                for (int i = t; i < n; ++i) {
+                    T sum = i == t ? (T)1 : (T)0;
+                    for (int k = t; k < i; ++k) sum -= A[(size_t)k * n + i] * Y[(size_t)k * ld + t];
+                    const T y = sum / A[(size_t)i * n + i];
+                    fin = fin && isfinite(y);
+                    Y[(size_t)i * ld + t] = y;
+                }
+                if (!fin) s_bad = 1;
+            }
+            __syncthreads();
+            if (s_bad) continue;
+            const int nt = n4 / 4, ntiles = nt * (nt + 1) / 2;
+            for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
+                int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);   // tile = ti (ti + 1) / 2 + tj, tj <= ti
+                while (ti * (ti + 1) / 2 > tile) --ti;
+                while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+                const int tj = tile - ti * (ti + 1) / 2;
+                const int i0 = 4 * ti, j0 = 4 * tj;
+                T acc[4][4] = {};
+                for (int k = i0; k < n4; ++k) {   // Y[k][i] = 0 for k < i, and i0 >= j0
+                    const T *yk = Y + (size_t)k * ld;
+                    T a[4], bb[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        a[q] = yk[i0 + q];
+                        bb[q] = yk[j0 + q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * bb[r];
+                }
+                bool fin = true;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * bb[r];
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int i = i0 + q, j = j0 + r;
-                    if (i < n && j < n) {
-                        F[(size_t)j * n + i] = acc[q][r];
-                        F[(size_t)i * n + j] = acc[q][r];
+                    for (int r = 0; r < 4; ++r) {
+                        const int i = i0 + q, j = j0 + r;
+                        fin = fin && isfinite(acc[q][r]);
+                        if (i < n && j < n) {
+                            F[(size_t)j * n + i] = acc[q][r];
+                            F[(size_t)i * n + j] = acc[q][r];
+                        }
                     }
-                }
+                if (!fin) s_bad = 1;
+            }
+            __syncthreads();
+            if (!s_bad) return;
+        }
+    }
+    // every attempt overflowed: the patch acts as the diagonal c I (as a point in no patch)
+    if constexpr (INV) {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int j = e / n, i = e - j * n;
+            F[e] = i == j ? (T)cb : (T)0;
         }
     }
 }
@@ -573,6 +610,7 @@ namespace {
 
 struct Work {
     DevMem x, xb, r, p, q, z, u32, b32, part, S, tmp;
+    DevMem u2, b2, q2;   // the two-level preconditioner's product (FP32 in / out, or FP64 out)
 };
 
 double read_dot(const double *a, const double *b, int64_t n, DevMem &part, DevMem &tmp, cudaStream_t s) {
@@ -625,18 +663,25 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
     ensure_ops(P, false, s);
     if (o.residual == IMQ_RESIDUAL_PLAN_F64) ensure_ops(RP ? *RP : P, true, s);
     if (o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);
-    if (o.precond == IMQ_PRECOND_SCHWARZ)
-        build_schwarz(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    const bool two_level = o.precond == IMQ_PRECOND_SCHWARZ_2L;
+    const bool pre = o.precond == IMQ_PRECOND_SCHWARZ || two_level;
+    if (pre) build_schwarz(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    if (two_level) coarse_setup(P, o.coarse_points > 0 ? o.coarse_points : P.leaf, o.coarse_gram, s);
     const Schwarz &Z = P.schwarz;
     Work w;
     w.x.alloc(8 * n); w.xb.alloc(8 * n); w.r.alloc(8 * n); w.p.alloc(8 * n); w.q.alloc(8 * n); w.z.alloc(8 * n);
     w.u32.alloc(4 * n); w.b32.alloc(4 * n); w.part.alloc(8 * kRedBlocks); w.S.alloc(sizeof(CGScalars));
     w.tmp.alloc(64);
+    if (two_level) {
+        w.u2.alloc(4 * n);
+        w.b2.alloc(4 * n);
+        w.q2.alloc(8 * n);
+    }
     DevMem xs, fs, rr_out, ax;
     xs.alloc(8 * n); fs.alloc(8 * n); ax.alloc(8 * n);
     CGScalars *S = w.S.as<CGScalars>();
     double *x = w.x.as<double>(), *r = w.r.as<double>(), *p = w.p.as<double>(), *q = w.q.as<double>();
-    double *z = o.precond == IMQ_PRECOND_SCHWARZ ? w.z.as<double>() : r;
+    double *z = pre ? w.z.as<double>() : r;
     const unsigned g = blocks_for(n, 256);
     const unsigned gr = kRedBlocks;
     // one product outside the capture sets kernel attributes and touches every buffer
@@ -646,6 +691,37 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
     if (op == IMQ_OPERATOR_FAST_F32) fmm_apply<float>(P, w.u32.as<float>(), w.b32.as<float>(), 1, s);
     else if (op == IMQ_OPERATOR_FAST_F64) fmm_apply<double>(P, p, q, 1, s);
     IMQ_CUDA(cudaStreamSynchronize(s));
+    // z = M r: the patch solves, and with the coarse level z += Q (r - A z); `done` (device,
+    // may be null) lets a converged solve skip the work inside the captured graph
+    const int *done_flag = reinterpret_cast<const int *>(reinterpret_cast<const char *>(S) + offsetof(CGScalars, done));
+    // the deflation's product A y uses the inner iterations' operator: y carries the patch
+    // solves' amplification, so a less accurate product would swamp r - A y
+    auto op_product = [&](const double *xin, cudaStream_t st, const CGScalars *Sd, const float **b32,
+                          const double **b64) {
+        *b32 = nullptr;
+        *b64 = nullptr;
+        if (op == IMQ_OPERATOR_FAST_F32) {
+            k_p_to_f32<<<gr, kRedThreads, 0, st>>>(xin, w.u2.as<float>(), n, Sd);
+            IMQ_LAUNCH_CHECK();
+            fmm_apply<float>(P, w.u2.as<float>(), w.b2.as<float>(), 1, st);
+            *b32 = w.b2.as<float>();
+        } else {
+            if (op == IMQ_OPERATOR_FAST_F64) fmm_apply<double>(P, xin, w.q2.as<double>(), 1, st);
+            else dense_f64_async(P.pos.as<double>(), n, P.c, xin, w.q2.as<double>(), st);
+            *b64 = w.q2.as<double>();
+        }
+    };
+    auto precond_apply = [&](const CGScalars *Sd, cudaStream_t st) {
+        schwarz_apply(P, Z, r, z, P.c, n, Sd, st);
+        if (!two_level) return;
+        const int *dn = Sd ? done_flag : nullptr;
+        const float *b32;
+        const double *b64;
+        op_product(z, st, Sd, &b32, &b64);
+        coarse_restrict(P, r, b32, b64, dn, st);
+        coarse_solve(P, dn, st);
+        coarse_prolong(P, z, z, dn, st);
+    };
 
     // ---- capture kIterPerGraph PCG iterations on a private stream
     GraphCapture cap;
@@ -663,8 +739,8 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         k_update_xr<<<gr, kRedThreads, 0, cs>>>(x, r, p, q, n, w.part.as<double>(), S);
         k_finish_rr<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S);
         k_copy_best<<<gr, kRedThreads, 0, cs>>>(x, w.xb.as<double>(), n, S);
-        if (o.precond == IMQ_PRECOND_SCHWARZ) {
-            schwarz_apply(P, Z, r, z, P.c, n, S, cs);
+        if (pre) {
+            precond_apply(S, cs);
             k_dot_part<<<gr, kRedThreads, 0, cs>>>(r, z, n, w.part.as<double>(), S);
             k_finish_beta<<<1, kRedThreads, 0, cs>>>(w.part.as<double>(), S, 0);
         } else {
@@ -723,16 +799,30 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                     max_outer > 0 ? std::max(o.inner_rtol, std::min(0.5, 0.5 * o.rtol / rel)) : 0.5 * o.rtol / rel;
                 IMQ_CUDA(cudaMemsetAsync(x, 0, 8 * n, s));
                 IMQ_CUDA(cudaMemsetAsync(w.xb.ptr, 0, 8 * n, s));
+                double rr_start = rr0;
+                if (two_level) {   // start the pass from the coarse solution d = Q r, r -= A d
+                    coarse_restrict(P, r, nullptr, nullptr, nullptr, s);
+                    coarse_solve(P, nullptr, s);
+                    coarse_prolong(P, nullptr, x, nullptr, s);
+                    IMQ_CUDA(cudaMemcpyAsync(w.xb.ptr, x, 8 * n, cudaMemcpyDeviceToDevice, s));
+                    const float *b32;
+                    const double *b64;
+                    op_product(x, s, nullptr, &b32, &b64);
+                    if (b32) k_sub_f32<<<gr, kRedThreads, 0, s>>>(r, b32, n);
+                    else k_sub_f64<<<gr, kRedThreads, 0, s>>>(r, b64, n);
+                    IMQ_LAUNCH_CHECK();
+                    rr_start = read_dot(r, r, n, w.part, w.tmp, s);
+                }
                 CGScalars h{};
-                h.rr = rr0;
+                h.rr = rr_start;
                 h.rr0 = rr0;
-                h.rr_best = rr0;
+                h.rr_best = rr_start;
                 h.rr_target = inner_rtol * inner_rtol * rr0;
                 h.maxit = o.maxit - iters;
-                if (o.precond == IMQ_PRECOND_SCHWARZ) {
+                if (pre) {
                     CGScalars hz = h;
                     IMQ_CUDA(cudaMemcpyAsync(S, &hz, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
-                    schwarz_apply(P, Z, r, z, P.c, n, S, s);
+                    precond_apply(S, s);
                     h.rz = read_dot(r, z, n, w.part, w.tmp, s);
                 } else {
                     h.rz = rr0;

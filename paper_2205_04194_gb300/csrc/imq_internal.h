@@ -175,6 +175,22 @@ struct GraphCapture {
     ~GraphCapture();
 };
 
+// Coarse space of the two-level Schwarz preconditioner (coarse.cu): the indicator
+// vectors of the largest tree boxes holding at most `cp` points (disjoint Morton
+// ranges covering all points), the Galerkin matrix E = Z^T A Z and its inverse.
+struct Coarse {
+    bool ready = false;
+    int cp = 0;          // max points per coarse box
+    int nc = 0;          // coarse boxes
+    DevMem cbeg;         // int32[nc + 1] Morton-order point ranges
+    DevMem einv;         // double[nc * nc] E^{-1} (symmetric)
+    DevMem g, cc;        // double[nc] restriction and coarse solution
+    double shift = 0;    // diagonal shift that made E factorable (relative to its mean diagonal)
+    bool gram_fp64 = false;   // E assembled with FP64 pairs
+    int gram_mode = 0;        // imq_cg_options.coarse_gram of the last set-up
+};
+constexpr int kCoarseMax = 16384;   // largest coarse space (E^{-1} is nc^2 doubles)
+
 // Streams and fork/join events of the concurrent FP32 product (per plan): the
 // far-field chain runs on a highest-priority stream, the near field on a
 // lowest-priority one, so free SM slots go to the latency-bound chain first.
@@ -256,6 +272,7 @@ struct Plan {
     std::vector<double> h_m2l_odd, h_l2l_odd, h_dzc;   // derivative path ([lev][40][K][Ko], [4][Ko][Ko])
     TypedOps ops32, ops64;
     Schwarz schwarz;
+    Coarse coarse;
     // statistics
     int64_t p2p_pairs = 0, m2l_pairs = 0;
     int64_t device_bytes() const;
@@ -291,6 +308,15 @@ void schwarz_setup(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s);
 // z = M r; Sv: per-solve state whose done flag skips the work (nullptr: always run)
 void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, double c, int64_t n, const void *Sv,
                    cudaStream_t s);
+// coarse.cu: two-level Schwarz coarse space (single plans)
+void coarse_setup(Plan &P, int cp, int gram, cudaStream_t s);   // gram: imq_cg_options.coarse_gram
+// g = Z^T (r - b), b = b32 (FP32) or b64 (FP64) or none: one block per coarse box, fixed-order FP64 sums
+void coarse_restrict(const Plan &P, const double *r, const float *b32, const double *b64, const int *done,
+                     cudaStream_t s);
+// cc = E^{-1} g
+void coarse_solve(const Plan &P, const int *done, cudaStream_t s);
+// z = y + Z cc (y may be null: z = Z cc)
+void coarse_prolong(const Plan &P, const double *y, double *z, const int *done, cudaStream_t s);
 // cg_batched.cu
 // rel_out / iters_out: host [nrhs][nprob] or nullptr
 void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_cg_options &o,

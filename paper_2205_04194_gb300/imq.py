@@ -146,14 +146,16 @@ class Plan:
 
     def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan", x0=None,
-              residual_plan=None, operator="fast_f32", schwarz_fp64=False, stream=None,
-              raise_on_failure=False):
+              residual_plan=None, operator="fast_f32", schwarz_fp64=False, coarse_points=0, coarse_gram="auto",
+              stream=None, raise_on_failure=False):
         """imq_cg_solve: coef with A coef = f.  Returns (coef, info dict); info["status"] is the
-        imq_status name (IMQ_NOT_CONVERGED keeps the best iterate in coef)."""
+        imq_status name (IMQ_NOT_CONVERGED keeps the best iterate in coef).
+        precond: "none", "schwarz" (leaf-neighbourhood patches) or "schwarz2" (the patches plus a
+        Galerkin coarse space of tree boxes holding at most coarse_points points)."""
         return self._solve("imq_cg_solve", f, coef, x0, stream, raise_on_failure, None, dict(
             rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
             refine_steps=refine_steps, inner_rtol=inner_rtol, residual=residual, residual_plan=residual_plan,
-            operator=operator, schwarz_fp64=schwarz_fp64))
+            operator=operator, schwarz_fp64=schwarz_fp64, coarse_points=coarse_points, coarse_gram=coarse_gram))
 
     def _solve(self, entry, f, coef, x0, stream, raise_on_failure, per_problem, kw):
         nrhs = 1 if len(np.shape(f)) == 1 else int(np.shape(f)[0])
@@ -165,7 +167,9 @@ class Plan:
         _lib.load().imq_cg_default_options(ctypes.byref(o))
         o.rtol = float(kw["rtol"])
         o.maxit = int(kw["maxit"])
-        o.precond = {"none": 0, None: 0, "schwarz": 1}[kw["precond"]]
+        o.precond = {"none": 0, None: 0, "schwarz": 1, "schwarz2": 2}[kw["precond"]]
+        o.coarse_points = int(kw.get("coarse_points", 0))
+        o.coarse_gram = {"auto": 0, "fp64": 1, "fp32": 2}[kw.get("coarse_gram", "auto")]
         o.schwarz_nmax = int(kw["schwarz_nmax"])
         o.schwarz_shift = float(kw["schwarz_shift"])
         o.refine_steps = int(kw["refine_steps"])

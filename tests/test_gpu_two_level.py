@@ -1,0 +1,66 @@
+"""Two-level Schwarz PCG on the GPU against the FP64 oracle.
+
+The clustered metric configuration scaled to 5,004 points (the analogue of
+tests/test_oracle_conditioning.py): the one-level preconditioner stalls above
+1e-6 while the two-level one (patches plus a Galerkin coarse space of leaf
+boxes) reaches it, with the residual certified by the dense FP64 product and
+re-measured by the oracle.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, need_gpu
+from oracle import solve as OS
+from paper_2205_04194_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+SCALE = 0.005
+
+
+def _analogue():
+    pts = W.clustered_points(int(round(87_500 * SCALE)), 8, int(round(300_000 * SCALE)), 0.03, 3)
+    return pts, 0.01 / np.sqrt(SCALE), W.franke(pts)
+
+
+def test_two_level_reaches_1e6_where_one_level_stalls():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    pts, c, f = _analogue()
+    plan = imq.Plan(cuda(pts), c, 12, 64, domain=(0.0, 0.0, 1.0))
+    # FP64 patches with a small shift (their amplification is what makes the coarse level pay),
+    # the dense FP64 operator, and a Galerkin matrix assembled with FP64 pairs (N^2 is small)
+    kw = dict(rtol=1e-6, maxit=400, schwarz_nmax=128, schwarz_shift=1e-9, schwarz_fp64=True,
+              operator="dense_f64", residual="dense")
+    _, i1 = plan.solve(cuda(f), precond="schwarz", **kw)
+    coef, i2 = plan.solve(cuda(f), precond="schwarz2", **kw)
+    assert i1["status"] != "IMQ_OK" and i1["max_rel_residual"] > 1e-6, i1
+    assert i2["status"] == "IMQ_OK", i2
+    assert OS.true_relres(pts, c, host(coef), f) <= 1e-6
+
+
+def test_two_level_with_the_fp32_fast_operator_and_refinement():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    pts, c, f = _analogue()
+    plan = imq.Plan(cuda(pts), c, 12, 64, domain=(0.0, 0.0, 1.0))
+    coef, info = plan.solve(cuda(f), rtol=1e-6, maxit=2000, precond="schwarz2", schwarz_nmax=128,
+                            schwarz_shift=1e-7, refine_steps=12, inner_rtol=1e-3, residual="dense")
+    r = OS.true_relres(pts, c, host(coef), f)
+    assert info["status"] in ("IMQ_OK", "IMQ_NOT_CONVERGED"), info
+    assert info["max_rel_residual"] == pytest.approx(r, rel=1e-2)
+    if info["status"] == "IMQ_OK":
+        assert r <= 1e-6
+    else:
+        assert r < 2e-4   # the FP32 operator's noise floor on this flat shape
+
+
+def test_two_level_rejected_on_batched_plans():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    pts = [W.uniform_points(500, 1, stream=k) for k in range(2)]
+    bp = imq.BatchedPlan([cuda(x) for x in pts], [0.05, 0.05], 8, 32, domain=(0.0, 0.0, 1.0))
+    with pytest.raises(imq.ImqError) as e:
+        bp._solve("imq_cg_solve_batched", cuda(np.ones(1000)), None, None, None, True, 2, dict(
+            rtol=1e-6, maxit=10, precond="schwarz2", schwarz_nmax=128, schwarz_shift=0.0, refine_steps=0,
+            inner_rtol=1e-4, residual="plan", residual_plan=None, operator="fast_f32", schwarz_fp64=False))
+    assert e.value.status == 7
