@@ -142,6 +142,25 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_rows(points, c, v, seconds: float, min_rows: int = 8):
     """Time the FP64 dense oracle (O1) on a sample of rows sized to ~`seconds`."""
     from oracle import dense
@@ -201,48 +220,63 @@ def run_batched(args, imq, dev):
                         domain=(0.0, 0.0, 1.0))
     tune_s = time.perf_counter() - t0
     P_b, leaf_b = tune["p"], tune["leaf"]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    bp = imq.BatchedPlan(pts, cs, P_b, leaf_b, domain=(0.0, 0.0, 1.0))
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    n_tot = bp.n
+    tiles = imq.tiles_of(tune)
+    n_tot = None
     f32 = f.float().contiguous()
-    for _ in range(3):
-        bp.matvec(f32)
-    reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        b32 = bp.matvec(f32)
-    e1.record()
-    torch.cuda.synchronize()
-    mv_ms = e0.elapsed_time(e1) / reps
-    # accuracy on 8 problems against the FP64 dense product on the GPU
-    errs = []
-    offs = bp.offsets
-    for b in np.linspace(0, len(probs) - 1, 8).astype(int):
-        sl = slice(int(offs[b]), int(offs[b + 1]))
-        ref = imq.dense_matvec(pts[b], cs[b], f[:, sl].contiguous())
-        got = b32[:, sl].double()
-        errs.append(float(max(((got[r] - ref[r]).norm() / ref[r].norm()).item() for r in range(4))))
-    coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, precond="schwarz", schwarz_nmax=128,
-                          schwarz_shift=1e-5)
-    rel = info["problem_rel_residual"]
-    bp.close()
-    return {"n_problems": len(probs), "n_total": n_tot, "nrhs": 4, "p": P_b, "leaf": leaf_b,
-            "autotune": {"seconds": tune_s, "met": tune["met"], "rel_err": tune["rel_err"],
-                         "sampled_rows": tune["sampled_rows"],
-                         "tried": [(t["p"], t["leaf"], t["rel_err"], t["matvec_ms"]) for t in tune["tried"]]},
-            "plan_build_s": build_s, "matvec_f32_ms": mv_ms,
-            "matvec_points_per_s": 4 * n_tot / (mv_ms * 1e-3),
-            "sampled_rel2_err_max": max(errs), "sampled_problems": 8,
-            "cg": {"rtol": 1e-6, "maxit": args.batched_cg_maxit, "status": info["status"],
-                   "iterations_max": info["iterations"], "solve_s": info["seconds"],
-                   "converged_fraction": float((rel <= 1e-6).mean()),
-                   "rel_residual_median": float(np.median(rel)), "rel_residual_max": float(rel.max()),
-                   "note": "c/h up to ~45: the larger problems are ill-conditioned, so the cap binds"}}
+    offs = None
+    out = {"n_problems": len(probs), "nrhs": 4, "p": P_b, "leaf": leaf_b,
+           "autotune": {"seconds": tune_s, "met": tune["met"], "rel_err": tune["rel_err"],
+                        "sampled_rows": tune["sampled_rows"], "choice": tiles,
+                        "tried": [(t["p"], t["leaf"], t["translations"], t["p2p_warps"], t["p2p_chunk"],
+                                   t["m2l_stages"], t["rel_err"], t["matvec_ms"]) for t in tune["tried"]]}}
+    # the tuned configuration, and the same (p, leaf) with FP32 translations if the tuner chose FP64
+    variants = [("tuned", tiles)]
+    if tiles["translations"] != "fp32":
+        variants.append(("fp32_translations", {"translations": "fp32"}))
+    for name, kw in variants:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bp = imq.BatchedPlan(pts, cs, P_b, leaf_b, domain=(0.0, 0.0, 1.0), **kw)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        n_tot, offs = bp.n, bp.offsets
+        for _ in range(3):
+            bp.matvec(f32)
+        reps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            b32 = bp.matvec(f32)
+        e1.record()
+        torch.cuda.synchronize()
+        mv_ms = e0.elapsed_time(e1) / reps
+        # accuracy on 16 problems, every right-hand side, against the FP64 dense product on the GPU
+        errs = []
+        for b in np.linspace(0, len(probs) - 1, 16).astype(int):
+            sl = slice(int(offs[b]), int(offs[b + 1]))
+            ref = imq.dense_matvec(pts[b], cs[b], f[:, sl].contiguous())
+            got = b32[:, sl].double()
+            errs.append([float(((got[r] - ref[r]).norm() / ref[r].norm()).item()) for r in range(4)])
+        errs = np.array(errs)
+        out[name] = {"plan": kw, "plan_build_s": build_s, "matvec_f32_ms": mv_ms,
+                     "ns_per_point_rhs": mv_ms * 1e6 / (4 * bp.n),
+                     "matvec_points_per_s": 4 * bp.n / (mv_ms * 1e-3),
+                     "sampled_rel2_err_max": float(errs.max()),
+                     "sampled_rel2_err_max_per_rhs": errs.max(axis=0).tolist(), "sampled_problems": 16}
+        if name == "tuned":
+            coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, precond="schwarz",
+                                  schwarz_shift=1e-5)
+            rel = info["problem_rel_residual"]
+            out["cg"] = {"rtol": 1e-6, "maxit": args.batched_cg_maxit, "precond": "schwarz (224-point patches)",
+                         "status": info["status"], "iterations_max": info["iterations"],
+                         "solve_s": info["seconds"], "converged_fraction": float((rel <= 1e-6).mean()),
+                         "rel_residual_median": float(np.median(rel)), "rel_residual_max": float(rel.max()),
+                         "residual_product": "fast FP64 of the batched plan",
+                         "note": "c/h up to ~45: the larger problems are ill-conditioned, so the cap binds"}
+        bp.close()
+    out["n_total"] = n_tot
+    return out
 
 
 def run_solves(args, imq, wl, d_pts, plan, dev):
@@ -251,19 +285,24 @@ def run_solves(args, imq, wl, d_pts, plan, dev):
     import torch
     from paper_2205_04194_gb300 import workloads as W
     out = {}
-    # CG at the metric configuration: f = Franke, 1e-6, capped iterations
+    # CG at the metric configuration: f = Franke, 1e-6, capped iterations; the one-level Schwarz
+    # preconditioner and the two-level one (coarse boxes of at most 1024 points)
     f = torch.from_numpy(wl.f).to(dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    coef, info = plan.solve(f, rtol=1e-6, maxit=args.cg_maxit, precond="schwarz", schwarz_nmax=128,
-                            schwarz_shift=1e-5)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    out["cg"] = {"workload": wl.name, "rtol": 1e-6, "maxit": args.cg_maxit, "precond": "schwarz(128, shift 1e-5/c)",
-                 "operator": "fast_f32", "status": info["status"], "iterations": info["iterations"],
-                 "solve_s": info["seconds"], "wall_s_incl_setup": wall,
-                 "s_per_iter": info["seconds"] / max(1, info["iterations"]),
-                 "true_rel_residual": info["max_rel_residual"], "residual_product": "fast FP64, same tree"}
+    for key, kw in (("cg_one_level", dict(precond="schwarz")),
+                    ("cg", dict(precond="schwarz2", coarse_points=1024))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        coef, info = plan.solve(f, rtol=1e-6, maxit=args.cg_maxit, schwarz_shift=1e-5, **kw)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[key] = {"workload": wl.name, "rtol": 1e-6, "maxit": args.cg_maxit,
+                    "precond": kw["precond"] + " (224-point patches, shift 1e-5/c"
+                               + (", coarse boxes <= 1024 points)" if "coarse_points" in kw else ")"),
+                    "operator": "fast_f32", "status": info["status"], "iterations": info["iterations"],
+                    "outer_steps": info["outer_steps"], "solve_s": info["seconds"],
+                    "wall_s_incl_setup": wall, "s_per_iter": info["seconds"] / max(1, info["iterations"]),
+                    "true_rel_residual": info["max_rel_residual"], "residual_product": "fast FP64, same tree",
+                    "note": "s_per_iter includes the FP64 true-residual products of the outer passes"}
     # 100k uniform, c = 2 x mean NN spacing, FP32 inner / FP64 refinement to 1e-8
     u = W.uniform_100k()
     pl = imq.Plan(torch.from_numpy(u.points).to(dev), u.c, u.p, u.leaf, domain=u.domain)
@@ -327,22 +366,53 @@ def run_solves(args, imq, wl, d_pts, plan, dev):
                              "best L of {1, 2, 3}.  Paper Table 1 (Xeon E5-2620 v3, FP64): dense 1.62..128 s, "
                              "translation 1.58..23.3 s, E 2.67e-9..1.06e-8"}
     out["batched_256"] = run_batched(args, imq, dev)
-    # gradient of the validation loss at N = 200k, 20k validation points, c = 0.05
+    # gradient of the validation loss at N = 200k, 20k validation points, c = 0.05 (the configuration:
+    # c/h ~ 45, the solves are capped and their status and residual are reported beside the gradient)
     from paper_2205_04194_gb300 import autograd as AG
     g = W.grad_200k()
+    d_tr, d_va = torch.from_numpy(g["train"]).to(dev), torch.from_numpy(g["val"]).to(dev)
+    d_y = torch.from_numpy(g["y_val"]).to(dev)
     ct = torch.tensor(g["c"], dtype=torch.float64, requires_grad=True)
     ft = torch.from_numpy(g["f"]).to(dev).requires_grad_(True)
-    cg = dict(rtol=1e-6, maxit=args.grad_maxit, precond="schwarz", schwarz_nmax=128, schwarz_shift=1e-5)
+    cg = dict(rtol=1e-6, maxit=args.grad_maxit, precond="schwarz", schwarz_shift=1e-5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L = AG.InterpLoss.apply(ct, ft, torch.from_numpy(g["train"]).to(dev), torch.from_numpy(g["val"]).to(dev),
-                            torch.from_numpy(g["y_val"]).to(dev), 12, 64, (0.0, 0.0, 1.0), torch.float32, cg)
+    L = AG.InterpLoss.apply(ct, ft, d_tr, d_va, d_y, 12, 64, (0.0, 0.0, 1.0), torch.float32, cg, True)
     L.backward()
     torch.cuda.synchronize()
+    li = AG.InterpLoss.last_info
     out["grad"] = {"n_train": 200000, "n_val": 20000, "c": g["c"], "p": 12, "loss": float(L.item()),
                    "dloss_dc": float(ct.grad.item()), "dloss_df_norm": float(ft.grad.norm().item()),
                    "wall_s": time.perf_counter() - t0, "cg_maxit_per_solve": args.grad_maxit,
-                   "note": "forward + adjoint; solves capped (c/h ~ 45 is ill-conditioned)"}
+                   "solve_status": li["status"], "solve_max_rel_residual": li["max_rel_residual"],
+                   "note": "forward + adjoint; c/h ~ 45 is ill-conditioned, the capped solves leave this "
+                           "gradient unvalidated (see grad_wellcond_200k)"}
+    # the same loss at a well-conditioned shape, c = 2 x mean NN spacing: gradient through the FP32 fast
+    # operator (solves to 1e-10 with FP64 refinement) against central differences of the loss
+    c2 = 2.0 * W.mean_nn_spacing(g["train"])
+    cg = dict(rtol=1e-10, maxit=6000, precond="schwarz", refine_steps=10, inner_rtol=1e-4)
+    ct = torch.tensor(c2, dtype=torch.float64, requires_grad=True)
+    ft = torch.from_numpy(g["f"]).to(dev).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = AG.InterpLoss.apply(ct, ft, d_tr, d_va, d_y, 12, 64, (0.0, 0.0, 1.0), torch.float32, cg)
+    L.backward()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    li = AG.InterpLoss.last_info
+    hh = 1e-3 * c2
+
+    def loss_at(cv):
+        return AG.InterpLoss.apply(torch.tensor(cv, dtype=torch.float64), ft.detach(), d_tr, d_va, d_y, 12, 64,
+                                   (0.0, 0.0, 1.0), torch.float64, cg).item()
+    fd = (loss_at(c2 + hh) - loss_at(c2 - hh)) / (2 * hh)
+    out["grad_wellcond_200k"] = {"n_train": 200000, "n_val": 20000, "c": c2, "p": 12, "loss": float(L.item()),
+                                 "dloss_dc": float(ct.grad.item()), "dloss_dc_central_diff": fd,
+                                 "rel_diff": abs(float(ct.grad.item()) - fd) / abs(fd), "fd_step": hh,
+                                 "wall_s": wall, "solve_status": li["status"],
+                                 "solve_max_rel_residual": li["max_rel_residual"],
+                                 "note": "gradient: FP32 evaluation and derivative products, FP32 inner CG with "
+                                         "FP64 refinement; central differences: the loss with FP64 evaluation"}
     return out
 
 
@@ -464,6 +534,42 @@ def main():
             dts.append(a.elapsed_time(b))
         dense_ms = statistics.mean(dts)
 
+    # the configuration's three orders p in {8, 12, 16}: time per product (L2 flushed) and, below,
+    # the sampled error against the FP64 oracle; and the all-FP64 product at the tuned p
+    per_p, outs_p = {}, {}
+    if rank == 0:
+        for pp in (8, 12, 16):
+            pl = plan if pp == wl.p else imq.Plan(d_pts, wl.c, pp, wl.leaf, domain=wl.domain)
+            o = torch.empty_like(d_v)
+            for _ in range(3):
+                pl.matvec(d_v, o)
+            ts = []
+            for k in range(10):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pl.matvec(d_v, o)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            per_p[pp] = {"fast_f32_ms": statistics.mean(ts), "k_real": pl.info()["k_real"]}
+            outs_p[pp] = o
+            if pl is not plan:
+                pl.close()
+        d_v64 = d_v.double()
+        o64 = torch.empty_like(d_v64)
+        plan.matvec(d_v64, o64)
+        ts = []
+        for k in range(3):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.matvec(d_v64, o64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        f64_ms = statistics.mean(ts)
+
     # end to end through the public API with pinned host buffers
     h_v = torch.from_numpy(wl.v).float().pin_memory()
     h_out = torch.empty_like(h_v).pin_memory()
@@ -494,12 +600,15 @@ def main():
         from oracle import dense as O
         O.build()
         dt, nrows, rows, ref, cores = cpu_oracle_rows(wl.points, wl.c, wl.v, args.cpu_seconds)
-        cpu = {"value": 1e3 * dt / nrows * wl.n, "unit": "ms", "cores": cores, "kind": "oracle",
+        cpu = {"value": 1e3 * dt / nrows * wl.n, "unit": "ms", "cores": cores, "cpu_model": cpu_model(),
+               "kind": "oracle",
                "sample": f"{nrows} random rows of the FP64 dense product (oracle O1) on the "
                          f"{wl.n}-point workload, scaled by N/rows to one full A v"}
         rel = lambda a: float(np.linalg.norm(a[rows] - ref) / np.linalg.norm(ref))
         err = {"fast_rel2_sampled": rel(b_fast), "dense_gpu_rel2_sampled": rel(b_dense),
-               "rows": int(nrows)}
+               "fast_f64_rel2_sampled": rel(o64.cpu().numpy()), "rows": int(nrows)}
+        for pp, o in outs_p.items():
+            per_p[pp]["rel2_sampled"] = rel(o.double().cpu().numpy())
 
     peaks, src = _peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -550,10 +659,14 @@ def main():
         "errors": err,
         "tree": {k: info[k] for k in ("n_boxes", "n_leaves", "max_level", "k_real", "n_u", "n_v", "n_w",
                                       "n_x", "p2p_pairs", "m2l_pairs")},
+        "per_p": {str(k): v for k, v in per_p.items()},
+        "fast_f64_ms": f64_ms,
         "cg": extras.get("cg"),
+        "cg_one_level": extras.get("cg_one_level"),
         "cg_uniform_100k": extras.get("cg_uniform_100k"),
         "table1_halton": extras.get("table1"),
         "grad_200k": extras.get("grad"),
+        "grad_wellcond_200k": extras.get("grad_wellcond_200k"),
         "batched_256": extras.get("batched_256"),
     }
     print(json.dumps(line), flush=True)

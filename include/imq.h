@@ -296,8 +296,9 @@ typedef struct imq_cg_options {
     double rtol;             /* target of the true relative residual                         */
     int32_t maxit;           /* cap on the total number of inner iterations                   */
     int32_t precond;         /* imq_precond                                                    */
-    int32_t schwarz_nmax;    /* max points per Schwarz patch, 1..224 (0: 128)                  */
-    double schwarz_shift;    /* patch diagonal shift, relative to A_ii = 1/c                   */
+    int32_t schwarz_nmax;    /* max points per Schwarz patch, 1..224 (0: 224; 160 with FP64)   */
+    double schwarz_shift;    /* patch diagonal shift, relative to A_ii = 1/c (FP32 patches: at
+                                least 1e-6)                                                    */
     int32_t refine_steps;    /* outer refinement steps (0: one pass, then the true residual)   */
     double inner_rtol;       /* lower bound of the inner relative tolerance when refining      */
     int32_t residual;        /* imq_residual                                                   */

@@ -19,13 +19,13 @@ from ._lib import CgInfo, CgOptions
 from .imq import F32, F64, EvalPlan, Plan, _buf, _stream
 
 
-def cg_options(rtol=1e-10, maxit=2000, precond="schwarz", schwarz_nmax=128, schwarz_fp64=False,
+def cg_options(rtol=1e-10, maxit=2000, precond="schwarz", schwarz_nmax=0, schwarz_fp64=False,
                schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan",
                operator="fast_f32") -> CgOptions:
     o = CgOptions()
     _lib.load().imq_cg_default_options(ctypes.byref(o))
     o.rtol, o.maxit = float(rtol), int(maxit)
-    o.precond = {"none": 0, "schwarz": 1}[precond]
+    o.precond = {"none": 0, "schwarz": 1, "schwarz2": 2}[precond]
     o.schwarz_nmax, o.schwarz_fp64 = int(schwarz_nmax), 1 if schwarz_fp64 else 0
     o.schwarz_shift = float(schwarz_shift)
     o.refine_steps, o.inner_rtol = int(refine_steps), float(inner_rtol)
@@ -56,16 +56,29 @@ def interp_loss_grad(train: Plan, evalp: EvalPlan, f, y, dtype=torch.float64, **
                                              "max_rel_residual": info.max_rel_residual}
 
 
+class UnconvergedSolve(RuntimeError):
+    """The solves behind a gradient did not reach their tolerance (info attached)."""
+
+    def __init__(self, info):
+        self.info = info
+        super().__init__(f"interpolation solves did not converge: {info}")
+
+
 class InterpLoss(torch.autograd.Function):
     """L(c, f) = mean_k (P(t_k) - y_k)^2 with P the IMQ interpolant of (x, f) at shape c.
 
-    apply(c, f, train_points, val_points, y_val, p, leaf, domain, dtype, cg_kwargs)
+    apply(c, f, train_points, val_points, y_val, p, leaf, domain, dtype, cg_kwargs, allow_unconverged)
     c: 0-d float64 tensor; f: float64 tensor [N] (CUDA); points float64 [.,2] (CUDA).
+    A gradient from solves that stopped short of their tolerance (IMQ_NOT_CONVERGED) or broke
+    down (IMQ_NUMERICAL) raises UnconvergedSolve unless allow_unconverged is true; either way the
+    solver info of the last forward pass is kept in InterpLoss.last_info.
     """
+
+    last_info = None
 
     @staticmethod
     def forward(ctx, c, f, train_points, val_points, y_val, p, leaf, domain=None, dtype=torch.float64,
-                cg_kwargs=None):
+                cg_kwargs=None, allow_unconverged=False):
         cval = float(c.detach().item())
         tp = Plan(train_points, cval, p, leaf, domain=domain)
         ep = EvalPlan(train_points, val_points, cval, p, leaf, domain=domain)
@@ -73,10 +86,13 @@ class InterpLoss(torch.autograd.Function):
                                                     dtype=dtype, **(cg_kwargs or {}))
         tp.close()
         ep.close()
+        InterpLoss.last_info = info
+        if info["status"] != "IMQ_OK" and not allow_unconverged:
+            raise UnconvergedSolve(info)
         ctx.save_for_backward(torch.tensor(dc, dtype=torch.float64, device=f.device), df)
         return torch.tensor(loss, dtype=torch.float64, device=f.device)
 
     @staticmethod
     def backward(ctx, g):
         dc, df = ctx.saved_tensors
-        return g * dc, g * df, None, None, None, None, None, None, None, None
+        return g * dc, g * df, None, None, None, None, None, None, None, None, None

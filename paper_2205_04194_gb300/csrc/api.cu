@@ -507,7 +507,7 @@ void imq_cg_default_options(imq_cg_options *o) {
     o->rtol = 1e-6;
     o->maxit = 1000;
     o->precond = IMQ_PRECOND_SCHWARZ;
-    o->schwarz_nmax = 128;
+    o->schwarz_nmax = 0;   // 224 points (FP32 patches), 160 (FP64)
     o->schwarz_shift = 0.0;
     o->refine_steps = 0;
     o->inner_rtol = 1e-4;

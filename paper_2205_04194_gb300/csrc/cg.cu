@@ -46,6 +46,7 @@ constexpr int kIterPerGraph = 8;
 // residual of the best iterate.  kNumerical is reserved for NaN / Inf.
 enum CGState : int { kRunning = 0, kConverged = 1, kNumerical = 2, kMaxIter = 3, kBreakdown = 4 };
 constexpr int kMaxRestarts = 16;   // restarts after a breakdown when no refinement steps are requested
+constexpr double kF32PatchShift = 1e-6;   // least diagonal shift of FP32 Schwarz patches, relative to 1/c
 
 struct CGScalars {
     double rz, rz_new, pq, rr, alpha, beta, rr_target, rr_best, rr0;
@@ -246,13 +247,13 @@ __global__ void k_scatter_f64(const double *__restrict__ v, const int32_t *__res
 // differences, right-looking Cholesky in shared memory; pivots below
 // dmin are raised to dmin (the patch matrices of flat shapes are numerically
 // singular).  Output (INV = false): the n x n column-major lower factor L.
-// INV = true: the explicit inverse (A_b + shift I)^{-1} = L^{-T} L^{-1}, so that
-// the apply is one dense matrix-vector product per patch (bandwidth-bound)
-// instead of two sequential triangular solves (latency-bound).  L^{-1} is
-// formed column by column (thread t solves L y = e_t) in a second shared
-// buffer Y, row-major with a padded stride (Y[k][t] at k * (n + 1) + t), then
-// the inverse by 4 x 4 register tiles of Y^T Y on and below the diagonal,
-// mirrored.
+// INV = true: the inverse factor L^{-1} (column-major, lower), so that the
+// apply z = L^{-T} (L^{-1} r) is two dense triangular matrix-vector products
+// per patch (bandwidth-bound) instead of two sequential triangular solves
+// (latency-bound), and r.z = |L^{-1} r|^2 stays positive in FP32 (an explicit
+// FP32 inverse L^{-T} L^{-1} of an ill-conditioned patch need not be).  L^{-1}
+// replaces L in shared memory column by column (last column first), with one
+// extra column of n values.
 template <class T, bool INV>
 __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
                                  const int64_t *__restrict__ foff, const double2 *__restrict__ pos,
@@ -267,8 +268,8 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
     const double cb = shape.of(leaves[b]);
     const T c2 = (T)(cb * cb), shift = (T)(shift_rel / cb);
     T *F = factor + foff[b];
-    // INV: an inverse that overflows (pivots at the clamp, L^{-1} growing beyond the FP32
-    // range) is recomputed with the clamp raised 1000-fold, up to three times
+    // INV: an inverse factor that overflows (pivots at the clamp, L^{-1} growing beyond the
+    // FP32 range) is recomputed with the clamp raised 1000-fold, up to three times
     for (int attempt = 0; attempt < (INV ? 4 : 1); ++attempt) {
         const T dmin = (T)(dmin_rel / cb * pow(1e3, (double)attempt));
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -309,57 +310,31 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
             }
             return;
         } else {
-            const int n4 = (n + 3) & ~3, ld = n4 + 1;
-            T *Y = A + (size_t)n * n;   // [n4][ld], rows k >= n and columns t >= n stay zero
-            for (int e = threadIdx.x; e < n4 * ld; e += blockDim.x) Y[e] = (T)0;
-            __syncthreads();
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {   // column t of L^{-1}
-                bool fin = true;
-                for (int i = t; i < n; ++i) {
-                    T sum = i == t ? (T)1 : (T)0;
-                    for (int k = t; k < i; ++k) sum -= A[(size_t)k * n + i] * Y[(size_t)k * ld + t];
-                    const T y = sum / A[(size_t)i * n + i];
-                    fin = fin && isfinite(y);
-                    Y[(size_t)i * ld + t] = y;
+            // L^{-1} in place, column j from the last to the first: X[i][j] = -(sum_{j < k <= i}
+            // X[i][k] L[k][j]) / L[j][j] for i > j, X[j][j] = 1 / L[j][j]; column j of L is copied
+            // to tmp first because the new column overwrites it
+            T *tmp = A + (size_t)n * n;
+            for (int jc = n - 1; jc >= 0; --jc) {
+                for (int k = jc + 1 + threadIdx.x; k < n; k += blockDim.x) tmp[k] = A[(size_t)jc * n + k];
+                __syncthreads();
+                const T d = (T)1 / A[(size_t)jc * n + jc];
+                for (int i = jc + 1 + threadIdx.x; i < n; i += blockDim.x) {
+                    T sum = 0;
+                    for (int k = jc + 1; k <= i; ++k) sum += A[(size_t)k * n + i] * tmp[k];
+                    const T x = -sum * d;
+                    if (!isfinite(x)) s_bad = 1;
+                    A[(size_t)jc * n + i] = x;
                 }
-                if (!fin) s_bad = 1;
+                if (threadIdx.x == 0) {
+                    A[(size_t)jc * n + jc] = d;
+                    if (!isfinite(d)) s_bad = 1;
+                }
+                __syncthreads();
             }
-            __syncthreads();
             if (s_bad) continue;
-            const int nt = n4 / 4, ntiles = nt * (nt + 1) / 2;
-            for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
-                int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);   // tile = ti (ti + 1) / 2 + tj, tj <= ti
-                while (ti * (ti + 1) / 2 > tile) --ti;
-                while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-                const int tj = tile - ti * (ti + 1) / 2;
-                const int i0 = 4 * ti, j0 = 4 * tj;
-                T acc[4][4] = {};
-                for (int k = i0; k < n4; ++k) {   // Y[k][i] = 0 for k < i, and i0 >= j0
-                    const T *yk = Y + (size_t)k * ld;
-                    T a[4], bb[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        a[q] = yk[i0 + q];
-                        bb[q] = yk[j0 + q];
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * bb[r];
-                }
-                bool fin = true;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int i = i0 + q, j = j0 + r;
-                        fin = fin && isfinite(acc[q][r]);
-                        if (i < n && j < n) {
-                            F[(size_t)j * n + i] = acc[q][r];
-                            F[(size_t)i * n + j] = acc[q][r];
-                        }
-                    }
-                if (!fin) s_bad = 1;
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                const int t = e / n, i = e - t * n;
+                F[e] = i >= t ? A[e] : (T)0;
             }
             __syncthreads();
             if (!s_bad) return;
@@ -369,7 +344,7 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
     if constexpr (INV) {
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int j = e / n, i = e - j * n;
-            F[e] = i == j ? (T)cb : (T)0;
+            F[e] = i == j ? (T)sqrt(cb) : (T)0;
         }
     }
 }
@@ -429,10 +404,12 @@ __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, co
     }
 }
 
-// One warp per patch: y = Ainv r_patch with the explicit FP32 inverse (column-major
-// n x n, n <= 32 * kInvRowsPerLane); r_j is broadcast from the lane holding it, and
-// lane l accumulates rows l, l + 32, ... (coalesced column reads).
-constexpr int kInvRowsPerLane = 5;   // patches up to 160 points
+// One warp per patch: y = L^{-T} (L^{-1} r_patch) with the FP32 inverse factor
+// (column-major n x n lower, n <= 32 * kInvRowsPerLane).  Pass 1, w = L^{-1} r:
+// r_k is broadcast from the lane holding it and lane l accumulates rows l, l + 32,
+// ... over the columns k (coalesced column reads).  Pass 2, y_k = column k . w:
+// one warp reduction per column.
+constexpr int kInvRowsPerLane = 7;   // patches up to 224 points
 __global__ void __launch_bounds__(128) k_schwarz_inv_apply(int npatch, const int32_t *__restrict__ poff,
                                                            const int32_t *__restrict__ ppts,
                                                            const int64_t *__restrict__ foff,
@@ -443,7 +420,7 @@ __global__ void __launch_bounds__(128) k_schwarz_inv_apply(int npatch, const int
     const int lane = threadIdx.x & 31;
     if (warp >= npatch) return;
     const int o = poff[warp], n = poff[warp + 1] - o;
-    const float *Ai = inv + foff[warp];
+    const float *Li = inv + foff[warp];
     float rv[kInvRowsPerLane], acc[kInvRowsPerLane];
 #pragma unroll
     for (int t = 0; t < kInvRowsPerLane; ++t) {
@@ -452,25 +429,33 @@ __global__ void __launch_bounds__(128) k_schwarz_inv_apply(int npatch, const int
         acc[t] = 0.f;
     }
 #pragma unroll
-    for (int jt = 0; jt < kInvRowsPerLane; ++jt) {
-        if (32 * jt >= n) break;
-        const int jn = min(32, n - 32 * jt);
-        const float *col0 = Ai + (size_t)(32 * jt) * n;
+    for (int kt = 0; kt < kInvRowsPerLane; ++kt) {
+        if (32 * kt >= n) break;
+        const int kn = min(32, n - 32 * kt);
+        const float *col0 = Li + (size_t)(32 * kt) * n;
 #pragma unroll 4
-        for (int jl = 0; jl < jn; ++jl) {
-            const float rj = __shfl_sync(0xFFFFFFFFu, rv[jt], jl);
-            const float *col = col0 + (size_t)jl * n;
+        for (int kl = 0; kl < kn; ++kl) {
+            const float rk = __shfl_sync(0xFFFFFFFFu, rv[kt], kl);
+            const float *col = col0 + (size_t)kl * n;
 #pragma unroll
-            for (int t = 0; t < kInvRowsPerLane; ++t) {
+            for (int t = kt; t < kInvRowsPerLane; ++t) {   // rows i >= 32 kt (the rest is zero)
                 const int i = lane + 32 * t;
-                if (i < n) acc[t] = fmaf(__ldg(col + i), rj, acc[t]);
+                if (i < n) acc[t] = fmaf(__ldg(col + i), rk, acc[t]);
             }
         }
     }
+    // acc = w = L^{-1} r; y_k = sum_{i >= k} L^{-1}[i][k] w_i
+    for (int k = 0; k < n; ++k) {
+        const float *col = Li + (size_t)k * n;
+        float part = 0.f;
 #pragma unroll
-    for (int t = 0; t < kInvRowsPerLane; ++t) {
-        const int i = lane + 32 * t;
-        if (i < n) ypatch[o + i] = (double)acc[t];
+        for (int t = 0; t < kInvRowsPerLane; ++t) {
+            const int i = lane + 32 * t;
+            if (i < n && i >= k) part = fmaf(__ldg(col + i), acc[t], part);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
+        if (lane == 0) ypatch[o + k] = (double)part;
     }
 }
 
@@ -555,10 +540,13 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     Z.ypatch.alloc(sizeof(double) * std::max<int64_t>(1, Z.total_slots));
     AsyncMem ncl(sizeof(int), s);
     IMQ_CUDA(cudaMemsetAsync(ncl.ptr, 0, sizeof(int), s));
-    // FP32 patches of at most 32 * kInvRowsPerLane points are applied through their explicit inverse
+    // FP32 patches get a diagonal shift of at least kF32PatchShift / c: a patch matrix that FP32
+    // cannot hold as positive definite otherwise meets clamped pivots whose Schur updates grow
+    // without bound
+    const double fshift = fp64 ? shift : std::max(shift, kF32PatchShift);
+    // FP32 patches of at most 32 * kInvRowsPerLane points are applied through their inverse factor
     Z.inverse = !fp64 && maxn <= 32 * kInvRowsPerLane;
-    const int n4 = (maxn + 3) & ~3;
-    const size_t smem = es * (size_t)maxn * maxn + (Z.inverse ? es * (size_t)n4 * (n4 + 1) : 0);
+    const size_t smem = es * ((size_t)maxn * maxn + (Z.inverse ? (size_t)maxn : 0));
     if (fp64) {
         IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
@@ -571,7 +559,7 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
         IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<Z.npatch, 256, smem, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
                                          Z.fac_off.as<int64_t>(), P.pos.as<double2>(), P.leaves.as<int32_t>(),
-                                         P.shape(), shift, 1e-6, Z.factor.as<float>(), ncl.as<int>());
+                                         P.shape(), fshift, 1e-6, Z.factor.as<float>(), ncl.as<int>());
     }
     IMQ_LAUNCH_CHECK();
     IMQ_CUDA(cudaStreamSynchronize(s));
@@ -650,6 +638,10 @@ void residual_product(Plan &P, Plan *RP, int mode, const double *vs, double *out
 
 void schwarz_setup(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) { build_schwarz(P, nmax, shift, fp64, s); }
 
+int schwarz_nmax_of(const imq_cg_options &o) {
+    return o.schwarz_nmax > 0 ? o.schwarz_nmax : (o.schwarz_fp64 ? 160 : 224);
+}
+
 double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s) {
     DevMem part, tmp;
     part.alloc(8 * kRedBlocks);
@@ -665,7 +657,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
     if (o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);
     const bool two_level = o.precond == IMQ_PRECOND_SCHWARZ_2L;
     const bool pre = o.precond == IMQ_PRECOND_SCHWARZ || two_level;
-    if (pre) build_schwarz(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    if (pre) build_schwarz(P, schwarz_nmax_of(o), o.schwarz_shift, o.schwarz_fp64 != 0, s);
     if (two_level) coarse_setup(P, o.coarse_points > 0 ? o.coarse_points : P.leaf, o.coarse_gram, s);
     const Schwarz &Z = P.schwarz;
     Work w;

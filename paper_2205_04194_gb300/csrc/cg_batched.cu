@@ -231,7 +231,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     ensure_ops(P, false, s);
     if (!dense_res || o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);   // FP64 fast product
     if (o.precond == IMQ_PRECOND_SCHWARZ)
-        schwarz_setup(P, o.schwarz_nmax > 0 ? o.schwarz_nmax : 128, o.schwarz_shift, o.schwarz_fp64 != 0, s);
+        schwarz_setup(P, schwarz_nmax_of(o), o.schwarz_shift, o.schwarz_fp64 != 0, s);
     const bool pre = o.precond == IMQ_PRECOND_SCHWARZ;
     const bool f64op = o.inner_operator == IMQ_OPERATOR_FAST_F64;
     const double *dpos = P.pos.as<double>(), *dprob_c = P.prob_c.as<double>();

@@ -305,6 +305,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
               imq_cg_info *info, cudaStream_t s);
 double device_dot(const double *a, const double *b, int64_t n, cudaStream_t s);   // deterministic, synchronises
 void schwarz_setup(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s);
+int schwarz_nmax_of(const imq_cg_options &o);   // the patch size a solve uses (0: 224 FP32, 160 FP64)
 // z = M r; Sv: per-solve state whose done flag skips the work (nullptr: always run)
 void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, double c, int64_t n, const void *Sv,
                    cudaStream_t s);

@@ -144,7 +144,7 @@ class Plan:
         call("imq_matvec", self._h, vp, op, nrhs, code, _stream(stream))
         return out
 
-    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
+    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=0,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan", x0=None,
               residual_plan=None, operator="fast_f32", schwarz_fp64=False, coarse_points=0, coarse_gram="auto",
               stream=None, raise_on_failure=False):
@@ -333,7 +333,7 @@ class BatchedPlan(Plan):
     def n_problems(self) -> int:
         return len(self.c_list)
 
-    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=128,
+    def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=0,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, x0=None, operator="fast_f32",
               schwarz_fp64=False, residual="plan", stream=None, raise_on_failure=False):
         """imq_cg_solve_batched: every problem's system at once, per-problem CG scalars.
