@@ -232,7 +232,7 @@ def run_batched(args, imq, dev):
     # the tuned configuration, and the same (p, leaf) with FP32 translations if the tuner chose FP64
     variants = [("tuned", tiles)]
     if tiles["translations"] != "fp32":
-        variants.append(("fp32_translations", {"translations": "fp32"}))
+        variants.append(("fp32_translations", dict(tiles, translations="fp32")))
     for name, kw in variants:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -264,7 +264,7 @@ def run_batched(args, imq, dev):
                      "matvec_points_per_s": 4 * bp.n / (mv_ms * 1e-3),
                      "sampled_rel2_err_max": float(errs.max()),
                      "sampled_rel2_err_max_per_rhs": errs.max(axis=0).tolist(), "sampled_problems": 16}
-        if name == "tuned":
+        if kw.get("translations", "fp32") == "fp32" and "cg" not in out:   # CG on the FP32-translation plan
             coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, precond="schwarz",
                                   schwarz_shift=1e-5)
             rel = info["problem_rel_residual"]
