@@ -84,6 +84,8 @@ typedef struct imq_options {
     int32_t p2p_chunk;         /* targets per P2P register tile: 8, 16 (default) or 32      */
     int32_t m2l_stages;        /* tensor-core M2L pipeline stages: 2..4 (default: as many as
                                   fit in shared memory; more than fit is clamped)            */
+    int32_t m2l_split;         /* tensor-core M2L: CTAs sharing one 128-box tile's offset
+                                  classes, 1..4 (default: by the tile count)                  */
     /* Optional allocator of the plan's own device buffers (tree, lists, operators,
      * expansions, solver work arrays), e.g. a framework's caching allocator.  Both
      * NULL: cudaMalloc / cudaFree.  alloc returns device memory of at least `bytes`
@@ -430,9 +432,10 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  *        with FP64 translations (IMQ_TRANS_FP64), whose error floor is lower;
  *     3. on the chosen (p, leaf, translations), the P2P tile shape (p2p_warps x
  *        p2p_chunk in {2, 4, 8} x {8, 16, 32}), then the tensor-core M2L
- *        pipeline depth (m2l_stages 2..4, as far as they fit): the fastest
- *        shape whose error still meets the target (else whose error does not
- *        grow by more than 1 %).
+ *        pipeline depth (m2l_stages 2..4, as far as they fit) and the number
+ *        of CTAs sharing an M2L tile (m2l_split 1..4): the fastest shape whose
+ *        error still meets the target (else whose error does not grow by more
+ *        than 1 %).
  *   If no candidate meets the target, the most accurate one is returned and
  *   met = 0.
  *
@@ -463,8 +466,7 @@ typedef struct imq_tune_entry {
     double rel_err;          /* sampled relative 2-norm error of the FP32 product */
     float matvec_ms;         /* best of the timed products                         */
     int32_t translations;    /* imq_translations                                   */
-    int32_t p2p_warps, p2p_chunk, m2l_stages;   /* tile shape (0: default)         */
-    int32_t reserved;
+    int32_t p2p_warps, p2p_chunk, m2l_stages, m2l_split;   /* tile shape (0: default) */
 } imq_tune_entry;
 
 typedef struct imq_tune_result {
@@ -475,7 +477,8 @@ typedef struct imq_tune_result {
     int32_t n_tried;
     int32_t sampled_rows;
     int32_t translations;    /* the choice's imq_translations                      */
-    int32_t p2p_warps, p2p_chunk, m2l_stages;   /* the choice's tile shape         */
+    int32_t p2p_warps, p2p_chunk, m2l_stages, m2l_split;   /* the choice's tile shape */
+    int32_t reserved;
     imq_tune_entry tried[IMQ_TUNE_MAX_TRIED];
 } imq_tune_result;
 

@@ -36,7 +36,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class ImqOptions(ctypes.Structure):
     _fields_ = [("struct_size", I32), ("has_domain", I32), ("x0", D), ("y0", D), ("side", D),
                 ("check_duplicates", I32), ("m2l_kernel", I32), ("algorithm", I32), ("levels", I32),
-                ("translations", I32), ("p2p_warps", I32), ("p2p_chunk", I32), ("m2l_stages", I32), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", P)]
+                ("translations", I32), ("p2p_warps", I32), ("p2p_chunk", I32), ("m2l_stages", I32),
+                ("m2l_split", I32), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", P)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -61,13 +62,14 @@ class CgInfo(ctypes.Structure):
 class TuneEntry(ctypes.Structure):
     _fields_ = [("p", I32), ("leaf", I32), ("rel_err", D), ("matvec_ms", ctypes.c_float),
                 ("translations", I32), ("p2p_warps", I32), ("p2p_chunk", I32), ("m2l_stages", I32),
-                ("reserved", I32)]
+                ("m2l_split", I32)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("p", I32), ("leaf", I32), ("rel_err", D), ("matvec_ms", ctypes.c_float), ("met", I32),
                 ("n_tried", I32), ("sampled_rows", I32), ("translations", I32), ("p2p_warps", I32),
-                ("p2p_chunk", I32), ("m2l_stages", I32), ("tried", TuneEntry * 64)]
+                ("p2p_chunk", I32), ("m2l_stages", I32), ("m2l_split", I32), ("reserved", I32),
+                ("tried", TuneEntry * 64)]
 
 
 # name -> (restype, argtypes)

@@ -190,23 +190,25 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
                 fail(IMQ_UNSUPPORTED, "imq_plan: FP64 translations need the fast multipole form and p <= 16");
             if (trans64) *trans64 = opt->translations == IMQ_TRANS_FP64;
         }
-        if (opt->struct_size >= (int)(offsetof(imq_options, m2l_stages) + sizeof(int32_t))) {
+        if (opt->struct_size >= (int)(offsetof(imq_options, m2l_split) + sizeof(int32_t))) {
             if (opt->p2p_warps != 0 && opt->p2p_warps != 2 && opt->p2p_warps != 4 && opt->p2p_warps != 8)
                 fail(IMQ_INVALID_ARG, "imq_plan: p2p_warps must be 0, 2, 4 or 8");
             if (opt->p2p_chunk != 0 && opt->p2p_chunk != 8 && opt->p2p_chunk != 16 && opt->p2p_chunk != 32)
                 fail(IMQ_INVALID_ARG, "imq_plan: p2p_chunk must be 0, 8, 16 or 32");
             if (opt->m2l_stages != 0 && (opt->m2l_stages < 2 || opt->m2l_stages > 4))
                 fail(IMQ_INVALID_ARG, "imq_plan: m2l_stages must be 0 or 2..4");
+            if (opt->m2l_split < 0 || opt->m2l_split > 4) fail(IMQ_INVALID_ARG, "imq_plan: m2l_split must be 0..4");
         }
     }
 }
 
 // tile shapes of the FP32 product from the options (0: default)
 void plan_tiles(Plan &P, const imq_options *opt) {
-    if (opt && opt->struct_size >= (int)(offsetof(imq_options, m2l_stages) + sizeof(int32_t))) {
+    if (opt && opt->struct_size >= (int)(offsetof(imq_options, m2l_split) + sizeof(int32_t))) {
         P.p2p_warps = opt->p2p_warps;
         P.p2p_chunk = opt->p2p_chunk;
         P.m2l_stages = opt->m2l_stages;
+        P.m2l_split = opt->m2l_split;
     }
 }
 

@@ -151,12 +151,13 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     if (opt) std::memcpy(&base, opt, std::min(sizeof(base), (size_t)std::max(0, opt->struct_size)));
     base.struct_size = sizeof(imq_options);
     // build one configuration, measure its sampled error and best-of-3 time, record it
-    auto measure = [&](int p, int leaf, int trans, int warps, int chunk, int stages) -> int {
+    auto measure = [&](int p, int leaf, int trans, int warps, int chunk, int stages, int split) -> int {
         imq_options o = base;
         o.translations = trans;
         o.p2p_warps = warps;
         o.p2p_chunk = chunk;
         o.m2l_stages = stages;
+        o.m2l_split = split;
         PlanHolder plan;
         if (nprob == 1)
             check(imq_plan(d_pts.as<double>(), N, cvals[0], p, leaf, &o, s, &plan.h));
@@ -199,6 +200,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
         t.p2p_warps = warps;
         t.p2p_chunk = chunk;
         t.m2l_stages = stages;
+        t.m2l_split = split;
         return out->n_tried++;
     };
     // 1-2: the smallest p meeting the target per leaf size, FP32 translations first
@@ -207,7 +209,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
         for (int li = 0; li < n_leaf; ++li)
             for (int p : ps) {
                 if (trans == IMQ_TRANS_FP64 && p > 16) continue;
-                const int k = measure(p, leaf_cand[li], trans, 0, 0, 0);
+                const int k = measure(p, leaf_cand[li], trans, 0, 0, 0, 0);
                 if (k < 0) return any;
                 if (out->tried[k].rel_err <= target) {
                     any = true;
@@ -242,7 +244,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     int cur = best;
     for (int warps : {2, 4, 8})
         for (int chunk : {8, 16, 32}) {
-            const int k = measure(chosen.p, chosen.leaf, chosen.translations, warps, chunk, 0);
+            const int k = measure(chosen.p, chosen.leaf, chosen.translations, warps, chunk, 0, 0);
             if (better(k, cur)) cur = k;
         }
     const int K = (chosen.p + 1) * (chosen.p + 2) / 2;   // reals of the parity-reduced expansion
@@ -252,7 +254,14 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
         const int smax = m2l_umma_max_stages(K, K);
         const imq_tune_entry tp = out->tried[cur];
         for (int stages = 2; stages <= smax; ++stages) {
-            const int k = measure(chosen.p, chosen.leaf, chosen.translations, tp.p2p_warps, tp.p2p_chunk, stages);
+            const int k =
+                measure(chosen.p, chosen.leaf, chosen.translations, tp.p2p_warps, tp.p2p_chunk, stages, 0);
+            if (better(k, cur)) cur = k;
+        }
+        const imq_tune_entry ts = out->tried[cur];
+        for (int split = 1; split <= 4; ++split) {
+            const int k = measure(chosen.p, chosen.leaf, chosen.translations, ts.p2p_warps, ts.p2p_chunk,
+                                  ts.m2l_stages, split);
             if (better(k, cur)) cur = k;
         }
     }
@@ -265,6 +274,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     out->p2p_warps = w.p2p_warps;
     out->p2p_chunk = w.p2p_chunk;
     out->m2l_stages = w.m2l_stages;
+    out->m2l_split = w.m2l_split;
     out->sampled_rows = S;
     check_device_errors(s);   // a bounded wait that ran out would invalidate the measured errors
 }

@@ -693,7 +693,7 @@ static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
     if (P.m2l_kernel == IMQ_M2L_TENSOR && !fits)
         fail(IMQ_UNSUPPORTED, "imq_plan: the expansion does not fit the tensor-core M2L");
     if (P.m2l_kernel == IMQ_M2L_CUDA_CORES || !fits) return;
-    m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, O.m2l_tmask, s);
+    m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, O.m2l_tmask, O.m2l_order, O.m2l_counter, s);
     O.umma = true;
 }
 
@@ -1020,8 +1020,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             IMQ_LAUNCH_CHECK();
             ++launches;
         } else if (P.n_m2l_tiles > 0 && O.umma) {
-            m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s,
-                            fuse_pack);
+            m2l_umma_launch(P, M, L, O, K, s, fuse_pack);
             launches += fuse_pack ? 1 : 2;
         } else if (P.n_m2l_tiles > 0) {
             m2l_tiled_launch(P, M, L, m2l, s);
@@ -1094,7 +1093,7 @@ int fmm_apply(Plan &P, const T *us, T *bs, int nrhs, cudaStream_t s, PhaseTimer 
         t0(kPhM2L);
         if constexpr (std::is_same<T, float>::value) {
             if (P.n_m2l_tiles > 0 && O.umma) {
-                m2l_umma_launch(P, M, L, O.m2l_img.as<float>(), O.Mpk.as<float>(), O.m2l_tmask.as<uint64_t>(), K, s);
+                m2l_umma_launch(P, M, L, O, K, s);
                 launches += 2;
             } else if (P.n_m2l_tiles > 0) {
                 m2l_tiled_launch(P, M, L, m2l, s);

@@ -136,6 +136,7 @@ struct TypedOps {        // operator set in one precision
     bool dz_ready = false;
     // tensor-core M2L (FP32 only): swizzled tf32 hi/lo operator images, packed multipoles
     DevMem m2l_img, Mpk, m2l_tmask;   // m2l_tmask: uint64 per tile, bit o = offset class o present
+    DevMem m2l_order, m2l_counter;    // tiles heaviest first; the persistent kernel's work counter
     bool umma = false;
 };
 
@@ -220,7 +221,7 @@ struct Plan {
     bool trans64 = false; // FP32 product with M2M / M2L / L2L in FP64 (imq_options.translations)
     // tile shapes of the FP32 product (imq_options; 0 = default): P2P warps per CTA and
     // target chunk, tensor-core M2L pipeline stages
-    int p2p_warps = 0, p2p_chunk = 0, m2l_stages = 0;
+    int p2p_warps = 0, p2p_chunk = 0, m2l_stages = 0, m2l_split = 0;
     int tc_depth = 0;    // IMQ_ALG_TREECODE: depth of the uniform partition (paper's L + 1)
     int nprob = 1;       // batched plans: independent problems sharing one flattened tree
     DevMem box_prob;     // int32[nbox] problem of each box (batched plans only)
@@ -359,12 +360,13 @@ void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
-                      cudaStream_t s);
+                      DevMem &order, DevMem &counter, cudaStream_t s);
 // packed: Mpk already holds the hi / lo rows of every box (written by P2M and M2M)
-void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
-                     int Kout, cudaStream_t s, bool packed = false);
+void m2l_umma_launch(const Plan &P, const float *M, float *L, const TypedOps &O, int Kout, cudaStream_t s,
+                     bool packed = false);
 int m2l_umma_kp(int K);   // padded row length KP of the hi / lo rows
 int m2l_umma_max_stages(int K, int Kout);   // pipeline stages that fit in shared memory
+int m2l_default_split(int ntiles);          // CTAs per M2L tile when the plan does not choose
 // batch.cu
 template <class T>
 void generate_m2l_ops(const Layout &Lo, const Layout &Li, const std::vector<double2> &slot_hc, int Kp, DevMem &dst,

@@ -103,28 +103,40 @@ __global__ void k_m2l_images(const float *__restrict__ ops, int64_t nblk, int K,
 //              eight threads per 128-byte row, and arrive on the stage's
 //              barrier through cp.async.mbarrier.arrive.noinc; thread 128 also
 //              issues the bulk copy of the operator image;
-//   warp 8     lane 0 issues the 12 MMAs of each chunk into one of two TMEM
+//   warp 8     lane 0 issues the 12 MMAs of each chunk into one of NA TMEM
 //              accumulators and commits them to the stage's "empty" barrier and
 //              the accumulator's "full" barrier.
 // Barriers: full[S] (129 arrivals + image bytes), empty[S] (MMA commit),
 // acc_full[NA] (MMA commit), acc_empty[NA] (4 drain warps); NA accumulators
 // rotate so that the MMAs of chunk it wait only for the drain of chunk it - NA.
+// A work item is (tile, part): a tile's offset classes are split over nsplit
+// CTAs, which add their partial sums to L with one RED per element each.
 constexpr int kDrainThreads = 128, kProdThreads = 128;
 constexpr int kThreadsWS = kDrainThreads + kProdThreads + 32;
 
+constexpr int kRing = 16;   // tile records in flight between the roles (a tile has >= 1 chunk)
+
+// Persistent: one CTA per SM pulls work items (tile, part) in the plan's order
+// (heaviest first) from a device counter until none is left.  The producer
+// leader fetches an item, writes its record (tile, class list) into a ring
+// slot and arrives on the slot's barrier; the MMA issuer and the drain read
+// the record after waiting on that barrier.  Chunk counters run across tiles,
+// so the pipeline never drains between tiles, and TMEM and the barriers are
+// set up once per CTA.
 template <int S, int NC>
 __global__ void __launch_bounds__(kThreadsWS, 1)
-    k_m2l_umma(const int4 *__restrict__ tiles, const uint64_t *__restrict__ tmask, const int32_t *__restrict__ tbox,
-               const int32_t *__restrict__ vtab, const float *__restrict__ Mpk, float *__restrict__ L,
-               const float *__restrict__ img, int Kout, int Kn, int NKC, int *err) {
+    k_m2l_umma(const int4 *__restrict__ tiles, const uint64_t *__restrict__ tmask, const int32_t *__restrict__ order,
+               const int32_t *__restrict__ tbox, const int32_t *__restrict__ vtab, const float *__restrict__ Mpk,
+               float *__restrict__ L, const float *__restrict__ img, int Kout, int Kn, int NKC, int n_items,
+               int nsplit, int *counter, int *err) {
     constexpr uint32_t kAccCols = NC <= 2 ? 64 : NC <= 4 ? 128 : 256;   // columns per accumulator
     constexpr int NA = NC <= 4 ? 4 : 2;                                   // accumulators in rotation
     constexpr uint32_t kTCols = NA * kAccCols;                            // <= 512
     extern __shared__ unsigned char smraw[];
-    __shared__ int s_cls[kOffsetClasses];
-    __shared__ int s_ncls;
+    __shared__ int s_tix[kRing], s_ncls[kRing];
+    __shared__ int8_t s_cls[kRing][kOffsetClasses];
     __shared__ volatile int s_abort;
-    __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_accf[4], s_acce[4];
+    __shared__ __align__(8) uint64_t s_full[S], s_empty[S], s_accf[4], s_acce[4], s_ring[kRing];
     __shared__ uint32_t s_tmem;
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -133,8 +145,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     const uint32_t img_bytes = 2u * (uint32_t)Kn * 128u;
     const uint32_t stage_bytes = 2u * kAStage + img_bytes;
     const int KP = 32 * NKC;
-    const int4 tile = tiles[blockIdx.x];
-    const int blk = tile.x, b0 = tile.y, nbt = tile.z;
 
     if (w == 0) tmem_alloc(&s_tmem, kTCols);
     if (tid == 32) {
@@ -147,66 +157,60 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             mbar_init(&s_accf[i], 1);
             mbar_init(&s_acce[i], kDrainThreads / 32);
         }
+        for (int i = 0; i < kRing; ++i) mbar_init(&s_ring[i], 1);
         fence_mbar_init();
-    }
-    __syncthreads();
-    // producer thread r gathers chunk (r & 7) of rows (r >> 3) + 16 k, k < 8: it keeps
-    // those rows' target boxes in registers and reads each source from vtab
-    int tgt[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) tgt[k] = -1;
-    if (tid >= kDrainThreads && tid < kDrainThreads + kProdThreads) {
-        const int r = tid - kDrainThreads;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int row = (r >> 3) + 16 * k;
-            tgt[k] = row < nbt ? tbox[b0 + row] : -1;
-        }
-    }
-    if (tid == 0) {   // the offset classes present in the tile (bit o of the plan's tile mask)
-        const uint64_t mk = tmask[blockIdx.x];
-        int n = 0;
-        for (int o = 0; o < kOffsetClasses; ++o)
-            if ((mk >> o) & 1ull) s_cls[n++] = o;
-        s_ncls = n;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int nitems = s_ncls * NKC;
     bool ok = true;
 
     if (w < 4) {
         // ---------------------------------------------------------------- drain
-        float acc[NC * 32];
-#pragma unroll
-        for (int i = 0; i < NC * 32; ++i) acc[i] = 0.f;
         const uint32_t tl = tmem + ((uint32_t)(w * 32) << 16);
-        for (int it = 0; it < nitems; ++it) {
-            const bool got = mbar_wait(&s_accf[it % NA], (uint32_t)(it / NA) & 1u);
-            if (!__all_sync(0xFFFFFFFFu, got) || s_abort) {
+        int g = 0;   // chunk counter across tiles
+        for (int t = 0;; ++t) {
+            const int slot = t % kRing;
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(&s_ring[slot], (uint32_t)(t / kRing) & 1u)) || s_abort) {
                 ok = false;
                 break;
             }
-            tc_fence_after();
-            const uint32_t a = tl + (uint32_t)(it % NA) * kAccCols;
+            const int ncls = s_ncls[slot];
+            if (ncls < 0) break;
+            const int4 tile = tiles[s_tix[slot]];
+            float acc[NC * 32];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                float v[32];
-                tmem_ld32(a + (uint32_t)(c * 32), v);
+            for (int i = 0; i < NC * 32; ++i) acc[i] = 0.f;
+            // every 32-wide K chunk is drained and summed in FP32 registers: fewer partial sums
+            // accumulated inside the tensor core keep the tf32 products' precision
+            const int nitems = ncls * NKC;
+            for (int it = 0; it < nitems; ++it, ++g) {
+                const bool got = mbar_wait(&s_accf[g % NA], (uint32_t)(g / NA) & 1u);
+                if (!__all_sync(0xFFFFFFFFu, got) || s_abort) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a = tl + (uint32_t)(g % NA) * kAccCols;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+                for (int c = 0; c < NC; ++c) {
+                    float v[32];
+                    tmem_ld32(a + (uint32_t)(c * 32), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_acce[g % NA]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_acce[it % NA]);
-        }
-        if (ok && nitems > 0 && tid < nbt) {
-            float *Lb = L + (int64_t)tbox[b0 + tid] * Kout;
+            if (!ok) break;
+            if (tid < tile.z) {
+                float *Lb = L + (int64_t)tbox[tile.y + tid] * Kout;
 #pragma unroll
-            for (int i = 0; i < NC * 32; ++i)
-                if (i < Kout) atomicAdd(Lb + i, acc[i]);   // onto the P2L terms in L: a RED, no load
+                for (int i = 0; i < NC * 32; ++i)
+                    if (i < Kout) atomicAdd(Lb + i, acc[i]);   // onto the P2L terms in L: a RED, no load
+            }
         }
     } else if (w < 8) {
         // ---------------------------------------------------------------- producers
@@ -216,88 +220,140 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         const int r = tid - kDrainThreads;
         const int j = r & 7;
         const unsigned char *imgb = reinterpret_cast<const unsigned char *>(img);
-        // the sources of class ci + 1 are loaded while class ci's chunks are gathered, so
-        // the table lookup is off the producer's per-chunk path
-        int src[8], nxt[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            src[k] = -1;
-            nxt[k] = (tgt[k] >= 0 && nitems > 0) ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + s_cls[0]) : -1;
-        }
-        for (int it = 0; it < nitems; ++it) {
-            const int st = it % S;
-            if (s_abort || (it >= S && !mbar_wait(&s_empty[st], (uint32_t)((it / S) + 1) & 1u))) {
-                ok = false;
-                break;
-            }
-            const int ci = it / NKC, o = s_cls[ci], kc = it - ci * NKC;
-            if (kc == 0) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) src[k] = nxt[k];
-                if (ci + 1 < s_ncls) {
-                    const int o1 = s_cls[ci + 1];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        nxt[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + o1) : -1;
-                }
-            }
-            const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
+        int g = 0;
+        for (int t = 0;; ++t) {
+            const int slot = t % kRing;
             if (r == 0) {
-                mbar_arrive_expect_tx(&s_full[st], img_bytes);
-                bulk_g2s(smraw + (sa - raw0) + 2 * kAStage,
-                         imgb + (((size_t)blk * kOffsetClasses + o) * NKC + kc) * (size_t)img_bytes, img_bytes,
-                         &s_full[st]);
+                // next work item with at least one class (empty ones are skipped here)
+                int ncls = -1, tix = 0;
+                for (;;) {
+                    const int item = s_abort ? n_items : atomicAdd(counter, 1);
+                    if (item >= n_items) break;
+                    tix = order[item / nsplit];
+                    const int part = item - (item / nsplit) * nsplit;
+                    const uint64_t mk = tmask[tix];
+                    const int all = __popcll(mk);
+                    const int c0 = (all * part) / nsplit, c1 = (all * (part + 1)) / nsplit;
+                    int n = 0, k = 0;
+                    for (int o = 0; o < kOffsetClasses; ++o)
+                        if ((mk >> o) & 1ull) {
+                            if (k >= c0 && k < c1) s_cls[slot][n++] = (int8_t)o;
+                            ++k;
+                        }
+                    if (n > 0) {
+                        ncls = n;
+                        break;
+                    }
+                }
+                s_tix[slot] = tix;
+                s_ncls[slot] = ncls;
+                mbar_arrive(&s_ring[slot]);   // release: the record is visible to whoever waits on it
             }
-            // 8 consecutive threads fetch the 8 16-byte chunks of one 128-byte row, so a
-            // warp instruction reads 4 whole rows (full sectors) rather than 32 fragments
+            asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");   // producers only
+            const int ncls = s_ncls[slot];
+            if (ncls < 0) break;
+            const int4 tile = tiles[s_tix[slot]];
+            const int blk = tile.x, b0 = tile.y, nbt = tile.z;
+            // producer thread r gathers chunk (r & 7) of rows (r >> 3) + 16 k, k < 8
+            int tgt[8], src[8], nxt[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int row = (r >> 3) + 16 * k;
-                const int sb = src[k];
-                const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)j);
-                if (sb >= 0) {
-                    const float *mh = Mpk + (int64_t)sb * 2 * KP + kc * 32 + 4 * j;
-                    cp_async16(sa + off, mh);
-                    cp_async16(sa + kAStage + off, mh + KP);
-                } else {
-                    cp_async16_zero(sa + off, Mpk);
-                    cp_async16_zero(sa + kAStage + off, Mpk);
-                }
+                tgt[k] = row < nbt ? tbox[b0 + row] : -1;
+                src[k] = -1;
+                nxt[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + s_cls[slot][0]) : -1;
             }
-            cp_async_arrive_noinc(&s_full[st]);
+            const int nitems = ncls * NKC;
+            for (int it = 0; it < nitems; ++it, ++g) {
+                const int st = g % S;
+                if (s_abort || (g >= S && !mbar_wait(&s_empty[st], (uint32_t)((g / S) + 1) & 1u))) {
+                    ok = false;
+                    break;
+                }
+                const int ci = it / NKC, o = s_cls[slot][ci], kc = it - ci * NKC;
+                if (kc == 0) {   // the next class's sources are loaded while this class is gathered
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) src[k] = nxt[k];
+                    if (ci + 1 < ncls) {
+                        const int o1 = s_cls[slot][ci + 1];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            nxt[k] = tgt[k] >= 0 ? __ldg(vtab + (int64_t)kOffsetClasses * tgt[k] + o1) : -1;
+                    }
+                }
+                const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
+                if (r == 0) {
+                    mbar_arrive_expect_tx(&s_full[st], img_bytes);
+                    bulk_g2s(smraw + (sa - raw0) + 2 * kAStage,
+                             imgb + (((size_t)blk * kOffsetClasses + o) * NKC + kc) * (size_t)img_bytes, img_bytes,
+                             &s_full[st]);
+                }
+                // 8 consecutive threads fetch the 8 16-byte chunks of one 128-byte row, so a
+                // warp instruction reads 4 whole rows (full sectors) rather than 32 fragments
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int row = (r >> 3) + 16 * k;
+                    const int sb = src[k];
+                    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)j);
+                    if (sb >= 0) {
+                        const float *mh = Mpk + (int64_t)sb * 2 * KP + kc * 32 + 4 * j;
+                        cp_async16(sa + off, mh);
+                        cp_async16(sa + kAStage + off, mh + KP);
+                    } else {
+                        cp_async16_zero(sa + off, Mpk);
+                        cp_async16_zero(sa + kAStage + off, Mpk);
+                    }
+                }
+                cp_async_arrive_noinc(&s_full[st]);
+            }
+            // a failed wait sets s_abort (below) and the leader then hands out no more tiles: the
+            // producers leave the loop together, right after the named barrier, so none of them
+            // waits at that barrier for one that has left
+            if (!ok) s_abort = 1;
         }
         cp_async_wait<0>();
     } else if (lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
         const uint32_t idesc = umma_idesc_tf32(kTB, (uint32_t)Kn);
-        for (int it = 0; it < nitems; ++it) {
-            const int st = it % S;
-            if (s_abort || !mbar_wait(&s_full[st], (uint32_t)(it / S) & 1u) ||
-                (it >= NA && !mbar_wait(&s_acce[it % NA], (uint32_t)((it / NA) + 1) & 1u))) {
+        int g = 0;
+        for (int t = 0; ok; ++t) {
+            const int slot = t % kRing;
+            if (s_abort || !mbar_wait(&s_ring[slot], (uint32_t)(t / kRing) & 1u)) {
                 ok = false;
                 break;
             }
-            // the A rows were written by cp.async (generic proxy); the MMA reads them
-            // through the async proxy
-            fence_proxy_async_smem();
-            tc_fence_after();
-            const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
-            const uint32_t bh = sa + 2 * kAStage, bl = bh + (uint32_t)Kn * 128u;
-            const uint32_t d = tmem + (uint32_t)(it % NA) * kAccCols;
+            const int ncls = s_ncls[slot];
+            if (ncls < 0) break;
+            const int nitems = ncls * NKC;
+            for (int it = 0; it < nitems; ++it, ++g) {
+                const int st = g % S;
+                if (s_abort || !mbar_wait(&s_full[st], (uint32_t)(g / S) & 1u) ||
+                    (g >= NA && !mbar_wait(&s_acce[g % NA], (uint32_t)((g / NA) + 1) & 1u))) {
+                    ok = false;
+                    break;
+                }
+                // the A rows were written by cp.async (generic proxy); the MMA reads them
+                // through the async proxy
+                fence_proxy_async_smem();
+                tc_fence_after();
+                const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
+                const uint32_t bh = sa + 2 * kAStage, bl = bh + (uint32_t)Kn * 128u;
+                const uint32_t d = tmem + (uint32_t)(g % NA) * kAccCols;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t dah = umma_desc_sw128(sa + 32 * ks), dal = umma_desc_sw128(sa + kAStage + 32 * ks);
-                const uint64_t dbh = umma_desc_sw128(bh + 32 * ks), dbl = umma_desc_sw128(bl + 32 * ks);
-                umma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                umma_tf32(d, dah, dbl, idesc, 1u);
-                umma_tf32(d, dal, dbh, idesc, 1u);
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t dah = umma_desc_sw128(sa + 32 * ks), dal = umma_desc_sw128(sa + kAStage + 32 * ks);
+                    const uint64_t dbh = umma_desc_sw128(bh + 32 * ks), dbl = umma_desc_sw128(bl + 32 * ks);
+                    umma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    umma_tf32(d, dah, dbl, idesc, 1u);
+                    umma_tf32(d, dal, dbh, idesc, 1u);
+                }
+                umma_commit(&s_empty[st]);
+                umma_commit(&s_accf[g % NA]);
             }
-            umma_commit(&s_empty[st]);
-            umma_commit(&s_accf[it % NA]);
         }
         // the last commits must land before the CTA releases its TMEM
-        if (ok && nitems > 0) {
-            const int last = nitems - 1;
+        if (ok && g > 0) {
+            const int last = g - 1;
             if (!mbar_wait(&s_empty[last % S], (uint32_t)(last / S) & 1u)) ok = false;
         }
     }
@@ -338,7 +394,7 @@ bool m2l_umma_supported(int K, int Kout) {
 }
 
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
-                      cudaStream_t s) {
+                      DevMem &order, DevMem &counter, cudaStream_t s) {
     const int K = P.layout.K;
     const UmmaDims d = umma_dims(K, Kout);
     const int Kp = 16 * m2l_tiled_rows(Kout);
@@ -351,39 +407,77 @@ void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMe
     Mpk.alloc(sizeof(float) * (size_t)P.nbox * 2 * d.KP);
     // the pads past K stay zero: the fused writers (P2M, M2M) store only the first K of each half
     IMQ_CUDA(cudaMemsetAsync(Mpk.ptr, 0, sizeof(float) * (size_t)P.nbox * 2 * d.KP, s));
-    tmask.alloc(sizeof(uint64_t) * (size_t)std::max(1, P.n_m2l_tiles));
+    const int nt = std::max(1, P.n_m2l_tiles);
+    tmask.alloc(sizeof(uint64_t) * (size_t)nt);
+    order.alloc(sizeof(int32_t) * (size_t)nt);
+    counter.alloc(sizeof(int32_t));
     if (P.n_m2l_tiles > 0) {
         k_tile_masks<<<(P.n_m2l_tiles + 3) / 4, 128, 0, s>>>(P.m2l_tiles.as<int4>(), P.n_m2l_tiles,
                                                             P.m2l_tbox.as<int32_t>(), P.vtab.as<int32_t>(),
                                                             tmask.as<uint64_t>());
         IMQ_LAUNCH_CHECK();
+        // the persistent kernel takes tiles heaviest first (classes x boxes), so the last
+        // ones to start are the short ones
+        std::vector<uint64_t> mk(P.n_m2l_tiles);
+        std::vector<int4> tl(P.n_m2l_tiles);
+        IMQ_CUDA(cudaMemcpyAsync(mk.data(), tmask.ptr, sizeof(uint64_t) * mk.size(), cudaMemcpyDeviceToHost, s));
+        IMQ_CUDA(cudaMemcpyAsync(tl.data(), P.m2l_tiles.ptr, sizeof(int4) * tl.size(), cudaMemcpyDeviceToHost, s));
+        IMQ_CUDA(cudaStreamSynchronize(s));
+        std::vector<int32_t> ord(P.n_m2l_tiles);
+        for (int t = 0; t < P.n_m2l_tiles; ++t) ord[t] = t;
+        auto cost = [&](int t) { return (int64_t)__builtin_popcountll(mk[t]) * tl[t].z; };
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        IMQ_CUDA(cudaMemcpyAsync(order.ptr, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, s));
+        IMQ_CUDA(cudaStreamSynchronize(s));
     }
 }
 
 int m2l_umma_kp(int K) { return 32 * ((K + 31) / 32); }
 
+int m2l_default_split(int ntiles) {
+    // measured at N = 1M clustered (384 tiles): splitting a tile's classes over more CTAs adds
+    // per-CTA set-up and RED traffic faster than it evens out the last wave; the autotuner
+    // measures other splits
+    (void)ntiles;
+    return 1;
+}
+
 int m2l_umma_max_stages(int K, int Kout) { return umma_dims(K, Kout).stages; }
 
-void m2l_umma_launch(const Plan &P, const float *M, float *L, const float *img, float *Mpk, const uint64_t *tmask,
-                     int Kout, cudaStream_t s, bool packed) {
+void m2l_umma_launch(const Plan &P, const float *M, float *L, const TypedOps &O, int Kout, cudaStream_t s,
+                     bool packed) {
     if (P.n_m2l_tiles == 0) return;
     const int K = P.layout.K;
     UmmaDims d = umma_dims(K, Kout);
     // the plan's tile choice: fewer pipeline stages than fit (never more)
     if (P.m2l_stages >= 2 && P.m2l_stages < d.stages) d.stages = P.m2l_stages;
+    float *Mpk = O.Mpk.as<float>();
     if (!packed) {
         k_pack_m<<<blocks_for((int64_t)P.nbox * d.KP, 256), 256, 0, s>>>(M, P.nbox, K, d.KP, Mpk);
         IMQ_LAUNCH_CHECK();
     }
     const size_t smem = d.smem();
     int *err = device_error_word();
+    // classes of a tile split over nsplit work items: the plan's choice, else one per tile
+    const int nsplit = P.m2l_split > 0 ? P.m2l_split : m2l_default_split(P.n_m2l_tiles);
+    const int n_items = P.n_m2l_tiles * nsplit;
+    static int n_sm[64] = {0};
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && n_sm[dev] == 0)
+        IMQ_CUDA(cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(n_items, (dev >= 0 && dev < 64 && n_sm[dev] > 0) ? n_sm[dev] : 152);
+    int *counter = O.m2l_counter.as<int>();
+    IMQ_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    const float *img = O.m2l_img.as<float>();
+    const uint64_t *tmask = O.m2l_tmask.as<uint64_t>();
+    const int32_t *order = O.m2l_order.as<int32_t>();
 #define IMQ_UMMA_CASE(SS, NCC)                                                                                    \
     if (d.stages == SS && d.tcols == NCC) {                                                                      \
         IMQ_CUDA(cudaFuncSetAttribute(k_m2l_umma<SS, NCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_m2l_umma<SS, NCC><<<P.n_m2l_tiles, kThreadsWS, smem, s>>>(P.m2l_tiles.as<int4>(), tmask,              \
-                                                                 P.m2l_tbox.as<int32_t>(),                         \
-                                                                 P.vtab.as<int32_t>(), Mpk, L, img, Kout, d.Kn,    \
-                                                                 d.NKC, err);                                      \
+        k_m2l_umma<SS, NCC><<<grid, kThreadsWS, smem, s>>>(P.m2l_tiles.as<int4>(), tmask, order,                  \
+                                                           P.m2l_tbox.as<int32_t>(), P.vtab.as<int32_t>(), Mpk, L,  \
+                                                           img, Kout, d.Kn, d.NKC, n_items, nsplit, counter, err); \
         launched = true;                                                                                          \
     }
     bool launched = false;

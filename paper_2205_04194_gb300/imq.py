@@ -79,7 +79,7 @@ TRANSLATIONS = {"fp32": 0, "fp64": 1}
 
 
 def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0,
-                  allocator=None, translations="fp32", p2p_warps=0, p2p_chunk=0, m2l_stages=0):
+                  allocator=None, translations="fp32", p2p_warps=0, p2p_chunk=0, m2l_stages=0, m2l_split=0):
     opt = ImqOptions()
     opt.struct_size = ctypes.sizeof(ImqOptions)
     if allocator is not None:
@@ -93,6 +93,7 @@ def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algori
     opt.levels = int(levels)
     opt.translations = TRANSLATIONS[translations]
     opt.p2p_warps, opt.p2p_chunk, opt.m2l_stages = int(p2p_warps), int(p2p_chunk), int(m2l_stages)
+    opt.m2l_split = int(m2l_split)
     return opt
 
 
@@ -105,14 +106,15 @@ class Plan:
     def __init__(self, points, c: float, p: int, leaf: int, domain=None,
                  check_duplicates: bool = False, stream=None, m2l_kernel: str = "auto",
                  algorithm: str = "fmm", levels: int = 0, allocator: str | None = None,
-                 translations: str = "fp32", p2p_warps: int = 0, p2p_chunk: int = 0, m2l_stages: int = 0):
+                 translations: str = "fp32", p2p_warps: int = 0, p2p_chunk: int = 0, m2l_stages: int = 0,
+                 m2l_split: int = 0):
         self._h = ctypes.c_void_p(0)
         # allocator="torch": the plan's own buffers come from torch's caching allocator
         self._alloc_cbs = _torch_allocator() if allocator == "torch" else None
         pts_ptr, keep = _buf(points, torch.float64)
         n = int(np.shape(points)[0])
         opt = _plan_options(domain, check_duplicates, m2l_kernel, algorithm, levels, self._alloc_cbs,
-                            translations, p2p_warps, p2p_chunk, m2l_stages)
+                            translations, p2p_warps, p2p_chunk, m2l_stages, m2l_split)
         call("imq_plan", pts_ptr, n, float(c), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
         del keep
@@ -307,7 +309,7 @@ class BatchedPlan(Plan):
 
     def __init__(self, points_list, c_list, p: int, leaf: int, domain=None, stream=None,
                  m2l_kernel: str = "auto", translations: str = "fp32", p2p_warps: int = 0, p2p_chunk: int = 0,
-                 m2l_stages: int = 0):
+                 m2l_stages: int = 0, m2l_split: int = 0):
         self._h = ctypes.c_void_p(0)
         sizes = [int(np.shape(x)[0]) for x in points_list]
         offs = np.zeros(len(sizes) + 1, dtype=np.int64)
@@ -319,7 +321,7 @@ class BatchedPlan(Plan):
         cs = np.ascontiguousarray(np.asarray(c_list, dtype=np.float64))
         pp, kp = _buf(pts, torch.float64)
         opt = _plan_options(domain, False, m2l_kernel, translations=translations, p2p_warps=p2p_warps,
-                            p2p_chunk=p2p_chunk, m2l_stages=m2l_stages)
+                            p2p_chunk=p2p_chunk, m2l_stages=m2l_stages, m2l_split=m2l_split)
         call("imq_plan_batched", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes),
              ctypes.c_void_p(cs.ctypes.data), int(p), int(leaf), ctypes.byref(opt), _stream(stream),
              ctypes.byref(self._h))
@@ -411,7 +413,7 @@ def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
     def entry(t):
         return {"p": t.p, "leaf": t.leaf, "rel_err": t.rel_err, "matvec_ms": t.matvec_ms,
                 "translations": names[t.translations], "p2p_warps": t.p2p_warps, "p2p_chunk": t.p2p_chunk,
-                "m2l_stages": t.m2l_stages}
+                "m2l_stages": t.m2l_stages, "m2l_split": t.m2l_split}
 
     tried = [entry(res.tried[k]) for k in range(res.n_tried)]
     out = entry(res)
@@ -421,7 +423,7 @@ def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
 
 def tiles_of(tune: dict) -> dict:
     """Plan keyword arguments (translations and tile shapes) of an autotune result."""
-    return {k: tune[k] for k in ("translations", "p2p_warps", "p2p_chunk", "m2l_stages")}
+    return {k: tune[k] for k in ("translations", "p2p_warps", "p2p_chunk", "m2l_stages", "m2l_split")}
 
 
 def sync_check(stream=None) -> None:

@@ -39,7 +39,7 @@ def _imq():
 def _phase1(res, translations="fp32"):
     """Entries of the (p, leaf) search: default tile shapes."""
     return [t for t in res["tried"] if t["translations"] == translations and t["p2p_warps"] == 0
-            and t["p2p_chunk"] == 0 and t["m2l_stages"] == 0]
+            and t["p2p_chunk"] == 0 and t["m2l_stages"] == 0 and t["m2l_split"] == 0]
 
 
 def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
@@ -62,16 +62,19 @@ def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
         assert ps == sorted(ps) and ps[0] == 4
         # ascending p until the first that meets the target
         assert all(t["rel_err"] > target for t in tried[:-1]) and tried[-1]["rel_err"] <= target
-    # every measured configuration, tile shapes included, reproduced against the oracle rows
+    # every measured configuration, tile shapes included, reproduced against the oracle rows; with
+    # m2l_split > 1 several CTAs add partial sums into the same locals, so the order of those FP32
+    # additions (and the last bits of the product) varies from run to run
     for t in res["tried"]:
         plan = imq.Plan(cuda(pts), c, t["p"], t["leaf"], **imq.tiles_of(t))
         b = host(plan.matvec(cuda(v, torch.float32)))
         err = np.linalg.norm(b[rows] - exact) / np.linalg.norm(exact)
-        assert err == pytest.approx(t["rel_err"], rel=1e-3), (t, err)
+        assert err == pytest.approx(t["rel_err"], rel=1e-3 if t["m2l_split"] <= 1 else 3e-2), (t, err)
         plan.close()
     # the tile sweep ran on the (p, leaf) choice: 9 P2P shapes, then the M2L pipeline depths
     tiles = [t for t in res["tried"] if t not in _phase1(res)]
-    assert len([t for t in tiles if t["m2l_stages"] == 0]) == 9
+    assert len([t for t in tiles if t["m2l_stages"] == 0 and t["m2l_split"] == 0]) == 9
+    assert sorted(t["m2l_split"] for t in tiles if t["m2l_split"] > 0) == [1, 2, 3, 4]
     assert all(t["p"] == res["p"] and t["leaf"] == res["leaf"] for t in tiles)
     # the result is the fastest measured configuration of that choice that meets the target
     same = [t for t in res["tried"] if t["p"] == res["p"] and t["leaf"] == res["leaf"] and t["rel_err"] <= target]
