@@ -729,6 +729,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
             if (RR < 0) fail(IMQ_UNSUPPORTED, "expansion order too large for the M2L kernel");
             generate_m2l_ops<float>(P.layout, P.layout, P.h_slot_hc, 16 * RR, O.m2l, s);
             prepare_tensor_m2l(P, O, (int)P.h_slot_hc.size(), s);
+            ensure_m2p_items(P, s);
         }
         O.ready = true;
         return;
@@ -767,6 +768,7 @@ void ensure_ops(Plan &P, bool fp64, cudaStream_t s) {
                 for (int r = 0; r < K; ++r) pad[(blk * K + i) * Kp + r] = P.h_m2l[(blk * K + i) * K + r];
         upload<float>(O.m2l, pad, s);
         prepare_tensor_m2l(P, O, std::max(1, nlev), s);
+        ensure_m2p_items(P, s);   // also the P2P leaf order (host work, here before any stream capture)
     }
     O.ready = true;
 }
@@ -945,7 +947,11 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     const float *m2m = O.m2m.as<float>(), *l2l = O.l2l.as<float>(), *m2l = O.m2l.as<float>(),
                 *coef = O.p2mc.as<float>();
     ensure_m2p_items(P, s0);
-    if (!P.near.ptr) P.near.alloc(sizeof(float) * (size_t)P.N);
+    // the near field of every right-hand side comes from one P2P pass (one kernel value per pair
+    // serves four right-hand sides); the buffers grow outside any stream capture (the CG
+    // solvers capture single right-hand-side products only)
+    if (P.near.bytes < sizeof(float) * (size_t)P.N * nrhs) P.near.alloc(sizeof(float) * (size_t)P.N * nrhs);
+    if (nrhs > 2 && !P.rec4b.ptr) P.rec4b.alloc(sizeof(float4) * (size_t)P.N);
     // the tensor-core M2L's tf32 hi / lo rows are written by P2M and M2M themselves
     // (both fixed-order / shared-memory kernels), so no packing pass sits on the chain
     // FP64 translations: the multipoles are widened after P2M, translated (M2M, M2L, L2L) in FP64
@@ -964,6 +970,13 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     int launches = 0;
     auto t0 = [&](int ph) { if (tm) tm->start(ph, s0); };
     auto t1 = [&]() { if (tm) tm->stop(s0); };
+    const int p2p_launches = 2 * ((nrhs + 3) / 4);
+    if (!conc) {
+        t0(kPhP2P);
+        p2p_near_f32(P, us, near, nrhs, s0);
+        launches += p2p_launches;
+        t1();
+    }
     for (int r = 0; r < nrhs; ++r) {
         const float *u = us + (size_t)r * P.N;
         float *b = bs + (size_t)r * P.N;
@@ -978,8 +991,10 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
                 ++launches;
             }
             IMQ_CUDA(cudaEventRecord(P.aux.xready, sa));
-            p2p_near_f32(P, u, near, sa);
-            launches += 2;
+            if (r == 0) {
+                p2p_near_f32(P, us, near, nrhs, sa);
+                launches += p2p_launches;
+            }
         }
         t0(kPhP2M);
         p2m_launch<float>(P, u, M, coef, s, fuse_pack ? O.Mpk.as<float>() : nullptr, kp_pack);
@@ -1037,12 +1052,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             l2l_launch<float>(P, L, l2l, K, s, &launches);
         }
         t1();
-        if (!conc) {
-            t0(kPhP2P);
-            p2p_near_f32(P, u, near, s);
-            launches += 2;
-            t1();
-        }
+
         t0(kPhFar);
         if (conc) {
             IMQ_CUDA(cudaStreamWaitEvent(s, P.aux.join, 0));
@@ -1050,7 +1060,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
             far_m2p_launch(P, M, s);
             if (P.n_m2p_items > 0) ++launches;
         }
-        far_l2p_launch(P, L, coef, near, b, s);
+        far_l2p_launch(P, L, coef, near + (size_t)r * P.N, b, s);
         ++launches;
         t1();
         if (conc) {

@@ -26,6 +26,8 @@
 #include "f32x2.cuh"
 #include "fixed_order.cuh"
 #include "fmm_common.cuh"
+#include <algorithm>
+
 #include "imq_internal.h"
 #include "util.cuh"
 
@@ -173,7 +175,9 @@ __global__ void __launch_bounds__(32 * kFarWarps, (P <= 12 ? 4 : 2)) k_l2p_t(
 void ensure_m2p_items(Plan &P, cudaStream_t s) {
     if (P.n_m2p_items >= 0) return;
     const int nl = P.nleaf;
-    std::vector<int32_t> leaves(nl), beg(P.nbox), en(P.nbox), woff(P.nbox + 1), witems(std::max<int64_t>(1, P.W.total));
+    std::vector<int32_t> leaves(nl), beg(P.nbox), en(P.nbox), woff(P.nbox + 1), witems(std::max<int64_t>(1, P.W.total)),
+        utot(P.nbox);
+    IMQ_CUDA(cudaMemcpyAsync(utot.data(), P.utot.ptr, 4 * (size_t)P.nbox, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(leaves.data(), P.leaves.ptr, 4 * (size_t)nl, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(beg.data(), P.begin.ptr, 4 * (size_t)P.nbox, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(en.data(), P.end.ptr, 4 * (size_t)P.nbox, cudaMemcpyDeviceToHost, s));
@@ -195,6 +199,15 @@ void ensure_m2p_items(Plan &P, cudaStream_t s) {
             }
     }
     if (off > 0x7FFFFFFF) fail(IMQ_UNSUPPORTED, "far field: too many M2P partial sums");
+    // the persistent P2P kernel pulls leaves in this order: most pairs first, so the last ones
+    // to start are short
+    std::vector<int32_t> ord(nl);
+    for (int k = 0; k < nl; ++k) ord[k] = k;
+    auto pairs = [&](int k) { return (int64_t)(en[leaves[k]] - beg[leaves[k]]) * utot[leaves[k]]; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return pairs(a) > pairs(b); });
+    P.p2p_order.alloc(4 * (size_t)std::max(1, nl));
+    P.p2p_counter.alloc(sizeof(int32_t));
+    if (nl > 0) IMQ_CUDA(cudaMemcpyAsync(P.p2p_order.ptr, ord.data(), 4 * (size_t)nl, cudaMemcpyHostToDevice, s));
     P.m2p_items.alloc(sizeof(int4) * std::max<size_t>(1, items.size()));
     P.wbase.alloc(4 * (size_t)std::max(1, nl));
     P.wpart.alloc(4 * (size_t)std::max<int64_t>(32, off));

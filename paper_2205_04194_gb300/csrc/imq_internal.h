@@ -259,14 +259,17 @@ struct Plan {
     // points, device, sorted order
     DevMem pos;        // double2[N]
     DevMem loc;        // float2[N]  offset from the leaf centre
-    DevMem rec4;       // float4[N]  P2P source records (x, y, u, 0) of the current product
+    DevMem rec4;       // float4[N]  P2P source records (x, y, u0, u1) of the current product
+    DevMem rec4b;      // float4[N]  (u2, u3, 0, 0) for three or four right-hand sides at once
+    DevMem p2p_order;  // int32[nleaf] leaves by P2P pair count, most first
+    DevMem p2p_counter;// int32 work counter of the persistent P2P kernel
     DevMem leaf_of;    // int32[N]
     // far field (FP32, fixed p): M2P items (leaf, W source, first point, partial offset)
     DevMem m2p_items;  // int4[n_m2p_items]
     DevMem wbase;      // int32[nleaf] offset of each leaf's M2P partial sums
     DevMem wpart;      // float[32 * n_m2p_items] partial sums, W-entry major then 32-point chunk
     int n_m2p_items = -1;   // -1: not built yet
-    DevMem near;       // float[N] near-field (P2P) sums of the current FP32 product
+    DevMem near;       // float[nrhs * N] near-field (P2P) sums of the current FP32 product
     AuxStream aux;     // the P2P / M2P stream of the concurrent FP32 product
     // operators
     std::vector<double> h_m2m, h_l2l, h_m2l, h_p2mc;   // FP64 host copies (h_m2l: [lev][40][K][K])
@@ -356,7 +359,8 @@ void far_m2p_launch(Plan &P, const float *M, cudaStream_t s);   // W-list M2P pa
 // b = L2P + the leaf's M2P partial sums (+ near[i] if near is not null)
 void far_l2p_launch(Plan &P, const float *L, const float *coef, const float *near, float *b, cudaStream_t s);
 // p2p.cu: near[i] = the P2P sum of point i (FP32, stored, not added)
-void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s);
+// u, near: [nrhs][N]; one kernel value per pair serves up to four right-hand sides
+void p2p_near_f32(Plan &P, const float *u, float *near, int nrhs, cudaStream_t s);
 // m2l_umma.cu: tensor-core M2L over the same tiles (value path, FP32 in and out)
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,

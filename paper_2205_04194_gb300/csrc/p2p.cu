@@ -21,6 +21,7 @@
 // x_j = loc_j + (c_s - c_t) becomes loc_j - delta with delta = c_t - c_s
 // rounded once from FP64, so the pair difference carries O(eps * box side)
 // error instead of O(eps * |x|).
+#include <algorithm>
 #include <type_traits>
 
 #include "f32x2.cuh"
@@ -61,38 +62,45 @@ __device__ __forceinline__ int source_index(int q, int &r, int u1, const int32_t
     return begin[uitems[r]] + (q - ucum[r]);
 }
 
-// Per product: one 16-byte record (x, y, u, 0) per sorted point, x and y the
-// offset from the point's leaf centre.
-__global__ void k_pack_records(const float2 *__restrict__ loc, const float *__restrict__ u, int64_t n,
-                               float4 *__restrict__ rec) {
+// Per product: 16-byte records per sorted point, x and y the offset from the
+// point's leaf centre: rec = (x, y, u0, u1) (u1 = 0 for one right-hand side) and,
+// for up to four right-hand sides, recb = (u2, u3, 0, 0).
+__global__ void k_pack_records(const float2 *__restrict__ loc, const float *__restrict__ u, int64_t n, int nr,
+                               float4 *__restrict__ rec, float4 *__restrict__ recb) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) {
         const float2 l = loc[i];
-        rec[i] = make_float4(l.x, l.y, u[i], 0.f);
+        rec[i] = make_float4(l.x, l.y, u[i], nr > 1 ? u[n + i] : 0.f);
+        if (nr > 2) recb[i] = make_float4(u[2 * n + i], nr > 3 ? u[3 * n + i] : 0.f, 0.f, 0.f);
     }
 }
 
-constexpr int kStageCap = 512;    // source records staged per warp at a time (8 KB)
+constexpr int kStageCap = 512;    // source records staged per warp at a time (8 KB per record array)
 
+template <int NR>
 struct WarpStage {
     float4 rec[kStageCap];
+    float4 recb[NR > 2 ? kStageCap : 1];
     uint64_t bar;
 };
 
 // Stage concatenated positions [q0, q0 + len) of the U-list sources of one leaf
-// into shared memory with 1-D TMA bulk copies, one per overlapping U entry, the
-// entries spread over the lanes (lane e sets up entry u0 + e, u0 + e + 32, ...);
-// wait for them (bounded), then shift each entry's records into the target
-// leaf's frame, the entry bounds and offset broadcast from the lane that loaded
-// them.  St: total source count of the leaf.  Returns false if the wait timed out.
-__device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, int q0, int len, int u0, int u1, int St,
-                                              const int32_t *__restrict__ begin, const int32_t *__restrict__ uitems,
-                                              const int32_t *__restrict__ ucum, const float2 *__restrict__ udelta,
-                                              const float4 *__restrict__ rec, int lane, int *err) {
+// into shared memory with 1-D TMA bulk copies, one per overlapping U entry and
+// record array, the entries spread over the lanes (lane e sets up entry u0 + e,
+// u0 + e + 32, ...); wait for them (bounded), then shift each entry's records
+// into the target leaf's frame, the entry bounds and offset broadcast from the
+// lane that loaded them.  St: total source count of the leaf.  Returns false if
+// the wait timed out.
+template <int NR>
+__device__ __forceinline__ bool stage_sources(WarpStage<NR> &ws, uint32_t &phase, int q0, int len, int u0, int u1,
+                                              int St, const int32_t *__restrict__ begin,
+                                              const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
+                                              const float2 *__restrict__ udelta, const float4 *__restrict__ rec,
+                                              const float4 *__restrict__ recb, int lane, int *err) {
     if (lane == 0) {
         // earlier generic-proxy writes to ws.rec must be ordered before the async-proxy copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&ws.bar, (uint32_t)len * 16u);
+        mbar_arrive_expect_tx(&ws.bar, (uint32_t)len * 16u * (NR > 2 ? 2u : 1u));
     }
     __syncwarp();
     int my_lo = 0, my_hi = 0;
@@ -106,7 +114,11 @@ __device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, in
             my_d = udelta[r];
         }
         const int a = max(lo, q0), bnd = min(hi, q0 + len);
-        if (a < bnd) bulk_g2s(&ws.rec[a - q0], rec + begin[uitems[r]] + (a - lo), (uint32_t)(bnd - a) * 16u, &ws.bar);
+        if (a < bnd) {
+            const int64_t src = begin[uitems[r]] + (a - lo);
+            bulk_g2s(&ws.rec[a - q0], rec + src, (uint32_t)(bnd - a) * 16u, &ws.bar);
+            if (NR > 2) bulk_g2s(&ws.recb[a - q0], recb + src, (uint32_t)(bnd - a) * 16u, &ws.bar);
+        }
     }
     const bool ok = mbar_wait(&ws.bar, phase & 1u);
     phase++;
@@ -140,13 +152,21 @@ __device__ __forceinline__ bool stage_sources(WarpStage &ws, uint32_t &phase, in
     return true;
 }
 
-template <int TC>
-__device__ __forceinline__ void p2p_tile_f32(const float4 *__restrict__ srec, int len, int lane, const u64 (&tx)[TC / 2],
-                                             const u64 (&ty)[TC / 2], u64 (&acc)[TC / 2], u64 cc) {
+// One kernel value per (source, target) pair serves all NR right-hand sides.
+template <int TC, int NR>
+__device__ __forceinline__ void p2p_tile_f32(const WarpStage<NR> &ws, int len, int lane, const u64 (&tx)[TC / 2],
+                                             const u64 (&ty)[TC / 2], u64 (&acc)[NR][TC / 2], u64 cc) {
     for (int q0 = 0; q0 < len; q0 += 32) {
         const int q = q0 + lane;
-        const float4 sr = q < len ? srec[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const u64 nx = pk2(-sr.x, -sr.x), ny = pk2(-sr.y, -sr.y), uu = pk2(sr.z, sr.z);
+        const float4 sr = q < len ? ws.rec[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 sb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NR > 2 && q < len) sb = ws.recb[q];
+        const u64 nx = pk2(-sr.x, -sr.x), ny = pk2(-sr.y, -sr.y);
+        u64 uu[NR];
+        uu[0] = pk2(sr.z, sr.z);
+        if (NR > 1) uu[1] = pk2(sr.w, sr.w);
+        if (NR > 2) uu[2] = pk2(sb.x, sb.x);
+        if (NR > 3) uu[3] = pk2(sb.y, sb.y);
 #pragma unroll
         for (int k = 0; k < TC / 2; ++k) {
             const u64 dx = add2(tx[k], nx);
@@ -154,18 +174,23 @@ __device__ __forceinline__ void p2p_tile_f32(const float4 *__restrict__ srec, in
             const u64 d2 = fma2(dx, dx, fma2(dy, dy, cc));
             float a, b;
             up2(d2, a, b);
-            acc[k] = fma2(pk2(rsqrtf(a), rsqrtf(b)), uu, acc[k]);
+            const u64 rr = pk2(rsqrtf(a), rsqrtf(b));
+#pragma unroll
+            for (int m = 0; m < NR; ++m) acc[m][k] = fma2(rr, uu[m], acc[m][k]);
         }
     }
 }
 
-template <int TC>
-__device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase, bool staged_all, int ti, int ntc,
-                                                  int lane, int u0, int u1, int St, const int32_t *__restrict__ begin,
-                                                  const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
-                                                  const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-                                                  const float4 *__restrict__ rec, float c2, int *err) {
-    u64 tx[TC / 2], ty[TC / 2], acc[TC / 2];
+// Sums of one chunk of up to TC targets for every right-hand side; lane L ends with
+// target L % TC's total in tot[m].
+template <int TC, int NR>
+__device__ __forceinline__ void p2p_chunk_staged(WarpStage<NR> &ws, uint32_t &phase, bool staged_all, int ti, int ntc,
+                                                 int lane, int u0, int u1, int St, const int32_t *__restrict__ begin,
+                                                 const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
+                                                 const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
+                                                 const float4 *__restrict__ rec, const float4 *__restrict__ recb,
+                                                 float c2, int *err, float (&tot)[NR]) {
+    u64 tx[TC / 2], ty[TC / 2], acc[NR][TC / 2];
 #pragma unroll
     for (int q = 0; q < TC / 2; ++q) {
         const int i0 = 2 * q, i1 = 2 * q + 1;
@@ -173,72 +198,90 @@ __device__ __forceinline__ float p2p_chunk_staged(WarpStage &ws, uint32_t &phase
         const float2 b = i1 < ntc ? loc[ti + i1] : make_float2(kFar, kFar);
         tx[q] = pk2(a.x, b.x);
         ty[q] = pk2(a.y, b.y);
-        acc[q] = 0ull;
+#pragma unroll
+        for (int m = 0; m < NR; ++m) acc[m][q] = 0ull;
     }
     const u64 cc = pk2(c2, c2);
     if (staged_all) {
-        p2p_tile_f32<TC>(ws.rec, St, lane, tx, ty, acc, cc);
+        p2p_tile_f32<TC, NR>(ws, St, lane, tx, ty, acc, cc);
     } else {
         for (int q0 = 0; q0 < St; q0 += kStageCap) {
             const int len = min(kStageCap, St - q0);
-            if (!stage_sources(ws, phase, q0, len, u0, u1, St, begin, uitems, ucum, udelta, rec, lane, err)) break;
-            p2p_tile_f32<TC>(ws.rec, len, lane, tx, ty, acc, cc);
+            if (!stage_sources<NR>(ws, phase, q0, len, u0, u1, St, begin, uitems, ucum, udelta, rec, recb, lane, err))
+                break;
+            p2p_tile_f32<TC, NR>(ws, len, lane, tx, ty, acc, cc);
             __syncwarp();
         }
     }
-    float s[TC];
 #pragma unroll
-    for (int k = 0; k < TC / 2; ++k) up2(acc[k], s[2 * k], s[2 * k + 1]);
-    return lane_reduce<float, TC>(s, lane);
+    for (int m = 0; m < NR; ++m) {
+        float sm[TC];
+#pragma unroll
+        for (int k = 0; k < TC / 2; ++k) up2(acc[m][k], sm[2 * k], sm[2 * k + 1]);
+        tot[m] = lane_reduce<float, TC>(sm, lane);
+    }
 }
 
-// STORE: write the near-field sum (b_near = sum); otherwise add it to bs.
-// W warps per CTA (one target leaf each); targets in chunks of at most TCMAX.
-template <bool STORE, int W, int TCMAX>
+// STORE: write the near-field sums (b_near = sum); otherwise add them to bs.  W warps per
+// CTA; each warp pulls target leaves from a device counter (the plan's order, most pairs
+// first) until none is left; targets in chunks of at most TCMAX; NR right-hand sides.
+template <bool STORE, int W, int TCMAX, int NR>
 __global__ void __launch_bounds__(32 * W) k_p2p_f32(
-    int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ begin, const int32_t *__restrict__ end,
-    const int32_t *__restrict__ uoffs, const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum,
-    const int32_t *__restrict__ utot, const float2 *__restrict__ udelta, const float2 *__restrict__ loc,
-    const float4 *__restrict__ rec, ShapeC shape, float *__restrict__ bs, int *err) {
+    int nleaf, const int32_t *__restrict__ leaves, const int32_t *__restrict__ order, int *counter,
+    const int32_t *__restrict__ begin, const int32_t *__restrict__ end, const int32_t *__restrict__ uoffs,
+    const int32_t *__restrict__ uitems, const int32_t *__restrict__ ucum, const int32_t *__restrict__ utot,
+    const float2 *__restrict__ udelta, const float2 *__restrict__ loc, const float4 *__restrict__ rec,
+    const float4 *__restrict__ recb, ShapeC shape, int64_t n, float *__restrict__ bs, int *err) {
     extern __shared__ __align__(128) unsigned char smraw_p2p[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpStage &ws = reinterpret_cast<WarpStage *>(smraw_p2p)[w];
+    WarpStage<NR> &ws = reinterpret_cast<WarpStage<NR> *>(smraw_p2p)[w];
     if (lane == 0) {
         mbar_init(&ws.bar, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    const int widx = blockIdx.x * W + w;
-    if (widx >= nleaf) return;
-    const int b = leaves[widx];
-    const int tb = begin[b], nt = end[b] - tb;
-    const int u0 = uoffs[b], u1 = uoffs[b + 1];
-    const int St = utot[b];
-    const double cb = shape.of(b);
-    const float c2 = (float)(cb * cb);
     uint32_t phase = 0;
-    const bool staged_all = St <= kStageCap;
-    if (staged_all && !stage_sources(ws, phase, 0, St, u0, u1, St, begin, uitems, ucum, udelta, rec, lane, err)) return;
-    for (int tc = 0; tc < nt; tc += TCMAX) {
-        const int ntc = min(TCMAX, nt - tc);
-        float tot;
-        int tcap;
-        if (ntc <= 8) {
-            tot = p2p_chunk_staged<8>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
-                                      udelta, loc, rec, c2, err);
-            tcap = 8;
-        } else if (TCMAX == 16 || ntc <= 16) {
-            tot = p2p_chunk_staged<16>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
-                                       udelta, loc, rec, c2, err);
-            tcap = 16;
-        } else {
-            tot = p2p_chunk_staged<(TCMAX > 16 ? 32 : 16)>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St,
-                                                           begin, uitems, ucum, udelta, loc, rec, c2, err);
-            tcap = TCMAX > 16 ? 32 : 16;
-        }
-        if (lane < tcap && lane < ntc) {
-            if (STORE) bs[tb + tc + lane] = tot;
-            else bs[tb + tc + lane] += tot;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= nleaf) break;
+        const int b = leaves[order[item]];
+        const int tb = begin[b], nt = end[b] - tb;
+        const int u0 = uoffs[b], u1 = uoffs[b + 1];
+        const int St = utot[b];
+        const double cb = shape.of(b);
+        const float c2 = (float)(cb * cb);
+        const bool staged_all = St <= kStageCap;
+        if (staged_all &&
+            !stage_sources<NR>(ws, phase, 0, St, u0, u1, St, begin, uitems, ucum, udelta, rec, recb, lane, err))
+            break;
+        for (int tc = 0; tc < nt; tc += TCMAX) {
+            const int ntc = min(TCMAX, nt - tc);
+            float tot[NR];
+            int tcap;
+            if (ntc <= 8) {
+                p2p_chunk_staged<8, NR>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems, ucum,
+                                        udelta, loc, rec, recb, c2, err, tot);
+                tcap = 8;
+            } else if (TCMAX == 16 || ntc <= 16) {
+                p2p_chunk_staged<16, NR>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St, begin, uitems,
+                                         ucum, udelta, loc, rec, recb, c2, err, tot);
+                tcap = 16;
+            } else {
+                p2p_chunk_staged<(TCMAX > 16 ? 32 : 16), NR>(ws, phase, staged_all, tb + tc, ntc, lane, u0, u1, St,
+                                                             begin, uitems, ucum, udelta, loc, rec, recb, c2, err,
+                                                             tot);
+                tcap = TCMAX > 16 ? 32 : 16;
+            }
+            if (lane < tcap && lane < ntc) {
+#pragma unroll
+                for (int m = 0; m < NR; ++m) {
+                    float *o = bs + (int64_t)m * n + tb + tc + lane;
+                    if (STORE) *o = tot[m];
+                    else *o += tot[m];
+                }
+            }
         }
     }
 }
@@ -294,44 +337,70 @@ __global__ void __launch_bounds__(32 * kP2PWarps) k_p2p_f64(
 
 }  // namespace
 
-template <bool STORE, int W, int TCMAX>
+template <bool STORE, int W, int TCMAX, int NR>
 void p2p_f32_launch_t(Plan &P, float *bs, cudaStream_t s) {
-    const unsigned grid = (unsigned)((P.nleaf + W - 1) / W);
-    const size_t smem = sizeof(WarpStage) * W;
-    IMQ_CUDA(cudaFuncSetAttribute(k_p2p_f32<STORE, W, TCMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_p2p_f32<STORE, W, TCMAX><<<grid, 32 * W, smem, s>>>(
-        P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(), P.end.as<int32_t>(), P.U.off.as<int32_t>(),
-        P.U.items.as<int32_t>(), P.ucum.as<int32_t>(), P.utot.as<int32_t>(), P.uoff.as<float2>(), P.loc.as<float2>(),
-        P.rec4.as<float4>(), P.shape(), bs, device_error_word());
+    const size_t smem = sizeof(WarpStage<NR>) * W;
+    auto kern = k_p2p_f32<STORE, W, TCMAX, NR>;
+    IMQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // persistent: enough CTAs to fill every SM several times over, each warp pulling leaves
+    static int n_sm[64] = {0}, per_sm[64][2][3][3] = {};
+    int dev = 0;
+    IMQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(IMQ_UNSUPPORTED, "P2P: device index out of range");
+    if (n_sm[dev] == 0) IMQ_CUDA(cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev));
+    int &occ = per_sm[dev][W == 2 ? 0 : W == 4 ? 1 : 2][NR == 1 ? 0 : NR == 2 ? 1 : 2][TCMAX == 8 ? 0 : TCMAX == 16 ? 1 : 2];
+    if (occ == 0) IMQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * W, smem));
+    const int64_t want = ((int64_t)P.nleaf + W - 1) / W;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)n_sm[dev] * std::max(1, occ)));
+    IMQ_CUDA(cudaMemsetAsync(P.p2p_counter.ptr, 0, sizeof(int), s));
+    kern<<<grid, 32 * W, smem, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.p2p_order.as<int32_t>(),
+                                    P.p2p_counter.as<int>(), P.begin.as<int32_t>(), P.end.as<int32_t>(),
+                                    P.U.off.as<int32_t>(), P.U.items.as<int32_t>(), P.ucum.as<int32_t>(),
+                                    P.utot.as<int32_t>(), P.uoff.as<float2>(), P.loc.as<float2>(), P.rec4.as<float4>(),
+                                    NR > 2 ? P.rec4b.as<float4>() : nullptr, P.shape(), P.N, bs, device_error_word());
     IMQ_LAUNCH_CHECK();
 }
 
 // The plan's P2P tile shape (warps per CTA, target chunk) selects the instance.
-template <bool STORE, int W>
+template <bool STORE, int W, int NR>
 void p2p_f32_launch_w(Plan &P, float *bs, cudaStream_t s) {
     switch (P.p2p_chunk) {
-        case 8: p2p_f32_launch_t<STORE, W, 8>(P, bs, s); break;
-        case 32: p2p_f32_launch_t<STORE, W, 32>(P, bs, s); break;
-        default: p2p_f32_launch_t<STORE, W, 16>(P, bs, s); break;
+        case 8: p2p_f32_launch_t<STORE, W, 8, NR>(P, bs, s); break;
+        case 32: p2p_f32_launch_t<STORE, W, 32, NR>(P, bs, s); break;
+        default: p2p_f32_launch_t<STORE, W, 16, NR>(P, bs, s); break;
     }
 }
 
-template <bool STORE>
-void p2p_f32_launch(Plan &P, const float *u, float *bs, cudaStream_t s) {
-    if (!P.rec4.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace missing");
-    k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u, P.N, P.rec4.as<float4>());
-    IMQ_LAUNCH_CHECK();
+template <bool STORE, int NR>
+void p2p_f32_launch_r(Plan &P, float *bs, cudaStream_t s) {
     switch (P.p2p_warps) {
-        case 2: p2p_f32_launch_w<STORE, 2>(P, bs, s); break;
-        case 8: p2p_f32_launch_w<STORE, 8>(P, bs, s); break;
-        default: p2p_f32_launch_w<STORE, 4>(P, bs, s); break;
+        case 2: p2p_f32_launch_w<STORE, 2, NR>(P, bs, s); break;
+        case 8: p2p_f32_launch_w<STORE, 8, NR>(P, bs, s); break;
+        default: p2p_f32_launch_w<STORE, 4, NR>(P, bs, s); break;
+    }
+}
+
+// u, bs: [nrhs][N]; the right-hand sides go through the kernel four at a time
+template <bool STORE>
+void p2p_f32_launch(Plan &P, const float *u, float *bs, int nrhs, cudaStream_t s) {
+    if (!P.rec4.ptr || !P.p2p_order.ptr) fail(IMQ_CUDA_ERROR, "P2P: record workspace or leaf order missing");
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+        const int nr = std::min(4, nrhs - r0);
+        if (nr > 2 && !P.rec4b.ptr) fail(IMQ_CUDA_ERROR, "P2P: second record workspace missing");
+        k_pack_records<<<blocks_for(P.N, 256), 256, 0, s>>>(P.loc.as<float2>(), u + (size_t)r0 * P.N, P.N, nr,
+                                                            P.rec4.as<float4>(), P.rec4b.as<float4>());
+        IMQ_LAUNCH_CHECK();
+        float *b = bs + (size_t)r0 * P.N;
+        if (nr == 1) p2p_f32_launch_r<STORE, 1>(P, b, s);
+        else if (nr == 2) p2p_f32_launch_r<STORE, 2>(P, b, s);
+        else p2p_f32_launch_r<STORE, 4>(P, b, s);
     }
 }
 
 template <class T>
 void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) {
-        p2p_f32_launch<false>(P, u, bs, s);
+        p2p_f32_launch<false>(P, u, bs, 1, s);
     } else {
         const unsigned grid = (unsigned)((P.nleaf + kP2PWarps - 1) / kP2PWarps);
         k_p2p_f64<<<grid, 32 * kP2PWarps, 0, s>>>(P.nleaf, P.leaves.as<int32_t>(), P.begin.as<int32_t>(),
@@ -342,7 +411,9 @@ void p2p_apply(Plan &P, const T *u, T *bs, cudaStream_t s) {
     }
 }
 
-void p2p_near_f32(Plan &P, const float *u, float *near, cudaStream_t s) { p2p_f32_launch<true>(P, u, near, s); }
+void p2p_near_f32(Plan &P, const float *u, float *near, int nrhs, cudaStream_t s) {
+    p2p_f32_launch<true>(P, u, near, nrhs, s);
+}
 
 template void p2p_apply<float>(Plan &, const float *, float *, cudaStream_t);
 template void p2p_apply<double>(Plan &, const double *, double *, cudaStream_t);
