@@ -95,23 +95,26 @@ __global__ void k_m2l_images(const float *__restrict__ ops, int64_t nblk, int K,
     }
 }
 
-// Warp roles (288 threads):
-//   warps 0-3  drain: thread b owns target row b (TMEM lane b); after each chunk
-//              it adds the chunk's accumulator to FP32 registers, and at the end
-//              adds them to the target's local coefficients;
-//   warps 4-7  producers: gather the 128 rows of A (hi and lo) by cp.async,
+// Warp roles (416 threads):
+//   warps 0-7  drain: warp w reads TMEM lane quarter w % 4 (thread b of the
+//              quarter owns target row 32 (w % 4) + b) and column half w / 4 of
+//              the accumulator; after each chunk it loads its NC x 16 columns
+//              with back-to-back tcgen05.ld and one wait, adds them to FP32
+//              registers, and at the end adds them to the target's local
+//              coefficients;
+//   warps 8-11 producers: gather the 128 rows of A (hi and lo) by cp.async,
 //              eight threads per 128-byte row, and arrive on the stage's
-//              barrier through cp.async.mbarrier.arrive.noinc; thread 128 also
-//              issues the bulk copy of the operator image;
-//   warp 8     lane 0 issues the 12 MMAs of each chunk into one of NA TMEM
+//              barrier through cp.async.mbarrier.arrive.noinc; the first
+//              producer thread also issues the bulk copy of the operator image;
+//   warp 12    lane 0 issues the 12 MMAs of each chunk into one of NA TMEM
 //              accumulators and commits them to the stage's "empty" barrier and
 //              the accumulator's "full" barrier.
 // Barriers: full[S] (129 arrivals + image bytes), empty[S] (MMA commit),
-// acc_full[NA] (MMA commit), acc_empty[NA] (4 drain warps); NA accumulators
+// acc_full[NA] (MMA commit), acc_empty[NA] (8 drain warps); NA accumulators
 // rotate so that the MMAs of chunk it wait only for the drain of chunk it - NA.
 // A work item is (tile, part): a tile's offset classes are split over nsplit
 // CTAs, which add their partial sums to L with one RED per element each.
-constexpr int kDrainThreads = 128, kProdThreads = 128;
+constexpr int kDrainWarps = 8, kDrainThreads = 32 * kDrainWarps, kProdThreads = 128;
 constexpr int kThreadsWS = kDrainThreads + kProdThreads + 32;
 
 constexpr int kRing = 16;   // tile records in flight between the roles (a tile has >= 1 chunk)
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         }
         for (int i = 0; i < NA; ++i) {
             mbar_init(&s_accf[i], 1);
-            mbar_init(&s_acce[i], kDrainThreads / 32);
+            mbar_init(&s_acce[i], kDrainWarps);
         }
         for (int i = 0; i < kRing; ++i) mbar_init(&s_ring[i], 1);
         fence_mbar_init();
@@ -166,9 +169,12 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     const uint32_t tmem = s_tmem;
     bool ok = true;
 
-    if (w < 4) {
+    if (w < kDrainWarps) {
         // ---------------------------------------------------------------- drain
-        const uint32_t tl = tmem + ((uint32_t)(w * 32) << 16);
+        constexpr int H = NC * 16;                 // columns of this warp's half
+        constexpr int BL = NC <= 3 ? NC : 2;       // 16-column loads in flight per wait
+        const int quarter = w & 3, half = w >> 2;
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * H);
         int g = 0;   // chunk counter across tiles
         for (int t = 0;; ++t) {
             const int slot = t % kRing;
@@ -179,9 +185,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             const int ncls = s_ncls[slot];
             if (ncls < 0) break;
             const int4 tile = tiles[s_tix[slot]];
-            float acc[NC * 32];
+            float acc[H];
 #pragma unroll
-            for (int i = 0; i < NC * 32; ++i) acc[i] = 0.f;
+            for (int i = 0; i < H; ++i) acc[i] = 0.f;
             // every 32-wide K chunk is drained and summed in FP32 registers: fewer partial sums
             // accumulated inside the tensor core keep the tf32 products' precision
             const int nitems = ncls * NKC;
@@ -194,25 +200,33 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 tc_fence_after();
                 const uint32_t a = tl + (uint32_t)(g % NA) * kAccCols;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    float v[32];
-                    tmem_ld32(a + (uint32_t)(c * 32), v);
+                for (int c0 = 0; c0 < NC; c0 += BL) {
+                    uint32_t v[BL * 16];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+                    for (int c = 0; c < BL; ++c)
+                        if (c0 + c < NC) tmem_ld16_issue(a + (uint32_t)((c0 + c) * 16), v + 16 * c);
+                    tmem_ld_wait_regs<BL * 16>(v);
+#pragma unroll
+                    for (int c = 0; c < BL; ++c)
+                        if (c0 + c < NC)
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) acc[(c0 + c) * 16 + i] += __uint_as_float(v[16 * c + i]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_acce[g % NA]);
             }
             if (!ok) break;
-            if (tid < tile.z) {
-                float *Lb = L + (int64_t)tbox[tile.y + tid] * Kout;
+            const int row = quarter * 32 + lane;
+            if (row < tile.z) {
+                float *Lb = L + (int64_t)tbox[tile.y + row] * Kout + half * H;
+                const int ncol = min(H, Kout - half * H);
 #pragma unroll
-                for (int i = 0; i < NC * 32; ++i)
-                    if (i < Kout) atomicAdd(Lb + i, acc[i]);   // onto the P2L terms in L: a RED, no load
+                for (int i = 0; i < H; ++i)
+                    if (i < ncol) atomicAdd(Lb + i, acc[i]);   // onto the P2L terms in L: a RED, no load
             }
         }
-    } else if (w < 8) {
+    } else if (w < kDrainWarps + 4) {
         // ---------------------------------------------------------------- producers
         // No producer waits for its own copies: each chunk ends with an arrive
         // that the hardware performs once the thread's copies have landed, so

@@ -133,4 +133,38 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Issue (without waiting) a load of 32 lanes x 16 consecutive 32-bit columns:
+// thread t of the warp gets lane (warp's lane quarter + t), columns
+// [col, col + 16).  The registers are valid only after tmem_ld_wait_regs.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+// Wait for every tcgen05.ld this thread issued; the N destination registers are
+// tied to the wait (in groups of 16) so that no use of them is scheduled before it.
+template <int N>
+__device__ __forceinline__ void tmem_ld_wait_regs(uint32_t *r) {
+    static_assert(N % 16 == 0, "groups of 16 registers");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int g = 16; g < N; g += 16)
+        asm volatile(""
+                     : "+r"(r[g + 0]), "+r"(r[g + 1]), "+r"(r[g + 2]), "+r"(r[g + 3]), "+r"(r[g + 4]),
+                       "+r"(r[g + 5]), "+r"(r[g + 6]), "+r"(r[g + 7]), "+r"(r[g + 8]), "+r"(r[g + 9]),
+                       "+r"(r[g + 10]), "+r"(r[g + 11]), "+r"(r[g + 12]), "+r"(r[g + 13]), "+r"(r[g + 14]),
+                       "+r"(r[g + 15])
+                     :
+                     : "memory");
+}
+
 }  // namespace imq
