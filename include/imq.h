@@ -291,6 +291,16 @@ typedef enum imq_residual {
     IMQ_RESIDUAL_PLAN_F64 = 0,   /* the fast product in FP64 (opt->residual_plan if given, else plan) */
     IMQ_RESIDUAL_DENSE_F64 = 1   /* the dense FP64 product (exact up to rounding, O(N^2))          */
 } imq_residual;
+/* Inner Krylov method.  CG: preconditioned conjugate gradients, graph-captured
+ * (A is symmetric positive definite, Micchelli; the paper's Section 2 names
+ * iterative solvers).  GMRES: right-preconditioned restarted GMRES(m) on the
+ * same operator and preconditioner (Arnoldi vectors, Gram-Schmidt applied
+ * twice and all dots in FP64; the small least-squares problem on the host).
+ * GMRES minimises the residual norm over each cycle, so it keeps converging
+ * where A is positive definite in exact arithmetic but not numerically (flat
+ * shapes, c many times the point spacing), where CG's p.Ap or r.z loses its
+ * sign and the pass ends.  Each cycle is one refinement pass. */
+typedef enum imq_krylov { IMQ_KRYLOV_CG = 0, IMQ_KRYLOV_GMRES = 1 } imq_krylov;
 #define IMQ_CG_MAX_RHS_INFO 16
 
 typedef struct imq_cg_options {
@@ -311,7 +321,9 @@ typedef struct imq_cg_options {
     int32_t coarse_points;   /* SCHWARZ_2L: max points per coarse box, 1..1024 (0: the leaf size) */
     int32_t coarse_gram;     /* SCHWARZ_2L: pairs of E = Z^T A Z in 0: FP64 if N^2 <= 4e10, else
                                 FP32 with FP64 partial sums; 1: FP64; 2: FP32                   */
-    int32_t reserved[4];
+    int32_t krylov;          /* imq_krylov (single plans; batched plans run CG)                 */
+    int32_t gmres_m;         /* GMRES restart length, 1..200 (0: 40); (m + 1) N doubles of basis */
+    int32_t reserved[2];
 } imq_cg_options;
 
 typedef struct imq_cg_info {

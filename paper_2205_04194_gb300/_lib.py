@@ -51,7 +51,8 @@ class CgOptions(ctypes.Structure):
     _fields_ = [("struct_size", I32), ("rtol", D), ("maxit", I32), ("precond", I32), ("schwarz_nmax", I32),
                 ("schwarz_shift", D), ("refine_steps", I32), ("inner_rtol", D), ("residual", I32),
                 ("x0_given", I32), ("residual_plan", P), ("inner_operator", I32), ("schwarz_fp64", I32),
-                ("coarse_points", I32), ("coarse_gram", I32), ("reserved", I32 * 4)]
+                ("coarse_points", I32), ("coarse_gram", I32), ("krylov", I32), ("gmres_m", I32),
+                ("reserved", I32 * 2)]
 
 
 class CgInfo(ctypes.Structure):

@@ -542,6 +542,9 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         if (o.coarse_points < 0 || o.coarse_points > 1024)
             fail(IMQ_INVALID_ARG, "imq_cg_solve: coarse_points must be in [0, 1024]");
         if (o.coarse_gram < 0 || o.coarse_gram > 2) fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown coarse_gram");
+        if (o.krylov != IMQ_KRYLOV_CG && o.krylov != IMQ_KRYLOV_GMRES)
+            fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown krylov method");
+        if (o.gmres_m < 0 || o.gmres_m > 200) fail(IMQ_INVALID_ARG, "imq_cg_solve: gmres_m must be in [0, 200]");
         if (o.schwarz_nmax < 0 || o.schwarz_nmax > 224) fail(IMQ_INVALID_ARG, "imq_cg_solve: schwarz_nmax must be in [0, 224]");
         if (o.inner_operator < IMQ_OPERATOR_FAST_F32 || o.inner_operator > IMQ_OPERATOR_DENSE_F64)
             fail(IMQ_INVALID_ARG, "imq_cg_solve: unknown inner operator");
@@ -562,6 +565,8 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         try {
             if (!P.prob_off.empty() && o.precond == IMQ_PRECOND_SCHWARZ_2L)
                 fail(IMQ_UNSUPPORTED, "imq_cg_solve: the two-level preconditioner is built for single plans");
+            if (!P.prob_off.empty() && o.krylov == IMQ_KRYLOV_GMRES)
+                fail(IMQ_UNSUPPORTED, "imq_cg_solve: GMRES is built for single plans");
             if (!P.prob_off.empty())
                 cg_solve_batched(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o,
                                  info, rel_out, iters_out, s);

@@ -225,6 +225,54 @@ __global__ void k_sub_f64(double *__restrict__ r, const double *__restrict__ b, 
         r[i] -= b[i];
 }
 
+// ---- GMRES (Arnoldi) helpers: V holds nv vectors of length n, one after another
+// part[i][block] = this block's partial of V_i . w (fixed order within the block)
+__global__ void __launch_bounds__(kRedThreads) k_multi_dot_part(const double *__restrict__ V, int64_t n, int nv,
+                                                                const double *__restrict__ w,
+                                                                double *__restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    for (int i = 0; i < nv; ++i) {
+        const double *vi = V + (size_t)i * n;
+        double acc = 0;
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+            acc += vi[k] * w[k];
+        const double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[(size_t)i * kRedBlocks + blockIdx.x] = t;
+        __syncthreads();   // sh is reused by the next vector
+    }
+}
+// h[i] = sum over blocks of part[i][*] (one block per vector, fixed order)
+__global__ void __launch_bounds__(kRedThreads) k_multi_sum(const double *__restrict__ part, double *__restrict__ h) {
+    const double v = final_sum(part + (size_t)blockIdx.x * kRedBlocks);
+    if (threadIdx.x == 0) h[blockIdx.x] = v;
+}
+// w -= sum_i h[i] V_i
+__global__ void __launch_bounds__(kRedThreads) k_multi_axpy(const double *__restrict__ V, int64_t n, int nv,
+                                                            const double *__restrict__ h, double *__restrict__ w) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0;
+        for (int i = 0; i < nv; ++i) acc += h[i] * V[(size_t)i * n + k];
+        w[k] -= acc;
+    }
+}
+// u = sum_i y[i] V_i
+__global__ void __launch_bounds__(kRedThreads) k_lincomb(const double *__restrict__ V, int64_t n, int nv,
+                                                         const double *__restrict__ y, double *__restrict__ u) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0;
+        for (int i = 0; i < nv; ++i) acc += y[i] * V[(size_t)i * n + k];
+        u[k] = acc;
+    }
+}
+__global__ void k_scale_to(const double *__restrict__ w, double a, double *__restrict__ v, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) v[i] = a * w[i];
+}
+__global__ void k_f32_to_f64(const float *__restrict__ b, double *__restrict__ q, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) q[i] = (double)b[i];
+}
+
 __global__ void k_sub(double *__restrict__ r, const double *__restrict__ f, const double *__restrict__ ax, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         r[i] = f[i] - ax[i];
@@ -599,6 +647,7 @@ namespace {
 struct Work {
     DevMem x, xb, r, p, q, z, u32, b32, part, S, tmp;
     DevMem u2, b2, q2;   // the two-level preconditioner's product (FP32 in / out, or FP64 out)
+    DevMem V, hpart, hdev;   // GMRES: Arnoldi basis, partial dots, coefficients
 };
 
 double read_dot(const double *a, const double *b, int64_t n, DevMem &part, DevMem &tmp, cudaStream_t s) {
@@ -715,6 +764,110 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
         coarse_prolong(P, z, z, dn, st);
     };
 
+    // ---- GMRES(m): one restart cycle on A d = r (right preconditioning, d = M u), the
+    // correction added to w.xb.  Arnoldi basis in w.V, Gram-Schmidt applied twice with
+    // FP64 dots in a fixed order, Givens rotations and the triangular solve on the host.
+    const bool gmres = o.krylov == IMQ_KRYLOV_GMRES;
+    const int gm = o.gmres_m > 0 ? o.gmres_m : 40;
+    if (gmres) {
+        w.V.alloc(sizeof(double) * (size_t)(gm + 1) * n);
+        w.hpart.alloc(sizeof(double) * (size_t)(gm + 1) * kRedBlocks);
+        w.hdev.alloc(sizeof(double) * (size_t)(gm + 1));
+    }
+    auto apply_M = [&](const double *in, double *out) {
+        if (!pre) {
+            IMQ_CUDA(cudaMemcpyAsync(out, in, 8 * n, cudaMemcpyDeviceToDevice, s));
+            return;
+        }
+        schwarz_apply(P, Z, in, out, P.c, n, nullptr, s);
+        if (!two_level) return;
+        const float *b32;
+        const double *b64;
+        op_product(out, s, nullptr, &b32, &b64);
+        coarse_restrict(P, in, b32, b64, nullptr, s);
+        coarse_solve(P, nullptr, s);
+        coarse_prolong(P, out, out, nullptr, s);
+    };
+    auto apply_A = [&](const double *in, double *out) {
+        if (op == IMQ_OPERATOR_FAST_F32) {
+            k_p_to_f32<<<gr, kRedThreads, 0, s>>>(in, w.u32.as<float>(), n, nullptr);
+            IMQ_LAUNCH_CHECK();
+            fmm_apply<float>(P, w.u32.as<float>(), w.b32.as<float>(), 1, s);
+            k_f32_to_f64<<<g, 256, 0, s>>>(w.b32.as<float>(), out, n);
+            IMQ_LAUNCH_CHECK();
+        } else if (op == IMQ_OPERATOR_FAST_F64) {
+            fmm_apply<double>(P, in, out, 1, s);
+        } else {
+            dense_f64_async(P.pos.as<double>(), n, P.c, in, out, s);
+        }
+    };
+    // returns kConverged (target met), kMaxIter (cycle or budget ended) or kNumerical; its += iterations
+    auto gmres_cycle = [&](const double *rv, double target, int budget, int &its) -> int {
+        double *V = w.V.as<double>(), *zb = w.p.as<double>(), *wv = w.q.as<double>(), *u = w.x.as<double>();
+        double *hd = w.hdev.as<double>();
+        const double beta0 = std::sqrt(read_dot(rv, rv, n, w.part, w.tmp, s));
+        if (!std::isfinite(beta0)) return kNumerical;
+        if (beta0 == 0) return kConverged;
+        k_scale_to<<<g, 256, 0, s>>>(rv, 1.0 / beta0, V, n);
+        IMQ_LAUNCH_CHECK();
+        std::vector<double> H((size_t)(gm + 1) * gm, 0.0), cs(gm, 0.0), sn(gm, 0.0), gv(gm + 1, 0.0), hh(gm + 1);
+        auto Hij = [&](int i, int j) -> double & { return H[(size_t)j * (gm + 1) + i]; };
+        gv[0] = beta0;
+        int k = 0, state = kMaxIter;
+        for (int j = 0; j < gm && its < budget; ++j) {
+            apply_M(V + (size_t)j * n, zb);
+            apply_A(zb, wv);
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                k_multi_dot_part<<<kRedBlocks, kRedThreads, 0, s>>>(V, n, j + 1, wv, w.hpart.as<double>());
+                k_multi_sum<<<j + 1, kRedThreads, 0, s>>>(w.hpart.as<double>(), hd);
+                k_multi_axpy<<<kRedBlocks, kRedThreads, 0, s>>>(V, n, j + 1, hd, wv);
+                IMQ_LAUNCH_CHECK();
+                IMQ_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+                IMQ_CUDA(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; ++i) Hij(i, j) += hh[i];
+            }
+            const double hn = std::sqrt(read_dot(wv, wv, n, w.part, w.tmp, s));
+            Hij(j + 1, j) = hn;
+            ++its;
+            k = j + 1;
+            for (int i = 0; i < j; ++i) {   // earlier rotations on the new column
+                const double a = Hij(i, j), b = Hij(i + 1, j);
+                Hij(i, j) = cs[i] * a + sn[i] * b;
+                Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+            }
+            const double a = Hij(j, j), b = Hij(j + 1, j), rho = std::hypot(a, b);
+            if (!std::isfinite(rho)) return kNumerical;
+            cs[j] = rho > 0 ? a / rho : 1.0;
+            sn[j] = rho > 0 ? b / rho : 0.0;
+            Hij(j, j) = rho;
+            Hij(j + 1, j) = 0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            if (std::fabs(gv[j + 1]) <= target || hn == 0) {
+                state = kConverged;
+                break;
+            }
+            k_scale_to<<<g, 256, 0, s>>>(wv, 1.0 / hn, V + (size_t)(j + 1) * n, n);
+            IMQ_LAUNCH_CHECK();
+        }
+        if (k == 0) return state;
+        std::vector<double> y(k, 0.0);   // H(0:k, 0:k) y = g(0:k), upper triangular
+        for (int i = k - 1; i >= 0; --i) {
+            double t = gv[i];
+            for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+            y[i] = Hij(i, i) != 0 ? t / Hij(i, i) : 0.0;
+            if (!std::isfinite(y[i])) return kNumerical;
+        }
+        IMQ_CUDA(cudaMemcpyAsync(hd, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+        k_lincomb<<<kRedBlocks, kRedThreads, 0, s>>>(V, n, k, hd, u);
+        IMQ_LAUNCH_CHECK();
+        apply_M(u, zb);
+        k_axpby<<<g, 256, 0, s>>>(w.xb.as<double>(), zb, 1.0, 1.0, n);
+        IMQ_LAUNCH_CHECK();
+        IMQ_CUDA(cudaStreamSynchronize(s));   // y lives on the host stack
+        return state;
+    };
+
     // ---- capture kIterPerGraph PCG iterations on a private stream
     GraphCapture cap;
     cudaStream_t cs = cap.begin();
@@ -761,6 +914,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
             const int max_outer = std::max(0, o.refine_steps);
             int restarts = 0;
             bool numerical = false;
+            double prev_rel = 0;
             for (int outer = 0;; ++outer) {
                 // residual r = f - A x (FP64 product unless x = 0)
                 if (outer == 0 && !o.x0_given) {
@@ -783,7 +937,10 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                 }
                 status = kMaxIter;
                 if (iters >= o.maxit) break;
-                if (max_outer > 0 ? outer >= max_outer : outer > restarts) break;
+                // GMRES cycles without refinement steps continue while each one lowers the true residual
+                if (gmres && max_outer == 0 && outer > 0 && !(rel < 0.999 * prev_rel)) break;
+                prev_rel = rel;
+                if (max_outer > 0 ? outer >= max_outer : (!gmres && outer > restarts)) break;
                 // inner PCG on A d = r from d = 0
                 // the recursive residual of the inner operator drifts from the true one by about the
                 // operator's rounding error, so a single pass aims at half the tolerance
@@ -804,6 +961,19 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                     else k_sub_f64<<<gr, kRedThreads, 0, s>>>(r, b64, n);
                     IMQ_LAUNCH_CHECK();
                     rr_start = read_dot(r, r, n, w.part, w.tmp, s);
+                }
+                if (gmres) {
+                    int its = 0;
+                    const int gs = gmres_cycle(r, inner_rtol * std::sqrt(rr0), o.maxit - iters, its);
+                    iters += its;
+                    k_axpby<<<g, 256, 0, s>>>(xs.as<double>(), w.xb.as<double>(), 1.0, 1.0, n);
+                    IMQ_LAUNCH_CHECK();
+                    outer_done = std::max(outer_done, outer + 1);
+                    if (gs == kNumerical) {
+                        numerical = true;
+                        break;
+                    }
+                    continue;
                 }
                 CGScalars h{};
                 h.rr = rr_start;

@@ -149,15 +149,17 @@ class Plan:
     def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=0,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan", x0=None,
               residual_plan=None, operator="fast_f32", schwarz_fp64=False, coarse_points=0, coarse_gram="auto",
-              stream=None, raise_on_failure=False):
+              krylov="cg", gmres_m=0, stream=None, raise_on_failure=False):
         """imq_cg_solve: coef with A coef = f.  Returns (coef, info dict); info["status"] is the
         imq_status name (IMQ_NOT_CONVERGED keeps the best iterate in coef).
         precond: "none", "schwarz" (leaf-neighbourhood patches) or "schwarz2" (the patches plus a
-        Galerkin coarse space of tree boxes holding at most coarse_points points)."""
+        Galerkin coarse space of tree boxes holding at most coarse_points points).
+        krylov: "cg" or "gmres" (restarted GMRES(gmres_m), for numerically indefinite flat shapes)."""
         return self._solve("imq_cg_solve", f, coef, x0, stream, raise_on_failure, None, dict(
             rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
             refine_steps=refine_steps, inner_rtol=inner_rtol, residual=residual, residual_plan=residual_plan,
-            operator=operator, schwarz_fp64=schwarz_fp64, coarse_points=coarse_points, coarse_gram=coarse_gram))
+            operator=operator, schwarz_fp64=schwarz_fp64, coarse_points=coarse_points, coarse_gram=coarse_gram,
+            krylov=krylov, gmres_m=gmres_m))
 
     def _solve(self, entry, f, coef, x0, stream, raise_on_failure, per_problem, kw):
         nrhs = 1 if len(np.shape(f)) == 1 else int(np.shape(f)[0])
@@ -182,6 +184,8 @@ class Plan:
         o.residual_plan = rp._h if rp is not None else None
         o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[kw["operator"]]
         o.schwarz_fp64 = 1 if kw["schwarz_fp64"] else 0
+        o.krylov = {"cg": 0, "gmres": 1}[kw.get("krylov", "cg")]
+        o.gmres_m = int(kw.get("gmres_m", 0))
         info = CgInfo()
         fp, kf = _buf(f, torch.float64)
         cp, kc = _buf(coef, torch.float64)
