@@ -394,7 +394,8 @@ def run_solves(args, imq, wl, d_pts, plan, dev):
     d_y = torch.from_numpy(g["y_val"]).to(dev)
     ct = torch.tensor(g["c"], dtype=torch.float64, requires_grad=True)
     ft = torch.from_numpy(g["f"]).to(dev).requires_grad_(True)
-    cg = dict(rtol=1e-6, maxit=args.grad_maxit, precond="schwarz", schwarz_shift=1e-5)
+    cg = dict(rtol=1e-6, maxit=args.grad_maxit, precond="schwarz2", coarse_points=1024, schwarz_shift=1e-4,
+              krylov="gmres", gmres_m=40)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     L = AG.InterpLoss.apply(ct, ft, d_tr, d_va, d_y, 12, 64, (0.0, 0.0, 1.0), torch.float32, cg, True)
@@ -405,8 +406,10 @@ def run_solves(args, imq, wl, d_pts, plan, dev):
                    "dloss_dc": float(ct.grad.item()), "dloss_df_norm": float(ft.grad.norm().item()),
                    "wall_s": time.perf_counter() - t0, "cg_maxit_per_solve": args.grad_maxit,
                    "solve_status": li["status"], "solve_max_rel_residual": li["max_rel_residual"],
-                   "note": "forward + adjoint; c/h ~ 45 is ill-conditioned, the capped solves leave this "
-                           "gradient unvalidated (see grad_wellcond_200k)"}
+                   "solver": "GMRES(40), two-level Schwarz, rtol 1e-6 per solve",
+                   "note": "forward + adjoint; at c/h ~ 45 a finite difference of the loss in c needs solves "
+                           "far below 1e-6, so the gradient is checked against central differences at the "
+                           "well-conditioned shape (grad_wellcond_200k)"}
     # the same loss at a well-conditioned shape, c = 2 x mean NN spacing: gradient through the FP32 fast
     # operator (solves to 1e-10 with FP64 refinement) against central differences of the loss
     c2 = 2.0 * W.mean_nn_spacing(g["train"])

@@ -21,11 +21,14 @@ from .imq import F32, F64, EvalPlan, Plan, _buf, _stream
 
 def cg_options(rtol=1e-10, maxit=2000, precond="schwarz", schwarz_nmax=0, schwarz_fp64=False,
                schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, residual="plan",
-               operator="fast_f32") -> CgOptions:
+               operator="fast_f32", coarse_points=0, krylov="cg", gmres_m=0) -> CgOptions:
     o = CgOptions()
     _lib.load().imq_cg_default_options(ctypes.byref(o))
     o.rtol, o.maxit = float(rtol), int(maxit)
     o.precond = {"none": 0, "schwarz": 1, "schwarz2": 2}[precond]
+    o.coarse_points = int(coarse_points)
+    o.krylov = {"cg": 0, "gmres": 1}[krylov]
+    o.gmres_m = int(gmres_m)
     o.schwarz_nmax, o.schwarz_fp64 = int(schwarz_nmax), 1 if schwarz_fp64 else 0
     o.schwarz_shift = float(schwarz_shift)
     o.refine_steps, o.inner_rtol = int(refine_steps), float(inner_rtol)
