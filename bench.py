@@ -37,7 +37,7 @@ METRIC = "IMQ A·v time & CG solve s at 1e-6 rel err, fast vs dense GPU matvec, 
 MUFU_PER_CLK_SM = 16        # rsqrt (MUFU) results per clock per SM
 FP32_FMA_PER_CLK_SM = 128   # FP32 lanes per SM
 N_SM = 152
-TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
+FP16_PER_BF16 = 1.0         # nominal dense tensor rates per GPU: fp16 and bf16 are equal
 
 
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum + dram__bytes_write.sum),
@@ -46,7 +46,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
 # SHA-256 of the kernel sources at capture time: once a source changes the figure is stale
 # and the bench reports null.  Summaries: profiles/launches_fast_product_clustered_1m.md.
 TRAFFIC = {
-    # k_m2l_umma: 87.44 MB read + 0.28 MB written per launch (its tf32 rows come from P2M / M2M)
+    # k_m2l_umma: 87.44 MB read + 0.28 MB written per launch (its packed rows come from P2M / M2M)
     "m2l": {"bytes": 87.44e6 + 0.28e6, "sources": {
         "paper_2205_04194_gb300/csrc/m2l_umma.cu": "9e188a398c2404daff8adacc4ba048cec2aff56d02309329976aeda8ede08319",
         "paper_2205_04194_gb300/csrc/umma.cuh": "a133f64894a1d5c359ee5202af3f44414abc786ea60768f20a375cecf456fcd6",
@@ -206,7 +206,8 @@ def run_reference(args, wl):
 
 def run_batched(args, imq, dev):
     """256 independent problems (N log-uniform in [1e3, 5e4], c uniform in [0.01, 0.2], 4 right-hand
-    sides) in one batched plan: plan build, the 4-RHS product, sampled accuracy and a capped CG solve."""
+    sides) in one batched plan: plan build, the 4-RHS product, its error on 16 whole problems against
+    the dense FP64 product, and a capped CG solve."""
     import torch
     from paper_2205_04194_gb300 import workloads as W
     probs = W.batched_256()
@@ -229,10 +230,14 @@ def run_batched(args, imq, dev):
                         "sampled_rows": tune["sampled_rows"], "choice": tiles,
                         "tried": [(t["p"], t["leaf"], t["translations"], t["p2p_warps"], t["p2p_chunk"],
                                    t["m2l_stages"], t["rel_err"], t["matvec_ms"]) for t in tune["tried"]]}}
-    # the tuned configuration, and the same (p, leaf) with FP32 translations if the tuner chose FP64
+    # the tuned configuration, and the same (p, leaf) with the other translation precision: the tuner
+    # measures its error on its own random vectors, while the workload's trig-sum right-hand sides
+    # cancel in the far field, so FP64 translations can be what meets 1e-6 on the actual data
     variants = [("tuned", tiles)]
     if tiles["translations"] != "fp32":
         variants.append(("fp32_translations", dict(tiles, translations="fp32")))
+    else:
+        variants.append(("fp64_translations", dict(tiles, translations="fp64")))
     for name, kw in variants:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -262,7 +267,7 @@ def run_batched(args, imq, dev):
         out[name] = {"plan": kw, "plan_build_s": build_s, "matvec_f32_ms": mv_ms,
                      "ns_per_point_rhs": mv_ms * 1e6 / (4 * bp.n),
                      "matvec_points_per_s": 4 * bp.n / (mv_ms * 1e-3),
-                     "sampled_rel2_err_max": float(errs.max()),
+                     "sampled_rel2_err_max": float(errs.max()), "meets_1e-6": bool(errs.max() <= 1e-6),
                      "sampled_rel2_err_max_per_rhs": errs.max(axis=0).tolist(), "sampled_problems": 16}
         if kw.get("translations", "fp32") == "fp32" and "cg" not in out:   # CG on the FP32-translation plan
             coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, precond="schwarz",
@@ -640,11 +645,11 @@ def main():
     p2p_peak = N_SM * MUFU_PER_CLK_SM * mhz * 1e6 / 1e9
     K = info["k_real"]
     m2l_tf = info["m2l_pairs"] * 2.0 * K * K / (phase_ms["m2l"] * 1e-3) / 1e12
-    # tensor-core M2L: 3 tf32 MMAs per product (hi*hi, hi*lo, lo*hi) on K padded to 32 and Kout to 16
+    # tensor-core M2L: 3 fp16 MMAs per product (hi*hi, hi*lo, lo*hi) on K padded to 32 and Kout to 16
     kp, kn = -(-K // 32) * 32, -(-K // 16) * 16
     m2l_exec_tf = 3 * info["m2l_pairs"] * 2.0 * kp * kn / (phase_ms["m2l"] * 1e-3) / 1e12
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    tf32_peak = bf16 * TF32_PER_BF16
+    f16_peak = bf16 * FP16_PER_BF16
     dominant = "p2p" if phase_ms["p2p"] >= phase_ms["m2l"] else "m2l"
     if dominant == "p2p":
         roof = {"kernel": "k_p2p<float>", "bound": "alu", "achieved": p2p_gps, "peak": p2p_peak,
@@ -652,12 +657,11 @@ def main():
                 "peak_source": f"derived: {N_SM} SMs x {MUFU_PER_CLK_SM} MUFU rsqrt/clk x {mhz:.0f} MHz "
                                f"({src} sm_max_mhz)"}
     else:
-        roof = {"kernel": "k_m2l_umma (tcgen05 kind::tf32, 3xTF32)", "bound": "tensor",
-                "achieved": m2l_tf, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m2l_tf / tf32_peak,
+        roof = {"kernel": "k_m2l_umma (tcgen05 kind::f16, fp16 hi/lo split)", "bound": "tensor",
+                "achieved": m2l_tf, "peak": f16_peak, "unit": "TFLOP/s", "frac": m2l_tf / f16_peak,
                 "traffic": _traffic("m2l") if (wl.n == 1_000_000 and wl.p == 12) else None,
-                "achieved_executed": m2l_exec_tf, "frac_executed": m2l_exec_tf / tf32_peak,
-                "peak_source": f"{src} bf16 burst {bf16:.1f} TFLOP/s x nominal tf32/bf16 ratio "
-                               f"{TF32_PER_BF16:.3f} (1.1 / 2.25 PFLOP/s dense)",
+                "achieved_executed": m2l_exec_tf, "frac_executed": m2l_exec_tf / f16_peak,
+                "peak_source": f"{src} bf16 burst {bf16:.1f} TFLOP/s (dense fp16 runs at the bf16 rate)",
                 "note": "achieved counts the algorithmic 2 K^2 flops per V pair (K = %d); executed counts "
                         "the 3 split MMAs on the padded %d x %d operator" % (K, kn, kp)}
     line = {

@@ -82,8 +82,9 @@ typedef struct imq_options {
     /* Tile shapes of the FP32 product (0: the default; imq_autotune measures them):        */
     int32_t p2p_warps;         /* target leaves (warps) per P2P CTA: 2, 4 (default) or 8    */
     int32_t p2p_chunk;         /* targets per P2P register tile: 8, 16 (default) or 32      */
-    int32_t m2l_stages;        /* tensor-core M2L pipeline stages: 2..4 (default: as many as
-                                  fit in shared memory; more than fit is clamped)            */
+    int32_t m2l_stages;        /* tensor-core M2L pipeline stages: 2..6 (default: as many as
+                                  fit in shared memory; more than fit, or fewer than 4, are
+                                  clamped)                                                   */
     int32_t m2l_split;         /* tensor-core M2L: CTAs sharing one 128-box tile's offset
                                   classes, 1..4 (default: by the tile count)                  */
     /* Optional allocator of the plan's own device buffers (tree, lists, operators,
@@ -444,7 +445,7 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  *        with FP64 translations (IMQ_TRANS_FP64), whose error floor is lower;
  *     3. on the chosen (p, leaf, translations), the P2P tile shape (p2p_warps x
  *        p2p_chunk in {2, 4, 8} x {8, 16, 32}), then the tensor-core M2L
- *        pipeline depth (m2l_stages 2..4, as far as they fit) and the number
+ *        pipeline depth (m2l_stages 4..6, as far as they fit) and the number
  *        of CTAs sharing an M2L tile (m2l_split 1..4): the fastest shape whose
  *        error still meets the target (else whose error does not grow by more
  *        than 1 %).

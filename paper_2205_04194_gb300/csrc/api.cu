@@ -195,8 +195,8 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
                 fail(IMQ_INVALID_ARG, "imq_plan: p2p_warps must be 0, 2, 4 or 8");
             if (opt->p2p_chunk != 0 && opt->p2p_chunk != 8 && opt->p2p_chunk != 16 && opt->p2p_chunk != 32)
                 fail(IMQ_INVALID_ARG, "imq_plan: p2p_chunk must be 0, 8, 16 or 32");
-            if (opt->m2l_stages != 0 && (opt->m2l_stages < 2 || opt->m2l_stages > 4))
-                fail(IMQ_INVALID_ARG, "imq_plan: m2l_stages must be 0 or 2..4");
+            if (opt->m2l_stages != 0 && (opt->m2l_stages < 2 || opt->m2l_stages > 6))
+                fail(IMQ_INVALID_ARG, "imq_plan: m2l_stages must be 0 or 2..6");
             if (opt->m2l_split < 0 || opt->m2l_split > 4) fail(IMQ_INVALID_ARG, "imq_plan: m2l_split must be 0..4");
         }
     }

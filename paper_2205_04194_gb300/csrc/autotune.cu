@@ -253,7 +253,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     if (tensor) {
         const int smax = m2l_umma_max_stages(K, K);
         const imq_tune_entry tp = out->tried[cur];
-        for (int stages = 2; stages <= smax; ++stages) {
+        for (int stages = m2l_umma_min_stages(); stages <= smax; ++stages) {
             const int k =
                 measure(chosen.p, chosen.leaf, chosen.translations, tp.p2p_warps, tp.p2p_chunk, stages, 0);
             if (better(k, cur)) cur = k;

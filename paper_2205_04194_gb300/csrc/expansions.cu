@@ -378,6 +378,8 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
     // child ids); triggering this late keeps waiting CTAs from holding SMs for long
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (UP) {
+        __shared__ int s_mx[kTS];   // largest |sum| of each parent (float bits, non-negative)
+        if (threadIdx.x < kTS) s_mx[threadIdx.x] = 0;
         __syncthreads();   // every warp is done with its staging area: reuse it for the quadrant products
         float *red = sx;   // [4][16][K]
 #pragma unroll
@@ -394,11 +396,26 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
             const float sum = ((red[(0 * kTS + g) * K + o] + red[(1 * kTS + g) * K + o]) + red[(2 * kTS + g) * K + o]) +
                               red[(3 * kTS + g) * K + o];
             X[(int64_t)s_par[g] * K + o] = sum;
-            if (Xpk) {   // the tf32 hi / lo rows the tensor-core M2L gathers
-                float *pk = Xpk + (int64_t)s_par[g] * 2 * KP;
-                const float hi = tf32_round(sum);
+            if (Xpk) atomicMax(&s_mx[g], __float_as_int(fabsf(sum)));
+        }
+        if (Xpk) {   // the scaled fp16 hi / lo rows the tensor-core M2L gathers (the same sums again)
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTS * K; e += blockDim.x) {
+                const int g = e / K, o = e - g * K;
+                if (g >= ng) continue;
+                const float sum = ((red[(0 * kTS + g) * K + o] + red[(1 * kTS + g) * K + o]) +
+                                   red[(2 * kTS + g) * K + o]) +
+                                  red[(3 * kTS + g) * K + o];
+                __half *pk = reinterpret_cast<__half *>(Xpk) + (int64_t)s_par[g] * 2 * KP;
+                __half hi, lo;
+                f16_split(sum * pow2f(m2l_pow2_exp(__int_as_float(s_mx[g]))), hi, lo);
                 pk[o] = hi;
-                pk[KP + o] = tf32_round(sum - hi);
+                pk[KP + o] = lo;
+            }
+            if (threadIdx.x < ng) {
+                __half *pk = reinterpret_cast<__half *>(Xpk) + (int64_t)s_par[threadIdx.x] * 2 * KP;
+                *reinterpret_cast<float *>(pk + m2l_scale_slot(K)) =
+                    pow2f(-m2l_pow2_exp(__int_as_float(s_mx[threadIdx.x])));
             }
         }
     } else {
@@ -694,6 +711,7 @@ static void prepare_tensor_m2l(Plan &P, TypedOps &O, int nblk, cudaStream_t s) {
         fail(IMQ_UNSUPPORTED, "imq_plan: the expansion does not fit the tensor-core M2L");
     if (P.m2l_kernel == IMQ_M2L_CUDA_CORES || !fits) return;
     m2l_umma_prepare(P, O.m2l.as<float>(), nblk, K, O.m2l_img, O.Mpk, O.m2l_tmask, O.m2l_order, O.m2l_counter, s);
+    O.m2l_nblk = nblk;
     O.umma = true;
 }
 

@@ -134,9 +134,11 @@ struct TypedOps {        // operator set in one precision
     // derivative in c (odd-parity locals): M2L even->odd, L2L odd, d/dz L2P coefficients
     DevMem m2l_odd, l2l_odd, dzc, Lodd;
     bool dz_ready = false;
-    // tensor-core M2L (FP32 only): swizzled tf32 hi/lo operator images, packed multipoles
+    // tensor-core M2L (FP32 only): swizzled fp16 hi/lo operator images and their coefficient
+    // scales, packed fp16 hi/lo multipole rows with their box scales
     DevMem m2l_img, Mpk, m2l_tmask;   // m2l_tmask: uint64 per tile, bit o = offset class o present
     DevMem m2l_order, m2l_counter;    // tiles heaviest first; the persistent kernel's work counter
+    int m2l_nblk = 0;                 // operator blocks (levels, or problem-levels) in m2l_img
     bool umma = false;
 };
 
@@ -346,7 +348,8 @@ int fmm_apply_dz(Plan &P, const T *u_sorted, T *b_sorted, int nrhs, cudaStream_t
 void build_m2l_tiles(Plan &P, cudaStream_t s);
 // p2m.cu: P2M for a compile-time order (FP32)
 bool p2m_fixed_p_supported(int p);
-// Mpk (may be null): also write the tf32 hi / lo rows [hi | pad to KP | lo | pad] of the tensor-core M2L
+// Mpk (may be null): also write the scaled fp16 hi / lo rows [hi | pad to KP | lo | pad] of the tensor-core
+// M2L, with the row's inverse scale in its padding
 void p2m_fixed_p_launch(const Plan &P, const float *u, float *M, const float *coef, cudaStream_t s,
                         float *Mpk = nullptr, int KP = 0);
 void p2l_fixed_p_prepare(cudaStream_t s);
@@ -365,11 +368,12 @@ void p2p_near_f32(Plan &P, const float *u, float *near, int nrhs, cudaStream_t s
 bool m2l_umma_supported(int K, int Kout);
 void m2l_umma_prepare(const Plan &P, const float *ops, int nblk, int Kout, DevMem &img, DevMem &Mpk, DevMem &tmask,
                       DevMem &order, DevMem &counter, cudaStream_t s);
-// packed: Mpk already holds the hi / lo rows of every box (written by P2M and M2M)
+// packed: Mpk already holds the fp16 hi / lo rows of every box (written by P2M and M2M)
 void m2l_umma_launch(const Plan &P, const float *M, float *L, const TypedOps &O, int Kout, cudaStream_t s,
                      bool packed = false);
-int m2l_umma_kp(int K);   // padded row length KP of the hi / lo rows
+int m2l_umma_kp(int K);   // padded length KP of each half (hi, lo) of a packed row
 int m2l_umma_max_stages(int K, int Kout);   // pipeline stages that fit in shared memory
+int m2l_umma_min_stages();                  // fewest pipeline stages the kernel runs with
 int m2l_default_split(int ntiles);          // CTAs per M2L tile when the plan does not choose
 // batch.cu
 template <class T>

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(32 * kP2MWarps) k_p2m_t(int nleaf, const int32
     }
     butterfly_reduce<NP>(acc, lane);
     float *Mb = M + (int64_t)b * K;
+    float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int idx = Q * lane + k;
@@ -107,18 +108,35 @@ __global__ void __launch_bounds__(32 * kP2MWarps) k_p2m_t(int nleaf, const int32
         const float vr = cc * re, vi = cc * im;
         Mb[slot] = vr;
         if (m > 0) Mb[slot + 1] = vi;
-        if (Mpk) {   // the tf32 hi / lo rows the tensor-core M2L gathers
-            float *pk = Mpk + (int64_t)b * 2 * KP;
-            const float hr = tf32_round(vr);
-            pk[slot] = hr;
-            pk[KP + slot] = tf32_round(vr - hr);
-            if (m > 0) {
-                const float hi = tf32_round(vi);
-                pk[slot + 1] = hi;
-                pk[KP + slot + 1] = tf32_round(vi - hi);
-            }
+        mx = fmaxf(mx, fmaxf(fabsf(vr), m > 0 ? fabsf(vi) : 0.f));
+    }
+    if (!Mpk) return;
+    // the scaled fp16 hi / lo rows the tensor-core M2L gathers, scale from the box's largest term
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    const int e = m2l_pow2_exp(mx);
+    const float sc = pow2f(e);
+    __half *pk = reinterpret_cast<__half *>(Mpk) + (int64_t)b * 2 * KP;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int idx = Q * lane + k;
+        if (idx >= NC) continue;
+        int m, slot;
+        decode_term<P>(idx, m, slot);
+        float re, im;
+        up2(acc[k], re, im);
+        const float cc = coef[slot];
+        __half hi, lo;
+        f16_split(cc * re * sc, hi, lo);
+        pk[slot] = hi;
+        pk[KP + slot] = lo;
+        if (m > 0) {
+            f16_split(cc * im * sc, hi, lo);
+            pk[slot + 1] = hi;
+            pk[KP + slot + 1] = lo;
         }
     }
+    if (lane == 0) *reinterpret_cast<float *>(pk + m2l_scale_slot(K)) = pow2f(-e);
 }
 
 constexpr int kP2LWarps = 4;

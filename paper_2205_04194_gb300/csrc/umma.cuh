@@ -10,6 +10,7 @@
 // start address by 32 bytes inside the atom.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "ptx.cuh"
@@ -80,6 +81,63 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr) {
     d |= (uint64_t)1u << 46;
     d |= (uint64_t)2u << 61;
     return d;
+}
+
+// 64-byte swizzle (the fp16 M2L): a row of 32 fp16 values is 64 bytes, an atom
+// is 8 rows (512 bytes), and the 16-byte chunk j (values 8j .. 8j+7) of row r
+// sits at chunk position j ^ ((r >> 1) & 3): the XOR of address bits 4-5 with
+// bits 7-8, as for the 128-byte swizzle one bit narrower.
+__host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t r, uint32_t j) {
+    return r * 64u + ((j ^ ((r >> 1) & 3u)) << 4);
+}
+// Descriptor of a K-major, 64-byte-swizzled operand: 8-row atoms 512 bytes
+// apart (stride byte offset), swizzle mode 4 = 64B (bits 61-63); a K-step of
+// 16 fp16 values advances the start address by 32 bytes inside the atom.
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16 with fp16 A and B (formats 0 at bits 7-9 and
+// 10-12), D f32 (bits 4-5 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(uint32_t M, uint32_t N) {
+    return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B^T for one K-step of 16 fp16 values; issued by a single thread.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Power-of-two scaling into the fp16 range: e with m 2^e in [2^13, 2^14) for the
+// largest magnitude m of a row (0 for a zero or non-finite m), clamped so that
+// 2^e and 2^-e are normal floats.
+__device__ __forceinline__ int m2l_pow2_exp(float m) {
+    if (!(m > 0.f) || !isfinite(m)) return 0;
+    return max(-120, min(120, 13 - ilogbf(m)));
+}
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// Half index (even) inside the hi part of a packed fp16 multipole row where the row's
+// inverse scale is kept as a float: past the K coefficients, inside the padding (for
+// every K = (p+1)(p+2)/2 with p <= 18 the padding to a multiple of 32 leaves room).
+__host__ __device__ constexpr int m2l_scale_slot(int K) { return (K + 1) & ~1; }
+
+// fp16 split x = hi + lo (each rounded to nearest), for values already scaled into
+// the fp16 range
+__device__ __forceinline__ void f16_split(float x, __half &hi, __half &lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
 }
 
 // Instruction descriptor, kind::tf32: D f32 (bits 4-5 = 1), A and B tf32

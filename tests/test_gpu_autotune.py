@@ -109,6 +109,9 @@ def test_batched_choice_meets_the_target_on_every_problem():
             exact = dense.matvec_rows(x, c, vq, rows)
             got = b[r, offs[q]:offs[q + 1]][rows]
             worst = max(worst, np.linalg.norm(got - exact) / np.linalg.norm(exact))
-    assert worst == pytest.approx(res["rel_err"], rel=1e-3)
+    # the recomputed error equals the reported one; with the M2L offset classes of a tile split
+    # over several CTAs (m2l_split > 1) their FP32 partial sums reach L by atomic adds in no fixed
+    # order, so the two products agree to rounding rather than bit for bit
+    assert worst == pytest.approx(res["rel_err"], rel=1e-3 if res["m2l_split"] <= 1 else 2e-2)
     assert worst <= 1e-6
     bp.close()
