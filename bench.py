@@ -40,16 +40,16 @@ N_SM = 152
 FP16_PER_BF16 = 1.0         # nominal dense tensor rates per GPU: fp16 and bf16 are equal
 
 
-# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum + dram__bytes_write.sum),
-# from one ncu capture of `python bench.py --steps 3 --warmup 1 --no-cpu --no-solve --p 12
-# --phase-steps 2` on the 1M clustered workload (L2 flushed between products), keyed by the
-# SHA-256 of the kernel sources at capture time: once a source changes the figure is stale
-# and the bench reports null.  Summaries: profiles/launches_fast_product_clustered_1m.md.
+# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum),
+# from one single-kernel ncu capture on the quarter-size clustered workload, scaled to the 1M launch
+# by the units it processes; keyed by the SHA-256 of the kernel sources at capture time: once a
+# source changes the figure is stale and the bench reports null.
 TRAFFIC = {
-    # k_m2l_umma: 87.44 MB read + 0.28 MB written per launch (its packed rows come from P2M / M2M)
-    "m2l": {"bytes": 87.44e6 + 0.28e6, "sources": {
-        "paper_2205_04194_gb300/csrc/m2l_umma.cu": "9e188a398c2404daff8adacc4ba048cec2aff56d02309329976aeda8ede08319",
-        "paper_2205_04194_gb300/csrc/umma.cuh": "a133f64894a1d5c359ee5202af3f44414abc786ea60768f20a375cecf456fcd6",
+    # k_m2l_umma<3>: 22.574336 MB read, 0 written per launch at N = 250,000 (267,324 V pairs), scaled by
+    # the V pairs (x 1,121,136 / 267,324) to the 1M launch
+    "m2l": {"bytes": 22.574336e6 * 1121136 / 267324, "sources": {
+        "paper_2205_04194_gb300/csrc/m2l_umma.cu": "9e0a67f53328edc9e42d70c3c353b82b6363535816ddd88947f94c6862a43e59",
+        "paper_2205_04194_gb300/csrc/umma.cuh": "ec6da3b3c75070f001a40973b94766e68b1db5c9604bc71cdac4d874440d5422",
         "paper_2205_04194_gb300/csrc/ptx.cuh": "9f11aae585d997f977cfb9515e1a6d3900bf168e91c1a75824dfdb29176bb76c"}},
 }
 
