@@ -300,7 +300,9 @@ typedef enum imq_residual {
  * GMRES minimises the residual norm over each cycle, so it keeps converging
  * where A is positive definite in exact arithmetic but not numerically (flat
  * shapes, c many times the point spacing), where CG's p.Ap or r.z loses its
- * sign and the pass ends.  Each cycle is one refinement pass. */
+ * sign and the pass ends.  Each cycle is one refinement pass.  On a batched
+ * plan every problem has its own Arnoldi scalars, Hessenberg matrix and
+ * convergence test; the vectors and the fast product are shared. */
 typedef enum imq_krylov { IMQ_KRYLOV_CG = 0, IMQ_KRYLOV_GMRES = 1 } imq_krylov;
 #define IMQ_CG_MAX_RHS_INFO 16
 
@@ -322,7 +324,7 @@ typedef struct imq_cg_options {
     int32_t coarse_points;   /* SCHWARZ_2L: max points per coarse box, 1..1024 (0: the leaf size) */
     int32_t coarse_gram;     /* SCHWARZ_2L: pairs of E = Z^T A Z in 0: FP64 if N^2 <= 4e10, else
                                 FP32 with FP64 partial sums; 1: FP64; 2: FP32                   */
-    int32_t krylov;          /* imq_krylov (single plans; batched plans run CG)                 */
+    int32_t krylov;          /* imq_krylov (batched plans: one Hessenberg matrix per problem)  */
     int32_t gmres_m;         /* GMRES restart length, 1..200 (0: 40); (m + 1) N doubles of basis */
     int32_t reserved[2];
 } imq_cg_options;
@@ -344,8 +346,9 @@ imq_status imq_cg_solve(imq_plan_t plan, const double *f, double *coef, int nrhs
  * imq_cg_solve_batched -- imq_cg_solve on a plan from imq_plan_batched: the
  * nprob systems A_b coef_b = f_b (Section 2, Eq. (3)-(4), one per problem)
  * are solved together, one fast product over all problems per iteration,
- * with per-problem CG scalars and convergence tests.  imq_cg_solve on a
- * batched plan does the same without the per-problem outputs.
+ * with per-problem Krylov scalars (CG, or GMRES with opt->krylov) and
+ * convergence tests.  imq_cg_solve on a batched plan does the same without
+ * the per-problem outputs.
  *
  *   f, coef      : double[nrhs][N_total], problems in the plan's order.
  *   rel_residual : host double[nrhs][nprob] or NULL: true relative residual

@@ -565,8 +565,6 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         try {
             if (!P.prob_off.empty() && o.precond == IMQ_PRECOND_SCHWARZ_2L)
                 fail(IMQ_UNSUPPORTED, "imq_cg_solve: the two-level preconditioner is built for single plans");
-            if (!P.prob_off.empty() && o.krylov == IMQ_KRYLOV_GMRES)
-                fail(IMQ_UNSUPPORTED, "imq_cg_solve: GMRES is built for single plans");
             if (!P.prob_off.empty())
                 cg_solve_batched(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o,
                                  info, rel_out, iters_out, s);

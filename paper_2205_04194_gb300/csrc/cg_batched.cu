@@ -208,6 +208,51 @@ __global__ void k_scatter(const double *__restrict__ v, const int32_t *__restric
     if (i < n) out[perm[i]] = v[i];
 }
 
+// ---- per-problem GMRES (Arnoldi vectors over the flattened points, every scalar per problem)
+// out[i * B + b] = (V_i . w) restricted to problem b; one block per (problem, vector)
+__global__ void __launch_bounds__(kThreads) k_seg_multi_dot(const double *__restrict__ V, int64_t n,
+                                                            const double *__restrict__ w,
+                                                            const int64_t *__restrict__ off, int B,
+                                                            double *__restrict__ out) {
+    const int b = blockIdx.x, i = blockIdx.y;
+    const int64_t lo = off[b], hi = off[b + 1];
+    const double *vi = V + (size_t)i * n;
+    double acc = 0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += kThreads) acc += vi[k] * w[k];
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) out[(size_t)i * B + b] = t;
+}
+// w -= sum_i h[i][problem] V_i
+__global__ void k_seg_multi_axpy(const double *__restrict__ V, int64_t n, int nv, const double *__restrict__ h,
+                                 const int32_t *__restrict__ prob, int B, double *__restrict__ w) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int b = prob[k];
+        double acc = 0;
+        for (int i = 0; i < nv; ++i) acc += h[(size_t)i * B + b] * V[(size_t)i * n + k];
+        w[k] -= acc;
+    }
+}
+// u = sum_i y[i][problem] V_i (y = 0 past a problem's own cycle length)
+__global__ void k_seg_lincomb(const double *__restrict__ V, int64_t n, int nv, const double *__restrict__ y,
+                              const int32_t *__restrict__ prob, int B, double *__restrict__ u) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int b = prob[k];
+        double acc = 0;
+        for (int i = 0; i < nv; ++i) acc += y[(size_t)i * B + b] * V[(size_t)i * n + k];
+        u[k] = acc;
+    }
+}
+// v = a[problem] * w
+__global__ void k_seg_scale(const double *__restrict__ w, const double *__restrict__ a,
+                            const int32_t *__restrict__ prob, int64_t n, double *__restrict__ v) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        v[k] = a[prob[k]] * w[k];
+}
+__global__ void k_f32_to_f64(const float *__restrict__ b, double *__restrict__ q, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        q[k] = (double)b[k];
+}
+
 std::vector<double> read_seg_dots(const double *a, const double *c, const int64_t *off, int B, DevMem &tmp,
                                   cudaStream_t s) {
     k_seg_dot<<<B, kThreads, 0, s>>>(a, c, off, tmp.as<double>());
@@ -280,6 +325,148 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     }
     cudaGraphExec_t exec = cap.instantiate();
 
+    // ---- GMRES(m) per problem: one restart cycle on A d = r for every active problem at once
+    // (right preconditioning, d = M u); the correction is added to xb
+    const bool gmres = o.krylov == IMQ_KRYLOV_GMRES;
+    const int gm = o.gmres_m > 0 ? o.gmres_m : 40;
+    DevMem V, hdev, ydev, scdev, zb, wv, ub;
+    if (gmres) {
+        V.alloc(sizeof(double) * (size_t)(gm + 1) * n);
+        hdev.alloc(sizeof(double) * (size_t)(gm + 1) * B);
+        ydev.alloc(sizeof(double) * (size_t)(gm + 1) * B);
+        scdev.alloc(sizeof(double) * B);
+        for (DevMem *d : {&zb, &wv, &ub}) d->alloc(8 * n);
+    }
+    const int32_t *prob = P.pt_prob.as<int32_t>();
+    auto apply_A = [&](const double *in, double *out) {
+        if (dense_op) {
+            dense_f64_seg_async(dpos, doff, B, dprob_c, in, out, n, s);
+        } else if (f64op) {
+            fmm_apply<double>(P, in, out, 1, s);
+        } else {
+            k_to_f32<<<gs, 256, 0, s>>>(in, u32.as<float>(), n);
+            fmm_apply<float>(P, u32.as<float>(), b32.as<float>(), 1, s);
+            k_f32_to_f64<<<gs, 256, 0, s>>>(b32.as<float>(), out, n);
+            IMQ_LAUNCH_CHECK();
+        }
+    };
+    auto apply_M = [&](const double *in, double *out) {
+        if (pre) schwarz_apply(P, P.schwarz, in, out, P.c, n, nullptr, s);
+        else IMQ_CUDA(cudaMemcpyAsync(out, in, 8 * n, cudaMemcpyDeviceToDevice, s));
+    };
+    auto seg_scale = [&](const double *w, const std::vector<double> &a, double *v) {
+        IMQ_CUDA(cudaMemcpyAsync(scdev.ptr, a.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+        k_seg_scale<<<gs, 256, 0, s>>>(w, scdev.as<double>(), prob, n, v);
+        IMQ_LAUNCH_CHECK();
+    };
+    // r holds each active problem's residual (zero on the others); returns per-problem iterations
+    auto gmres_cycle = [&](const std::vector<double> &target, const std::vector<int> &budget,
+                           std::vector<int> &its, std::vector<char> &bad) {
+        double *Vp = V.as<double>();
+        const std::vector<double> bb = read_seg_dots(r.as<double>(), r.as<double>(), doff, B, tmp, s);
+        std::vector<double> beta(B), sc(B, 0.0);
+        std::vector<char> live(B, 0);
+        std::vector<int> kb(B, 0);
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            beta[b] = std::sqrt(bb[b]);
+            if (!std::isfinite(beta[b])) {
+                bad[b] = 1;
+                continue;
+            }
+            live[b] = beta[b] > target[b] && budget[b] > 0;
+            sc[b] = live[b] ? 1.0 / beta[b] : 0.0;
+            any |= live[b] != 0;
+        }
+        if (!any) return;
+        seg_scale(r.as<double>(), sc, Vp);
+        const size_t HS = (size_t)(gm + 1) * gm;
+        std::vector<double> H(HS * B, 0.0), cs((size_t)gm * B), sn((size_t)gm * B), gv((size_t)(gm + 1) * B, 0.0),
+            hh((size_t)(gm + 1) * B);
+        auto Hb = [&](int b, int i, int j) -> double & { return H[(size_t)b * HS + (size_t)j * (gm + 1) + i]; };
+        for (int b = 0; b < B; ++b) gv[(size_t)b * (gm + 1)] = beta[b];
+        int jmax = 0;
+        for (int j = 0; j < gm && any; ++j) {
+            apply_M(Vp + (size_t)j * n, zb.as<double>());
+            apply_A(zb.as<double>(), wv.as<double>());
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                k_seg_multi_dot<<<dim3(B, j + 1), kThreads, 0, s>>>(Vp, n, wv.as<double>(), doff, B,
+                                                                    hdev.as<double>());
+                k_seg_multi_axpy<<<gs, 256, 0, s>>>(Vp, n, j + 1, hdev.as<double>(), prob, B, wv.as<double>());
+                IMQ_LAUNCH_CHECK();
+                IMQ_CUDA(cudaMemcpyAsync(hh.data(), hdev.ptr, sizeof(double) * (size_t)(j + 1) * B,
+                                         cudaMemcpyDeviceToHost, s));
+                IMQ_CUDA(cudaStreamSynchronize(s));
+                for (int b = 0; b < B; ++b)
+                    if (live[b])
+                        for (int i = 0; i <= j; ++i) Hb(b, i, j) += hh[(size_t)i * B + b];
+            }
+            const std::vector<double> hn2 = read_seg_dots(wv.as<double>(), wv.as<double>(), doff, B, tmp, s);
+            jmax = j + 1;
+            any = false;
+            for (int b = 0; b < B; ++b) {
+                sc[b] = 0.0;
+                if (!live[b]) continue;
+                double *g = &gv[(size_t)b * (gm + 1)];
+                double *c = &cs[(size_t)b * gm], *sv = &sn[(size_t)b * gm];
+                const double hn = std::sqrt(hn2[b]);
+                Hb(b, j + 1, j) = hn;
+                ++its[b];
+                kb[b] = j + 1;
+                for (int i = 0; i < j; ++i) {   // earlier rotations on the new column
+                    const double a = Hb(b, i, j), e = Hb(b, i + 1, j);
+                    Hb(b, i, j) = c[i] * a + sv[i] * e;
+                    Hb(b, i + 1, j) = -sv[i] * a + c[i] * e;
+                }
+                const double a = Hb(b, j, j), e = Hb(b, j + 1, j), rho = std::hypot(a, e);
+                if (!std::isfinite(rho)) {
+                    bad[b] = 1;
+                    live[b] = 0;
+                    kb[b] = 0;
+                    continue;
+                }
+                c[j] = rho > 0 ? a / rho : 1.0;
+                sv[j] = rho > 0 ? e / rho : 0.0;
+                Hb(b, j, j) = rho;
+                Hb(b, j + 1, j) = 0;
+                g[j + 1] = -sv[j] * g[j];
+                g[j] = c[j] * g[j];
+                if (std::fabs(g[j + 1]) <= target[b] || hn == 0 || its[b] >= budget[b]) {
+                    live[b] = 0;
+                    continue;
+                }
+                sc[b] = 1.0 / hn;
+                any = true;
+            }
+            seg_scale(wv.as<double>(), sc, Vp + (size_t)(j + 1) * n);
+        }
+        // y_b from H_b(0:k, 0:k) y_b = g_b(0:k), problem by problem
+        std::vector<double> y((size_t)(gm + 1) * B, 0.0);
+        for (int b = 0; b < B; ++b) {
+            const int k = kb[b];
+            const double *g = &gv[(size_t)b * (gm + 1)];
+            for (int i = k - 1; i >= 0; --i) {
+                double t = g[i];
+                for (int l = i + 1; l < k; ++l) t -= Hb(b, i, l) * y[(size_t)l * B + b];
+                const double d = Hb(b, i, i);
+                y[(size_t)i * B + b] = d != 0 ? t / d : 0.0;
+                if (!std::isfinite(y[(size_t)i * B + b])) {
+                    bad[b] = 1;
+                    for (int l = 0; l < k; ++l) y[(size_t)l * B + b] = 0.0;
+                    break;
+                }
+            }
+        }
+        if (jmax == 0) return;
+        IMQ_CUDA(cudaMemcpyAsync(ydev.ptr, y.data(), sizeof(double) * (size_t)jmax * B, cudaMemcpyHostToDevice, s));
+        k_seg_lincomb<<<gs, 256, 0, s>>>(Vp, n, jmax, ydev.as<double>(), prob, B, ub.as<double>());
+        IMQ_LAUNCH_CHECK();
+        apply_M(ub.as<double>(), zb.as<double>());
+        k_add<<<gs, 256, 0, s>>>(xb.as<double>(), zb.as<double>(), n);
+        IMQ_LAUNCH_CHECK();
+        IMQ_CUDA(cudaStreamSynchronize(s));   // y lives on the host
+    };
+
     const auto t0 = std::chrono::steady_clock::now();
     int total_iter = 0, outer_done = 0, final_status = kConverged;
     double worst_rel = 0;
@@ -297,6 +484,8 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             std::vector<int> status(B, kMaxIter), iters(B, 0);
             const int max_outer = std::max(0, o.refine_steps);
             int restarts = 0;
+            std::vector<double> prev_rel(B, 0.0);
+            std::vector<char> stalled(B, 0);
             auto true_residual = [&]() {
                 if (dense_res) dense_f64_seg_async(dpos, doff, B, dprob_c, xs.as<double>(), ax.as<double>(), n, s);
                 else fmm_apply<double>(P, xs.as<double>(), ax.as<double>(), 1, s);
@@ -321,10 +510,39 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                     else if (rel[b] <= o.rtol) status[b] = kConverged;
                     else {
                         status[b] = kMaxIter;
-                        if (iters[b] < o.maxit) any = true;
+                        // GMRES cycles without refinement steps continue while each lowers the true residual
+                        if (gmres && max_outer == 0 && outer > 0 && !(rel[b] < 0.999 * prev_rel[b])) stalled[b] = 1;
+                        if (iters[b] < o.maxit && !stalled[b]) any = true;
                     }
+                    prev_rel[b] = rel[b];
                 }
-                if (!any || (max_outer > 0 ? outer >= max_outer : outer > restarts)) break;
+                if (!any || (max_outer > 0 ? outer >= max_outer : (!gmres && outer > restarts))) break;
+                if (gmres) {
+                    // problems not in this cycle: zero residual segments (their correction is zero)
+                    std::vector<double> keep(B), target(B);
+                    std::vector<int> budget(B), its(B, 0);
+                    std::vector<char> bad(B, 0);
+                    for (int b = 0; b < B; ++b) {
+                        const bool act = status[b] == kMaxIter && iters[b] < o.maxit && !stalled[b];
+                        keep[b] = act ? 1.0 : 0.0;
+                        const double inner_rtol =
+                            max_outer > 0 ? std::max(o.inner_rtol, std::min(0.5, 0.5 * o.rtol / rel[b]))
+                                          : 0.5 * o.rtol / rel[b];
+                        target[b] = inner_rtol * std::sqrt(rr0[b]);
+                        budget[b] = act ? o.maxit - iters[b] : 0;
+                    }
+                    seg_scale(r.as<double>(), keep, r.as<double>());
+                    IMQ_CUDA(cudaMemsetAsync(xb.ptr, 0, 8 * n, s));
+                    gmres_cycle(target, budget, its, bad);
+                    k_add<<<gs, 256, 0, s>>>(xs.as<double>(), xb.as<double>(), n);
+                    IMQ_LAUNCH_CHECK();
+                    outer_done = std::max(outer_done, outer + 1);
+                    for (int b = 0; b < B; ++b) {
+                        iters[b] += its[b];
+                        if (bad[b]) status[b] = kNumerical;
+                    }
+                    continue;
+                }
                 IMQ_CUDA(cudaMemsetAsync(x.ptr, 0, 8 * n, s));
                 IMQ_CUDA(cudaMemsetAsync(xb.ptr, 0, 8 * n, s));
                 std::vector<double> rz = rr0;

@@ -79,18 +79,42 @@ def test_gmres_full_size_clustered_1m_metric_solve():
     torch.cuda.synchronize()
 
 
-def test_gmres_rejected_on_batched_plans_and_bad_options():
+def test_gmres_batched_meets_1e9_on_every_problem_against_the_oracle():
+    """Per-problem GMRES on a batched plan (three problems of different size, c = 2h each, as in the
+    batched CG tests), dense FP64 residuals and FP64 refinement: each problem's coefficients are
+    certified by the oracle, and each problem needs about as many iterations as the same solve on
+    its own single plan (the batched product equals the per-problem products)."""
     need_gpu()
     from paper_2205_04194_gb300 import imq
-    pts = [W.uniform_points(500, 1, stream=k) for k in range(2)]
-    bp = imq.BatchedPlan([cuda(x) for x in pts], [0.05, 0.05], 8, 32, domain=(0.0, 0.0, 1.0))
-    with pytest.raises(imq.ImqError) as e:
-        bp._solve("imq_cg_solve_batched", cuda(np.ones(1000)), None, None, None, True, 2, dict(
-            rtol=1e-6, maxit=10, precond="schwarz", schwarz_nmax=128, schwarz_shift=0.0, refine_steps=0,
-            inner_rtol=1e-4, residual="plan", residual_plan=None, operator="fast_f32", schwarz_fp64=False,
-            krylov="gmres"))
-    assert e.value.status == 7
-    plan = imq.Plan(cuda(pts[0]), 0.05, 8, 32, domain=(0.0, 0.0, 1.0))
+    sizes = [900, 2000, 3100]
+    pts = [W.uniform_points(n, 31, stream=k) for k, n in enumerate(sizes)]
+    cs = [2.0 * W.mean_nn_spacing(x) for x in pts]
+    fs = [np.sin(6 * x[:, 0]) * np.cos(4 * x[:, 1]) for x in pts]
+    kw = dict(rtol=1e-9, maxit=4000, precond="schwarz", residual="dense", refine_steps=10, inner_rtol=1e-5,
+              krylov="gmres", gmres_m=40)
+    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, 12, 32, domain=(0.0, 0.0, 1.0))
+    coef, info = bp.solve(cuda(np.concatenate(fs)), **kw)
+    assert info["status"] == "IMQ_OK", info
+    coef = host(coef)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for k in range(len(sizes)):
+        r = OS.true_relres(pts[k], cs[k], coef[offs[k]:offs[k + 1]], fs[k])
+        assert r <= 1e-9, (k, r)
+        assert info["problem_rel_residual"][0, k] == pytest.approx(r, rel=1e-2, abs=1e-12)
+        sp = imq.Plan(cuda(pts[k]), cs[k], 12, 32, domain=(0.0, 0.0, 1.0))
+        _, i1 = sp.solve(cuda(fs[k]), **kw)
+        assert i1["status"] == "IMQ_OK", i1
+        its = int(info["problem_iterations"][0, k])
+        assert 0.5 * i1["iterations"] <= its <= 1.5 * i1["iterations"] + 5, (k, its, i1["iterations"])
+        sp.close()
+    bp.close()
+
+
+def test_gmres_rejects_bad_options():
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    pts = W.uniform_points(500, 1)
+    plan = imq.Plan(cuda(pts), 0.05, 8, 32, domain=(0.0, 0.0, 1.0))
     with pytest.raises(imq.ImqError) as e:
         plan.solve(cuda(np.ones(500)), krylov="gmres", gmres_m=201, raise_on_failure=True)
     assert e.value.status == 1
