@@ -270,13 +270,16 @@ def run_batched(args, imq, dev):
                      "sampled_rel2_err_max": float(errs.max()), "meets_1e-6": bool(errs.max() <= 1e-6),
                      "sampled_rel2_err_max_per_rhs": errs.max(axis=0).tolist(), "sampled_problems": 16}
         if kw.get("translations", "fp32") == "fp32" and "cg" not in out:   # solves on the FP32-translation plan
-            for key, kk in (("cg", dict(krylov="cg")), ("gmres", dict(krylov="gmres", gmres_m=40))):
-                coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, precond="schwarz",
-                                      schwarz_shift=1e-4, **kk)
+            for key, kk in (("cg", dict(krylov="cg")), ("gmres", dict(krylov="gmres", gmres_m=40)),
+                            ("gmres_two_level", dict(krylov="gmres", gmres_m=40, precond="schwarz2",
+                                                     coarse_points=1024))):
+                kk = dict(dict(precond="schwarz"), **kk)
+                coef, info = bp.solve(f, rtol=1e-6, maxit=args.batched_cg_maxit, schwarz_shift=1e-4, **kk)
                 rel = info["problem_rel_residual"]
                 out[key] = {"rtol": 1e-6, "maxit_per_rhs": args.batched_cg_maxit,
                             "krylov": "PCG" if kk["krylov"] == "cg" else "GMRES(40), per-problem scalars",
-                            "precond": "schwarz (224-point patches, shift 1e-4/c)",
+                            "precond": kk["precond"] + " (224-point patches, shift 1e-4/c"
+                                       + (", coarse boxes <= 1024 points per problem)" if "coarse_points" in kk else ")"),
                             "status": info["status"], "iterations_max": info["iterations"],
                             "solve_s": info["seconds"], "converged_fraction": float((rel <= 1e-6).mean()),
                             "rel_residual_median": float(np.median(rel)), "rel_residual_max": float(rel.max()),

@@ -279,8 +279,9 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
  * coarse_points points), E = Z^T A Z assembled exactly over every pair and
  * inverted in FP64 once; applied in the deflated form z = y + Q (r - A y),
  * y the patch solves, Q = Z E^{-1} Z^T, each inner pass started from Q r.
- * One extra FP32 fast product per iteration; single plans only, at most
- * 16384 coarse boxes.  (Section 4 leaves the preconditioner to future work;
+ * One extra FP32 fast product per iteration; at most 16384 coarse boxes.  On a
+ * batched plan the coarse boxes are each problem's own (E is block diagonal)
+ * and the two-level preconditioner runs with GMRES only.  (Section 4 leaves the preconditioner to future work;
  * Section 1 cites preconditioned iterations.) */
 typedef enum imq_precond { IMQ_PRECOND_NONE = 0, IMQ_PRECOND_SCHWARZ = 1, IMQ_PRECOND_SCHWARZ_2L = 2 } imq_precond;
 typedef enum imq_operator {

@@ -563,8 +563,8 @@ imq_status cg_entry(imq_plan_t plan, const double *f, double *coef, int nrhs, co
         DevOut dx(coef, bytes, s);
         if (o.x0_given && dx.tmp) IMQ_CUDA(cudaMemcpyAsync(dx.ptr, coef, bytes, cudaMemcpyHostToDevice, s));
         try {
-            if (!P.prob_off.empty() && o.precond == IMQ_PRECOND_SCHWARZ_2L)
-                fail(IMQ_UNSUPPORTED, "imq_cg_solve: the two-level preconditioner is built for single plans");
+            if (!P.prob_off.empty() && o.precond == IMQ_PRECOND_SCHWARZ_2L && o.krylov != IMQ_KRYLOV_GMRES)
+                fail(IMQ_UNSUPPORTED, "imq_cg_solve: on batched plans the two-level preconditioner runs with GMRES");
             if (!P.prob_off.empty())
                 cg_solve_batched(P, static_cast<const double *>(df.ptr), static_cast<double *>(dx.ptr), nrhs, o,
                                  info, rel_out, iters_out, s);

@@ -191,6 +191,11 @@ __global__ void k_sub(double *__restrict__ r, const double *__restrict__ f, cons
         r[i] = f[i] - ax[i];
 }
 
+__global__ void k_sub_from(double *__restrict__ r, const double *__restrict__ ax, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] -= ax[i];
+}
+
 __global__ void k_add(double *__restrict__ y, const double *__restrict__ x, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] += x[i];
@@ -275,9 +280,12 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     const bool dense_op = o.inner_operator == IMQ_OPERATOR_DENSE_F64;
     ensure_ops(P, false, s);
     if (!dense_res || o.inner_operator == IMQ_OPERATOR_FAST_F64) ensure_ops(P, true, s);   // FP64 fast product
-    if (o.precond == IMQ_PRECOND_SCHWARZ)
-        schwarz_setup(P, schwarz_nmax_of(o), o.schwarz_shift, o.schwarz_fp64 != 0, s);
-    const bool pre = o.precond == IMQ_PRECOND_SCHWARZ;
+    const bool two_level = o.precond == IMQ_PRECOND_SCHWARZ_2L;
+    if (two_level && o.krylov != IMQ_KRYLOV_GMRES)
+        fail(IMQ_UNSUPPORTED, "imq_cg_solve_batched: the two-level preconditioner runs with GMRES on batched plans");
+    const bool pre = o.precond == IMQ_PRECOND_SCHWARZ || two_level;
+    if (pre) schwarz_setup(P, schwarz_nmax_of(o), o.schwarz_shift, o.schwarz_fp64 != 0, s);
+    if (two_level) coarse_setup(P, o.coarse_points > 0 ? o.coarse_points : P.leaf, o.coarse_gram, s);
     const bool f64op = o.inner_operator == IMQ_OPERATOR_FAST_F64;
     const double *dpos = P.pos.as<double>(), *dprob_c = P.prob_c.as<double>();
 
@@ -329,13 +337,13 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
     // (right preconditioning, d = M u); the correction is added to xb
     const bool gmres = o.krylov == IMQ_KRYLOV_GMRES;
     const int gm = o.gmres_m > 0 ? o.gmres_m : 40;
-    DevMem V, hdev, ydev, scdev, zb, wv, ub;
+    DevMem V, hdev, ydev, scdev, zb, wv, ub, ay;
     if (gmres) {
         V.alloc(sizeof(double) * (size_t)(gm + 1) * n);
         hdev.alloc(sizeof(double) * (size_t)(gm + 1) * B);
         ydev.alloc(sizeof(double) * (size_t)(gm + 1) * B);
         scdev.alloc(sizeof(double) * B);
-        for (DevMem *d : {&zb, &wv, &ub}) d->alloc(8 * n);
+        for (DevMem *d : {&zb, &wv, &ub, &ay}) d->alloc(8 * n);
     }
     const int32_t *prob = P.pt_prob.as<int32_t>();
     auto apply_A = [&](const double *in, double *out) {
@@ -350,9 +358,18 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
             IMQ_LAUNCH_CHECK();
         }
     };
+    // z = M r: the patch solves y, and with the coarse level z = y + Q (r - A y)
     auto apply_M = [&](const double *in, double *out) {
-        if (pre) schwarz_apply(P, P.schwarz, in, out, P.c, n, nullptr, s);
-        else IMQ_CUDA(cudaMemcpyAsync(out, in, 8 * n, cudaMemcpyDeviceToDevice, s));
+        if (!pre) {
+            IMQ_CUDA(cudaMemcpyAsync(out, in, 8 * n, cudaMemcpyDeviceToDevice, s));
+            return;
+        }
+        schwarz_apply(P, P.schwarz, in, out, P.c, n, nullptr, s);
+        if (!two_level) return;
+        apply_A(out, ay.as<double>());
+        coarse_restrict(P, in, nullptr, ay.as<double>(), nullptr, s);
+        coarse_solve(P, nullptr, s);
+        coarse_prolong(P, out, out, nullptr, s);
     };
     auto seg_scale = [&](const double *w, const std::vector<double> &a, double *v) {
         IMQ_CUDA(cudaMemcpyAsync(scdev.ptr, a.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
@@ -533,6 +550,14 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                     }
                     seg_scale(r.as<double>(), keep, r.as<double>());
                     IMQ_CUDA(cudaMemsetAsync(xb.ptr, 0, 8 * n, s));
+                    if (two_level) {   // start from the coarse solution d = Q r, r -= A d (zero off the cycle)
+                        coarse_restrict(P, r.as<double>(), nullptr, nullptr, nullptr, s);
+                        coarse_solve(P, nullptr, s);
+                        coarse_prolong(P, nullptr, xb.as<double>(), nullptr, s);
+                        apply_A(xb.as<double>(), ay.as<double>());
+                        k_sub_from<<<gs, 256, 0, s>>>(r.as<double>(), ay.as<double>(), n);
+                        IMQ_LAUNCH_CHECK();
+                    }
                     gmres_cycle(target, budget, its, bad);
                     k_add<<<gs, 256, 0, s>>>(xs.as<double>(), xb.as<double>(), n);
                     IMQ_LAUNCH_CHECK();

@@ -8,7 +8,8 @@
 // Galerkin coarse space:
 //
 //   Z   : one indicator vector per coarse box, the largest tree boxes holding
-//         at most cp points (disjoint Morton ranges that cover every point);
+//         at most cp points (disjoint Morton ranges that cover every point; on a
+//         batched plan each problem's own boxes, so E is block diagonal);
 //   E   = Z^T A Z, E_ab = sum_{i in a} sum_{j in b} 1 / sqrt(|x_i - x_j|^2 + c^2);
 //   Q   = Z E^{-1} Z^T.
 //
@@ -43,10 +44,14 @@ constexpr double kGramFp64Pairs = 4e10;   // largest N^2 whose Galerkin matrix i
 // sources folded into FP64.  T = double: every pair in FP64 (for problems whose
 // N^2 the FP64 units finish quickly; the coarse correction amplifies any error
 // of E by the patch solves' norm).
+// On a batched plan (cprob != nullptr) each coarse box belongs to one problem: pairs of
+// different problems are zero (A is block diagonal) and a problem's pairs use its own c.
 template <class T>
 __global__ void __launch_bounds__(kGramThreads) k_coarse_gram(int nc, const int32_t *__restrict__ cbeg,
                                                                const double2 *__restrict__ ccen,
                                                                const double2 *__restrict__ pos, double c,
+                                                               const int32_t *__restrict__ cprob,
+                                                               const double *__restrict__ prob_c,
                                                                double *__restrict__ E) {
     __shared__ T srcx[kGramThreads * kGramTPT], srcy[kGramThreads * kGramTPT];
     __shared__ double sh[kGramThreads / 32][32];
@@ -68,9 +73,11 @@ __global__ void __launch_bounds__(kGramThreads) k_coarse_gram(int nc, const int3
             nt = k + 1;
         }
     }
-    const T c2 = (T)(c * c);
+    const double ca_c = cprob ? prob_c[cprob[a]] : c;
+    const T c2 = (T)(ca_c * ca_c);
     for (int b = 0; b < nc; ++b) {
-        const int b0 = cbeg[b], nb = cbeg[b + 1] - b0;
+        const bool same = !cprob || cprob[b] == cprob[a];   // uniform over the block
+        const int b0 = cbeg[b], nb = same ? cbeg[b + 1] - b0 : 0;
         const double2 cb = ccen[b];
         const T dx0 = (T)(ca.x - cb.x), dy0 = (T)(ca.y - cb.y);
         __syncthreads();   // the previous box's sources are no longer read
@@ -199,21 +206,27 @@ void cusolver_check(cusolverStatus_t st, const char *what) {
 void coarse_setup(Plan &P, int cp, int gram, cudaStream_t s) {
     Coarse &C = P.coarse;
     if (C.ready && C.cp == cp && C.gram_mode == gram) return;
-    if (P.nprob > 1) fail(IMQ_UNSUPPORTED, "two-level Schwarz: batched plans are not supported");
     if (cp < 1 || cp > kGramThreads * kGramTPT)
         fail(IMQ_INVALID_ARG, "two-level Schwarz: coarse_points must be in [1, 1024]");
     // ---- coarse boxes: the largest boxes holding at most cp points, in Morton order
     const int nb = P.nbox;
-    std::vector<int32_t> beg(nb), en(nb), ch(4 * (size_t)nb);
+    const bool batched = P.nprob > 1;
+    std::vector<int32_t> beg(nb), en(nb), ch(4 * (size_t)nb), par(nb), bprob(batched ? nb : 0);
     std::vector<double2> cen(nb);
+    IMQ_CUDA(cudaMemcpyAsync(par.data(), P.parent.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
+    if (batched)
+        IMQ_CUDA(cudaMemcpyAsync(bprob.data(), P.box_prob.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(beg.data(), P.begin.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(en.data(), P.end.ptr, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(ch.data(), P.child.ptr, sizeof(int32_t) * 4 * (size_t)nb, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaMemcpyAsync(cen.data(), P.centre.ptr, sizeof(double2) * nb, cudaMemcpyDeviceToHost, s));
     IMQ_CUDA(cudaStreamSynchronize(s));
-    std::vector<int32_t> cb{0};
+    std::vector<int32_t> cb{0}, cpr;
     std::vector<double2> cc;
-    std::vector<int> stack{0};
+    // one root per problem (box order = problem order), each walked in Morton order
+    std::vector<int> stack;
+    for (int b = nb - 1; b >= 0; --b)
+        if (par[b] < 0) stack.push_back(b);
     while (!stack.empty()) {
         const int b = stack.back();
         stack.pop_back();
@@ -227,6 +240,7 @@ void coarse_setup(Plan &P, int cp, int gram, cudaStream_t s) {
             if (beg[b] != cb.back()) fail(IMQ_CUDA_ERROR, "two-level Schwarz: coarse boxes are not contiguous");
             cb.push_back(en[b]);
             cc.push_back(cen[b]);
+            cpr.push_back(batched ? bprob[b] : 0);
             continue;
         }
         for (int q = 3; q >= 0; --q)   // children in Morton order
@@ -239,17 +253,20 @@ void coarse_setup(Plan &P, int cp, int gram, cudaStream_t s) {
                                   std::to_string(kCoarseMax) + "; raise coarse_points");
     C.cbeg.alloc(sizeof(int32_t) * (nc + 1));
     IMQ_CUDA(cudaMemcpyAsync(C.cbeg.ptr, cb.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
-    AsyncMem dcen(sizeof(double2) * nc, s), E(sizeof(double) * (size_t)nc * nc, s);
+    AsyncMem dcen(sizeof(double2) * nc, s), E(sizeof(double) * (size_t)nc * nc, s), dcpr(sizeof(int32_t) * nc, s);
     IMQ_CUDA(cudaMemcpyAsync(dcen.ptr, cc.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, s));
+    IMQ_CUDA(cudaMemcpyAsync(dcpr.ptr, cpr.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+    const int32_t *cprob = batched ? dcpr.as<int32_t>() : nullptr;
+    const double *pc = batched ? P.prob_c.as<double>() : nullptr;
     // ---- Galerkin matrix, every pair
     // FP64 pairs while N^2 stays within about a second of the FP64 units, FP32 pairs beyond
     C.gram_fp64 = gram == 1 || (gram == 0 && (double)P.N * (double)P.N <= kGramFp64Pairs);
     if (C.gram_fp64)
         k_coarse_gram<double><<<nc, kGramThreads, 0, s>>>(nc, C.cbeg.as<int32_t>(), dcen.as<double2>(),
-                                                          P.pos.as<double2>(), P.c, E.as<double>());
+                                                          P.pos.as<double2>(), P.c, cprob, pc, E.as<double>());
     else
         k_coarse_gram<float><<<nc, kGramThreads, 0, s>>>(nc, C.cbeg.as<int32_t>(), dcen.as<double2>(),
-                                                         P.pos.as<double2>(), P.c, E.as<double>());
+                                                         P.pos.as<double2>(), P.c, cprob, pc, E.as<double>());
     IMQ_LAUNCH_CHECK();
     const unsigned gq = blocks_for((int64_t)nc * nc, 256);
     k_symmetrize<<<gq, 256, 0, s>>>(E.as<double>(), nc);

@@ -341,15 +341,17 @@ class BatchedPlan(Plan):
 
     def solve(self, f, coef=None, rtol=1e-6, maxit=1000, precond="schwarz", schwarz_nmax=0,
               schwarz_shift=0.0, refine_steps=0, inner_rtol=1e-4, x0=None, operator="fast_f32",
-              schwarz_fp64=False, residual="plan", krylov="cg", gmres_m=0, stream=None, raise_on_failure=False):
+              schwarz_fp64=False, residual="plan", krylov="cg", gmres_m=0, coarse_points=0, coarse_gram="auto",
+              stream=None, raise_on_failure=False):
         """imq_cg_solve_batched: every problem's system at once, per-problem Krylov scalars (CG, or
-        GMRES(gmres_m) with a Hessenberg matrix per problem).
+        GMRES(gmres_m) with a Hessenberg matrix per problem; precond="schwarz2" needs GMRES).
         residual="dense" certifies each problem with its own dense FP64 product.
         info adds "problem_rel_residual" and "problem_iterations" ([nrhs, n_problems])."""
         return self._solve("imq_cg_solve_batched", f, coef, x0, stream, raise_on_failure, self.n_problems, dict(
             rtol=rtol, maxit=maxit, precond=precond, schwarz_nmax=schwarz_nmax, schwarz_shift=schwarz_shift,
             refine_steps=refine_steps, inner_rtol=inner_rtol, residual=residual, residual_plan=None,
-            operator=operator, schwarz_fp64=schwarz_fp64, krylov=krylov, gmres_m=gmres_m))
+            operator=operator, schwarz_fp64=schwarz_fp64, krylov=krylov, gmres_m=gmres_m,
+            coarse_points=coarse_points, coarse_gram=coarse_gram))
 
 
 def dense_matvec(points, c: float, v, out=None, stream=None):

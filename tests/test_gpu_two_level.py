@@ -54,7 +54,7 @@ def test_two_level_with_the_fp32_fast_operator_and_refinement():
         assert r < 2e-4   # the FP32 operator's noise floor on this flat shape
 
 
-def test_two_level_rejected_on_batched_plans():
+def test_two_level_with_cg_rejected_on_batched_plans():
     need_gpu()
     from paper_2205_04194_gb300 import imq
     pts = [W.uniform_points(500, 1, stream=k) for k in range(2)]
@@ -64,3 +64,28 @@ def test_two_level_rejected_on_batched_plans():
             rtol=1e-6, maxit=10, precond="schwarz2", schwarz_nmax=128, schwarz_shift=0.0, refine_steps=0,
             inner_rtol=1e-4, residual="plan", residual_plan=None, operator="fast_f32", schwarz_fp64=False))
     assert e.value.status == 7
+
+
+def test_two_level_gmres_on_a_batched_plan_meets_1e6_per_problem():
+    """Three problems in one batched plan: the clustered analogue's generator at two scales (c/h ~ 40
+    in the clusters) and a uniform set at c = 4 h.  Per-problem GMRES with the two-level
+    preconditioner, whose coarse boxes are each problem's own (a block-diagonal Galerkin matrix),
+    meets 1e-6 on every problem's oracle residual."""
+    need_gpu()
+    from paper_2205_04194_gb300 import imq
+    p1 = W.clustered_points(int(round(87_500 * 0.005)), 8, int(round(300_000 * 0.005)), 0.03, 3)
+    p2 = W.clustered_points(int(round(87_500 * 0.004)), 8, int(round(300_000 * 0.004)), 0.03, 5)
+    p3 = W.uniform_points(2500, 9)
+    pts = [p1, p2, p3]
+    cs = [0.01 / np.sqrt(0.005), 0.01 / np.sqrt(0.004), 4.0 * W.mean_nn_spacing(p3)]
+    fs = [W.franke(x) for x in pts]
+    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, 12, 64, domain=(0.0, 0.0, 1.0))
+    coef, info = bp.solve(cuda(np.concatenate(fs)), rtol=1e-6, maxit=2000, precond="schwarz2", coarse_points=256,
+                          schwarz_shift=1e-4, residual="dense", krylov="gmres", gmres_m=40)
+    assert info["status"] == "IMQ_OK", info
+    coef = host(coef)
+    offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in pts])])
+    for k in range(3):
+        r = OS.true_relres(pts[k], cs[k], coef[offs[k]:offs[k + 1]], fs[k])
+        assert r <= 1e-6, (k, r)
+    bp.close()
