@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -282,6 +283,15 @@ struct Plan {
     // statistics
     int64_t p2p_pairs = 0, m2l_pairs = 0;
     int64_t device_bytes() const;
+    // CUDA graph of the FP32 product (gather, expansions, near field, scatter) on the plan's own
+    // input / output buffers, replayed by calls that synchronise anyway (host buffers); declared
+    // last so that it is released before the streams and buffers it refers to
+    struct ProductGraph {
+        std::unique_ptr<GraphCapture> cap;
+        cudaGraphExec_t exec = nullptr;
+        int nrhs = 0;
+        DevMem in, out, us, bs;
+    } pgraph;
 };
 
 // Optional per-phase timing of a product with CUDA events on the launching stream.

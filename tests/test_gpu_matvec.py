@@ -69,6 +69,29 @@ def test_fast_plain_2k():
     _fast_case(wl.points, wl.c, wl.p, wl.leaf, wl.domain)
 
 
+def test_fast_host_buffers_replay_the_same_product():
+    """Host input / output buffers run the plan's cached graph of the product: pinned and pageable
+    buffers, repeated calls and a change of nrhs give the bits of the device-buffer product."""
+    import torch
+    imq = _imq()
+    pts = W.clustered_points(1500, 8, 6000, 0.03, 4)
+    plan = imq.Plan(cuda(pts), 0.01, 12, 64, domain=(0.0, 0.0, 1.0))
+    n = pts.shape[0]
+    v2 = np.random.default_rng(7).uniform(-1, 1, (2, n)).astype(np.float32)
+    ref1 = host(plan.matvec(cuda(v2[0])))
+    ref2 = host(plan.matvec(cuda(v2)))
+    for _ in range(2):
+        pinned = torch.from_numpy(v2[0].copy()).pin_memory()
+        out = torch.empty(n, dtype=torch.float32).pin_memory()
+        plan.matvec(pinned, out)
+        assert np.array_equal(out.numpy(), ref1)
+        out2 = np.empty((2, n), dtype=np.float32)
+        plan.matvec(v2, out2)                      # pageable numpy buffers, nrhs = 2
+        assert np.array_equal(out2, ref2)
+    assert rel2(ref1, dense.matvec(pts, 0.01, v2[0].astype(np.float64))) <= 1e-6
+    plan.close()
+
+
 def test_fast_clustered_small_c():
     pts = W.clustered_points(1500, 8, 6000, 0.03, 3)
     _fast_case(pts, 0.01, 12, 64, nrhs=2)
