@@ -131,26 +131,31 @@ def test_fast_full_size_clustered_1m_sampled_rows():
     assert rel2(b[rows], ref) < 1e-6
 
 
-@pytest.mark.parametrize("p,leaf", [(8, 32), (12, 64), (16, 40)])
+@pytest.mark.parametrize("p,leaf", [(8, 32), (12, 64), (16, 40), (18, 64)])
 def test_tensor_core_m2l_matches_cuda_core_m2l_and_oracle(p, leaf):
-    """The tcgen05 M2L (3xTF32 split) against the register-tiled FP32 M2L and the
-    FP64 FMM reference on the same tree; p = 16 (K = 153) runs the two-stage pipeline."""
+    """The tcgen05 M2L (fp16 hi/lo split, power-of-two scaled rows) against the register-tiled FP32
+    M2L and the FP64 FMM reference on the same tree.  p = 16 (K = 153) and p = 18 (K = 190) use
+    five and six accumulator column groups; at p = 18 the row scale fills the last two padding
+    halfs of the packed row (K = 190 of KP = 192)."""
     import torch
     imq = _imq()
     pts = W.clustered_points(2000, 6, 4000, 0.04, 5)
     c = 0.005
     v = W.random_vector(pts.shape[0], 13, nrhs=2)
     tc = imq.Plan(cuda(pts), c, p, leaf, domain=(0.0, 0.0, 1.0), m2l_kernel="tensor")
-    cc = imq.Plan(cuda(pts), c, p, leaf, domain=(0.0, 0.0, 1.0), m2l_kernel="cuda_cores")
+    # the register-tiled CUDA-core M2L stages the whole operator in shared memory: up to p = 16
+    cc = imq.Plan(cuda(pts), c, p, leaf, domain=(0.0, 0.0, 1.0), m2l_kernel="cuda_cores") if p <= 16 else None
     assert tc.info()["m2l_pairs"] > 1000
     bt = host(tc.matvec(cuda(v, torch.float32)))
-    bc = host(cc.matvec(cuda(v, torch.float32)))
+    bc = host(cc.matvec(cuda(v, torch.float32))) if cc else None
     for r in range(2):
         ofmm = fmm.fmm_matvec(pts, c, v[r], p, leaf, (0.0, 0.0, 1.0))
-        assert rel2(bt[r], bc[r]) < 5e-7
+        if cc:
+            assert rel2(bt[r], bc[r]) < 5e-7
         assert rel2(bt[r], ofmm) < 1e-6
     tc.close()
-    cc.close()
+    if cc:
+        cc.close()
 
 
 def test_tensor_core_m2l_batched_matches_cuda_cores():
