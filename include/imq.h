@@ -470,7 +470,8 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  *   out     : HOST result; out->tried lists every configuration measured.
  *
  *   Sample: 2048 rows (single problem) or 32 rows per problem, evenly spaced
- *   in the caller's order; the test vectors are SplitMix64 values in [-1, 1);
+ *   in the caller's order; the test vectors are SplitMix64 values in [-1, 1)
+ *   (imq_autotune_v: the caller's own);
  *   exact rows are FP64 direct sums.  The time of a configuration is the best
  *   of 3 products after one warm-up (CUDA events on `stream`).  Builds and
  *   frees one plan per configuration; synchronises `stream`.
@@ -503,6 +504,18 @@ imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob,
                         double target, const int32_t *p_cand, int n_p, const int32_t *leaf_cand,
                         int n_leaf, int nrhs, const imq_options *opt, void *stream,
                         imq_tune_result *out);
+
+/* imq_autotune_v -- imq_autotune with the caller's test vectors instead of
+ * SplitMix64 values: v is float[nrhs][N] in the caller's point order, host or
+ * device.  Data whose far-field sums cancel (oscillating right-hand sides, flat
+ * shapes) have a larger relative error than random vectors at the same p and
+ * translations; tuning on representative vectors makes `met` hold for them.
+ * Errors: as imq_autotune; IMQ_INVALID_ARG for v == NULL.  (Section 2.3 as for
+ * imq_autotune.) */
+imq_status imq_autotune_v(const double *points, const int64_t *offsets, int nprob, const double *cvals,
+                          double target, const int32_t *p_cand, int n_p, const int32_t *leaf_cand,
+                          int n_leaf, int nrhs, const float *v, const imq_options *opt, void *stream,
+                          imq_tune_result *out);
 
 /* ------------------------------------------------------------------------- *
  * imq_sync_check -- synchronise `stream` and report a failed bounded wait.

@@ -92,6 +92,7 @@ SIGNATURES = {
     "imq_interp_loss_grad": (INT, [P, P, P, P, P, INT, P, P, P, P, P, P]),
     "imq_dense_matvec_noalloc": (INT, [P, I64, D, P, P, P]),
     "imq_autotune": (INT, [P, P, INT, P, D, P, INT, P, INT, INT, P, P, P]),
+    "imq_autotune_v": (INT, [P, P, INT, P, D, P, INT, P, INT, INT, P, P, P, P]),
     "imq_sync_check": (INT, [P]),
     "imq_selftest_wait_timeout": (INT, [P]),
     "imq_plan_get_info": (INT, [P, P]),

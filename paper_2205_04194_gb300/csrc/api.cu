@@ -501,10 +501,10 @@ imq_status imq_matvec_timed(imq_plan_t plan, const void *v, void *out, int nrhs,
     });
 }
 
-imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
-                        const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
-                        const imq_options *opt, void *stream, imq_tune_result *out) {
-    return guard([&] {
+static void autotune_entry(const double *points, const int64_t *offsets, int nprob, const double *cvals,
+                           double target, const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf,
+                           int nrhs, const float *v, const imq_options *opt, void *stream, imq_tune_result *out) {
+    {
         if (!points || !offsets || !cvals || !p_cand || !leaf_cand || !out)
             fail(IMQ_INVALID_ARG, "imq_autotune: NULL pointer");
         if (nprob < 1) fail(IMQ_INVALID_ARG, "imq_autotune: nprob must be >= 1");
@@ -523,8 +523,27 @@ imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob,
         }
         if (offsets[nprob] > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_autotune: too many points");
         check_device();
-        autotune(points, offsets, nprob, cvals, target, p_cand, n_p, leaf_cand, n_leaf, nrhs, opt,
+        autotune(points, offsets, nprob, cvals, target, p_cand, n_p, leaf_cand, n_leaf, nrhs, v, opt,
                  static_cast<cudaStream_t>(stream), out);
+    }
+}
+
+imq_status imq_autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
+                        const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+                        const imq_options *opt, void *stream, imq_tune_result *out) {
+    return guard([&] {
+        autotune_entry(points, offsets, nprob, cvals, target, p_cand, n_p, leaf_cand, n_leaf, nrhs, nullptr, opt,
+                       stream, out);
+    });
+}
+
+imq_status imq_autotune_v(const double *points, const int64_t *offsets, int nprob, const double *cvals,
+                          double target, const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf,
+                          int nrhs, const float *v, const imq_options *opt, void *stream, imq_tune_result *out) {
+    return guard([&] {
+        if (!v) fail(IMQ_INVALID_ARG, "imq_autotune_v: NULL test vectors");
+        autotune_entry(points, offsets, nprob, cvals, target, p_cand, n_p, leaf_cand, n_leaf, nrhs, v, opt, stream,
+                       out);
     });
 }
 

@@ -97,7 +97,7 @@ struct PlanHolder {
 }  // namespace
 
 void autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
-              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs, const float *v,
               const imq_options *opt, cudaStream_t s, imq_tune_result *out) {
     const int64_t N = offsets ? offsets[nprob] : 0;
     // ---- sampled rows: evenly spaced within each problem, in the caller's order
@@ -125,8 +125,12 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
     IMQ_CUDA(cudaMemcpyAsync(d_lo.ptr, lo.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
     IMQ_CUDA(cudaMemcpyAsync(d_hi.ptr, hi.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
     IMQ_CUDA(cudaMemcpyAsync(d_c.ptr, cs.data(), 8 * (size_t)S, cudaMemcpyHostToDevice, s));
-    k_fill_pm1<<<blocks_for((int64_t)nrhs * N, 256), 256, 0, s>>>(d_v.as<float>(), (int64_t)nrhs * N);
-    IMQ_LAUNCH_CHECK();
+    if (v) {   // the caller's vectors (host or device)
+        IMQ_CUDA(cudaMemcpyAsync(d_v.ptr, v, sizeof(float) * (size_t)nrhs * N, cudaMemcpyDefault, s));
+    } else {
+        k_fill_pm1<<<blocks_for((int64_t)nrhs * N, 256), 256, 0, s>>>(d_v.as<float>(), (int64_t)nrhs * N);
+        IMQ_LAUNCH_CHECK();
+    }
     k_exact_rows<<<S, kRowThreads, 0, s>>>(d_pts.as<double2>(), N, d_v.as<float>(), nrhs, d_row.as<int64_t>(),
                                            d_lo.as<int64_t>(), d_hi.as<int64_t>(), d_c.as<double>(), S,
                                            d_exact.as<double>());

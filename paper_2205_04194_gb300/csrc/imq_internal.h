@@ -417,9 +417,10 @@ imq_status guarded_call(F &&f) {   // run f, translate exceptions into a status 
     }
 }
 
-// Measured choice of p and leaf size (autotune.cu); arguments already checked.
+// Measured choice of p and leaf size (autotune.cu); arguments already checked.  v: the caller's
+// test vectors (float[nrhs][N], host or device) or nullptr for SplitMix64 values.
 void autotune(const double *points, const int64_t *offsets, int nprob, const double *cvals, double target,
-              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs,
+              const int32_t *p_cand, int n_p, const int32_t *leaf_cand, int n_leaf, int nrhs, const float *v,
               const imq_options *opt, cudaStream_t s, imq_tune_result *out);
 
 }  // namespace imq

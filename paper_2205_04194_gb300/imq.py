@@ -386,13 +386,15 @@ def dense_matvec_noalloc(points, c: float, v, out, stream=None):
 
 
 def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
-             leaf_candidates=(32, 64, 128), nrhs: int = 1, domain=None, m2l_kernel: str = "auto", stream=None):
+             leaf_candidates=(32, 64, 128), nrhs: int = 1, domain=None, m2l_kernel: str = "auto", stream=None,
+             v=None):
     """imq_autotune: the measured choice of (p, leaf) for one point set, or for a batch.
 
     points: [N, 2] float64 (host or CUDA) with a scalar c, or a list of [N_b, 2]
-    arrays with a list of c_b (batched plans).  Returns a dict with the choice
-    ("p", "leaf", "rel_err", "matvec_ms", "met") and every measured
-    configuration under "tried".
+    arrays with a list of c_b (batched plans).  v: optional test vectors
+    ([nrhs, N] float32, the caller's point order; imq_autotune_v), else
+    SplitMix64 values.  Returns a dict with the choice ("p", "leaf", "rel_err",
+    "matvec_ms", "met") and every measured configuration under "tried".
     """
     if isinstance(points, (list, tuple)):
         sizes = [int(np.shape(x)[0]) for x in points]
@@ -412,9 +414,16 @@ def autotune(points, c, target: float = 1e-6, p_candidates=(8, 10, 12, 14, 16),
     pp, kp = _buf(pts, torch.float64)
     opt = _plan_options(domain, False, m2l_kernel)
     res = TuneResult()
-    call("imq_autotune", pp, ctypes.c_void_p(offs.ctypes.data), len(sizes), ctypes.c_void_p(cs.ctypes.data),
-         float(target), ctypes.c_void_p(pc.ctypes.data), len(pc), ctypes.c_void_p(lc.ctypes.data), len(lc),
-         int(nrhs), ctypes.byref(opt), _stream(stream), ctypes.byref(res))
+    args = [pp, ctypes.c_void_p(offs.ctypes.data), len(sizes), ctypes.c_void_p(cs.ctypes.data),
+            float(target), ctypes.c_void_p(pc.ctypes.data), len(pc), ctypes.c_void_p(lc.ctypes.data), len(lc),
+            int(nrhs)]
+    if v is None:
+        call("imq_autotune", *args, ctypes.byref(opt), _stream(stream), ctypes.byref(res))
+    else:
+        if int(np.prod(np.shape(v))) != int(nrhs) * int(offs[-1]):
+            raise ValueError("v must hold nrhs x N values")
+        vp, kv = _buf(v, torch.float32)
+        call("imq_autotune_v", *args, vp, ctypes.byref(opt), _stream(stream), ctypes.byref(res))
     names = {v: k for k, v in TRANSLATIONS.items()}
 
     def entry(t):

@@ -115,3 +115,33 @@ def test_batched_choice_meets_the_target_on_every_problem():
     assert worst == pytest.approx(res["rel_err"], rel=1e-3 if res["m2l_split"] <= 1 else 2e-2)
     assert worst <= 1e-6
     bp.close()
+
+
+def test_autotune_on_the_callers_vectors_reports_their_error():
+    """imq_autotune_v: the batched workload's own right-hand sides (Franke data and trig sums) as the
+    test vectors; the reported error of the choice is recomputed with the oracle on the same rows and
+    vectors, and it meets the target."""
+    import torch
+    imq = _imq()
+    probs = W.batched_256(n_problems=3, n_lo=4000, n_hi=8000)
+    pts = [x for x, _, _ in probs]
+    cs = [c for _, c, _ in probs]
+    f = np.concatenate([r for _, _, r in probs], axis=1).astype(np.float32)   # [4, N]
+    res = imq.autotune([cuda(x) for x in pts], cs, 1e-6, p_candidates=(10, 12, 14), leaf_candidates=(64,),
+                       nrhs=4, domain=(0.0, 0.0, 1.0), v=cuda(f))
+    assert res["met"], res
+    bp = imq.BatchedPlan([cuda(x) for x in pts], cs, res["p"], res["leaf"], domain=(0.0, 0.0, 1.0),
+                         **imq.tiles_of(res))
+    b = host(bp.matvec(cuda(f)))
+    offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in pts])])
+    worst = 0.0
+    for q, (x, c) in enumerate(zip(pts, cs)):
+        rows = _rows(x.shape[0], 32)
+        for r in range(4):
+            exact = dense.matvec_rows(x, c, f[r, offs[q]:offs[q + 1]].astype(np.float64), rows)
+            got = b[r, offs[q]:offs[q + 1]][rows]
+            worst = max(worst, np.linalg.norm(got - exact) / np.linalg.norm(exact))
+    # m2l_split > 1 adds FP32 partial sums to L in no fixed order: rounding-level differences
+    assert worst == pytest.approx(res["rel_err"], rel=1e-3 if res["m2l_split"] <= 1 else 2e-2)
+    assert worst <= 1e-6
+    bp.close()
