@@ -235,10 +235,9 @@ def run_batched(args, imq, dev):
     # measures its error on its own random vectors, while the workload's trig-sum right-hand sides
     # cancel in the far field, so FP64 translations can be what meets 1e-6 on the actual data
     variants = [("tuned", tiles)]
-    if tiles["translations"] != "fp32":
-        variants.append(("fp32_translations", dict(tiles, translations="fp32")))
-    else:
-        variants.append(("fp64_translations", dict(tiles, translations="fp64")))
+    for tr in ("fp32", "mixed", "fp64"):
+        if tiles["translations"] != tr:
+            variants.append((tr + "_translations", dict(tiles, translations=tr)))
     for name, kw in variants:
         torch.cuda.synchronize()
         t0 = time.perf_counter()

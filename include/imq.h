@@ -122,8 +122,11 @@ typedef enum imq_algorithm { IMQ_ALG_FMM = 0, IMQ_ALG_TREECODE = 1 } imq_algorit
  *          cancel (oscillating vectors, flat shapes), the FP32 rounding of the
  *          translated coefficients sets the error floor of the product
  *          (relative 2-norm error ~1e-6 at c ~ 0.15-0.2 on trig-sum vectors);
- *          FP64 translations remove that term at the cost of FP64 M2L. */
-typedef enum imq_translations { IMQ_TRANS_FP32 = 0, IMQ_TRANS_FP64 = 1 } imq_translations;
+ *          FP64 translations remove that term at the cost of FP64 M2L.
+ *   MIXED: M2M and L2L in FP64 (latency-bound levels, cheap on the FP64
+ *          units), M2L on the tensor cores from the narrowed multipoles (FP32
+ *          in and out): between the two in cost and error. */
+typedef enum imq_translations { IMQ_TRANS_FP32 = 0, IMQ_TRANS_FP64 = 1, IMQ_TRANS_MIXED = 2 } imq_translations;
 
 /* M2L kernel of the FP32 product.  AUTO takes the tensor cores when the
  * expansion fits them (K, K_out <= 256 reals), else the CUDA cores.
@@ -446,7 +449,8 @@ imq_status imq_dense_matvec_noalloc(const double *points, int64_t N, double c, c
  *        fast product meets `target` (relative 2-norm error on sampled rows,
  *        worst over problems and right-hand sides), then the fastest of those;
  *     2. if no candidate meets the target with FP32 translations, step 1 again
- *        with FP64 translations (IMQ_TRANS_FP64), whose error floor is lower;
+ *        with IMQ_TRANS_MIXED and then with IMQ_TRANS_FP64, whose error floors
+ *        are lower;
  *     3. on the chosen (p, leaf, translations), the P2P tile shape (p2p_warps x
  *        p2p_chunk in {2, 4, 8} x {8, 16, 32}), then the tensor-core M2L
  *        pipeline depth (m2l_stages 4..6, as far as they fit) and the number

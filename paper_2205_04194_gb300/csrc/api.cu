@@ -153,7 +153,7 @@ Allocator plan_allocator(const imq_options *opt) {
 
 void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *opt, double &x0, double &y0,
                      double &side, bool &dups, int *m2l_kernel = nullptr, int *algorithm = nullptr,
-                     int *tc_depth = nullptr, bool *trans64 = nullptr) {
+                     int *tc_depth = nullptr, int *trans_mode = nullptr) {
     if (N < 1 || N > 0x7FFFFFFF) fail(IMQ_INVALID_ARG, "imq_plan: N must be in [1, 2^31-1]");
     if (!std::isfinite(c) || c <= 0) fail(IMQ_INVALID_ARG, "imq_plan: c must be finite and > 0");
     if (p < 1 || p > IMQ_MAX_P) fail(IMQ_UNSUPPORTED, "imq_plan: p must be in [1, IMQ_MAX_P]");
@@ -184,11 +184,12 @@ void parse_plan_args(int64_t N, double c, int p, int leaf, const imq_options *op
         if (algorithm) *algorithm = opt->algorithm;
         if (tc_depth) *tc_depth = opt->algorithm == IMQ_ALG_TREECODE ? opt->levels + 1 : 0;
         if (opt->struct_size >= (int)(offsetof(imq_options, translations) + sizeof(int32_t))) {
-            if (opt->translations != IMQ_TRANS_FP32 && opt->translations != IMQ_TRANS_FP64)
+            if (opt->translations != IMQ_TRANS_FP32 && opt->translations != IMQ_TRANS_FP64 &&
+                opt->translations != IMQ_TRANS_MIXED)
                 fail(IMQ_INVALID_ARG, "imq_plan: unknown translations precision");
-            if (opt->translations == IMQ_TRANS_FP64 && (p > 16 || opt->algorithm != IMQ_ALG_FMM))
-                fail(IMQ_UNSUPPORTED, "imq_plan: FP64 translations need the fast multipole form and p <= 16");
-            if (trans64) *trans64 = opt->translations == IMQ_TRANS_FP64;
+            if (opt->translations != IMQ_TRANS_FP32 && (p > 16 || opt->algorithm != IMQ_ALG_FMM))
+                fail(IMQ_UNSUPPORTED, "imq_plan: FP64 or mixed translations need the fast multipole form and p <= 16");
+            if (trans_mode) *trans_mode = opt->translations;
         }
         if (opt->struct_size >= (int)(offsetof(imq_options, m2l_split) + sizeof(int32_t))) {
             if (opt->p2p_warps != 0 && opt->p2p_warps != 2 && opt->p2p_warps != 4 && opt->p2p_warps != 8)
@@ -217,8 +218,8 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
     double x0, y0, side;
     bool dups;
     int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM, depth = 0;
-    bool t64 = false;
-    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth, &t64);
+    int tmode = IMQ_TRANS_FP32;
+    parse_plan_args(N, c, p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, &depth, &tmode);
     const Allocator al = plan_allocator(opt);
     check_device();
     auto *h = new imq_plan_s;
@@ -238,12 +239,13 @@ imq_plan_s *plan_create(const double *d_points, int64_t N, int64_t n_nodes, doub
         P.m2l_kernel = m2lk;
         P.algorithm = alg;
         P.tc_depth = depth;
-        P.trans64 = t64;
+        P.trans64 = tmode == IMQ_TRANS_FP64;
+        P.trans_mixed = tmode == IMQ_TRANS_MIXED;
         plan_tiles(P, opt);
         P.layout.build(p, 0);
         build_tree(P, d_points, s, dups);
         ensure_ops(P, false, s);
-        if (t64) ensure_ops(P, true, s);
+        if (tmode != IMQ_TRANS_FP32) ensure_ops(P, true, s);
         IMQ_CUDA(cudaStreamSynchronize(s));
     } catch (...) {
         delete h;
@@ -313,8 +315,8 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
         double x0, y0, side;
         bool dups;
         int m2lk = IMQ_M2L_AUTO, alg = IMQ_ALG_FMM;
-        bool t64 = false;
-        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, nullptr, &t64);
+        int tmode = IMQ_TRANS_FP32;
+        parse_plan_args(N, cs[0], p, leaf, opt, x0, y0, side, dups, &m2lk, &alg, nullptr, &tmode);
         (void)plan_allocator(opt);
         if (alg != IMQ_ALG_FMM) fail(IMQ_UNSUPPORTED, "imq_plan_batched: the treecode is built for single plans only");
         check_device();
@@ -350,12 +352,13 @@ imq_status imq_plan_batched(const double *points, const int64_t *offsets, int np
             P.y0 = y0;
             P.side = side;
             P.m2l_kernel = m2lk;
-            P.trans64 = t64;
+            P.trans64 = tmode == IMQ_TRANS_FP64;
+            P.trans_mixed = tmode == IMQ_TRANS_MIXED;
             plan_tiles(P, opt);
             P.layout.build(p, 0);
             build_batched_plan(P, static_cast<const double *>(pts.ptr), offs, cs, dups, s);
             ensure_ops(P, false, s);
-            if (t64) ensure_ops(P, true, s);
+            if (tmode != IMQ_TRANS_FP32) ensure_ops(P, true, s);
             IMQ_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
             delete hp;

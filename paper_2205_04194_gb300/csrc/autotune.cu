@@ -212,7 +212,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
         bool any = false;
         for (int li = 0; li < n_leaf; ++li)
             for (int p : ps) {
-                if (trans == IMQ_TRANS_FP64 && p > 16) continue;
+                if (trans != IMQ_TRANS_FP32 && p > 16) continue;
                 const int k = measure(p, leaf_cand[li], trans, 0, 0, 0, 0);
                 if (k < 0) return any;
                 if (out->tried[k].rel_err <= target) {
@@ -223,6 +223,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
         return any;
     };
     bool met = search(IMQ_TRANS_FP32);
+    if (!met && ps.front() <= 16) met = search(IMQ_TRANS_MIXED);
     if (!met && ps.front() <= 16) met = search(IMQ_TRANS_FP64);
     // the fastest configuration that meets the target, else the most accurate one
     auto pick = [&](int from) {
@@ -252,7 +253,7 @@ void autotune(const double *points, const int64_t *offsets, int nprob, const dou
             if (better(k, cur)) cur = k;
         }
     const int K = (chosen.p + 1) * (chosen.p + 2) / 2;   // reals of the parity-reduced expansion
-    const bool tensor = !chosen.translations && (!opt || opt->m2l_kernel != IMQ_M2L_CUDA_CORES) &&
+    const bool tensor = chosen.translations != IMQ_TRANS_FP64 && (!opt || opt->m2l_kernel != IMQ_M2L_CUDA_CORES) &&
                         m2l_umma_supported(K, K);
     if (tensor) {
         const int smax = m2l_umma_max_stages(K, K);

@@ -974,12 +974,14 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     // (both fixed-order / shared-memory kernels), so no packing pass sits on the chain
     // FP64 translations: the multipoles are widened after P2M, translated (M2M, M2L, L2L) in FP64
     // and narrowed for M2P and L2P; the FP32 M2L path and its packed rows are not used
-    const bool t64 = P.trans64;
-    if (t64 && !P.ops64.ready) fail(IMQ_CUDA_ERROR, "FP64 translation operators missing");
-    double *Md = t64 ? P.ops64.M.as<double>() : nullptr, *Ld = t64 ? P.ops64.L.as<double>() : nullptr;
+    const bool t64 = P.trans64, tmx = P.trans_mixed;   // FP64 M2M / M2L / L2L; FP64 M2M / L2L only
+    if ((t64 || tmx) && !P.ops64.ready) fail(IMQ_CUDA_ERROR, "FP64 translation operators missing");
+    double *Md = (t64 || tmx) ? P.ops64.M.as<double>() : nullptr;
+    double *Ld = (t64 || tmx) ? P.ops64.L.as<double>() : nullptr;
     const int64_t nK = (int64_t)nb * K;
     const unsigned gw = (unsigned)std::min<int64_t>(blocks_for(nK, 256), 4 * 152);
-    const bool fuse_pack = !t64 && O.umma && P.n_m2l_tiles > 0 && p2m_fixed_p_supported(P.p) && K <= kTransSmemMaxK;
+    const bool fuse_pack =
+        !t64 && !tmx && O.umma && P.n_m2l_tiles > 0 && p2m_fixed_p_supported(P.p) && K <= kTransSmemMaxK;
     const int kp_pack = m2l_umma_kp(K);
     const bool conc = tm == nullptr;
     if (conc) P.aux.ensure();
@@ -1019,7 +1021,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         ++launches;
         t1();
         t0(kPhM2M);
-        if (t64) {
+        if (t64 || tmx) {
             k_widen<<<gw, 256, 0, s>>>(M, Md, nK, 0);
             m2m_levels<double>(P, Md, P.ops64.m2m.as<double>(), s, &launches);
             k_narrow<<<gw, 256, 0, s>>>(Md, M, nK);
@@ -1061,7 +1063,12 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
         }
         t1();
         t0(kPhL2L);
-        if (t64) {
+        if (tmx) {   // the tensor-core M2L left L (P2L + M2L terms) in FP32
+            k_widen<<<gw, 256, 0, s>>>(L, Ld, nK, 0);
+            IMQ_LAUNCH_CHECK();
+            ++launches;
+        }
+        if (t64 || tmx) {
             l2l_launch<double>(P, Ld, P.ops64.l2l.as<double>(), K, s, &launches);
             k_narrow<<<gw, 256, 0, s>>>(Ld, L, nK);
             IMQ_LAUNCH_CHECK();

@@ -222,6 +222,7 @@ struct Plan {
     int m2l_kernel = 0;  // imq_m2l_kernel
     int algorithm = 0;   // imq_algorithm
     bool trans64 = false; // FP32 product with M2M / M2L / L2L in FP64 (imq_options.translations)
+    bool trans_mixed = false;   // FP32 product with M2M / L2L in FP64, M2L on the tensor cores
     // tile shapes of the FP32 product (imq_options; 0 = default): P2P warps per CTA and
     // target chunk, tensor-core M2L pipeline stages
     int p2p_warps = 0, p2p_chunk = 0, m2l_stages = 0, m2l_split = 0;

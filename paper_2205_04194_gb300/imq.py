@@ -75,7 +75,7 @@ def _torch_allocator():
     return _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
 
 
-TRANSLATIONS = {"fp32": 0, "fp64": 1}
+TRANSLATIONS = {"fp32": 0, "fp64": 1, "mixed": 2}
 
 
 def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0,

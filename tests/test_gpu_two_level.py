@@ -70,7 +70,9 @@ def test_two_level_gmres_on_a_batched_plan_meets_1e6_per_problem():
     """Three problems in one batched plan: the clustered analogue's generator at two scales (c/h ~ 40
     in the clusters) and a uniform set at c = 4 h.  Per-problem GMRES with the two-level
     preconditioner, whose coarse boxes are each problem's own (a block-diagonal Galerkin matrix),
-    meets 1e-6 on every problem's oracle residual."""
+    meets 1e-6 on every problem's oracle residual.  The second problem's FP32-operator floor sits
+    near 1e-6 (its single-plan solve ends at 9.4e-7), so the solve refines: each GMRES pass lowers
+    the dense FP64 residual by 1e-3 at most, and the next pass starts from that residual."""
     need_gpu()
     from paper_2205_04194_gb300 import imq
     p1 = W.clustered_points(int(round(87_500 * 0.005)), 8, int(round(300_000 * 0.005)), 0.03, 3)
@@ -81,7 +83,8 @@ def test_two_level_gmres_on_a_batched_plan_meets_1e6_per_problem():
     fs = [W.franke(x) for x in pts]
     bp = imq.BatchedPlan([cuda(x) for x in pts], cs, 12, 64, domain=(0.0, 0.0, 1.0))
     coef, info = bp.solve(cuda(np.concatenate(fs)), rtol=1e-6, maxit=2000, precond="schwarz2", coarse_points=256,
-                          schwarz_shift=1e-4, residual="dense", krylov="gmres", gmres_m=40)
+                          schwarz_shift=1e-4, residual="dense", krylov="gmres", gmres_m=40, refine_steps=20,
+                          inner_rtol=1e-3)
     assert info["status"] == "IMQ_OK", info
     coef = host(coef)
     offs = np.concatenate([[0], np.cumsum([x.shape[0] for x in pts])])
