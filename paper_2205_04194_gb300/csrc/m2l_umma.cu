@@ -17,15 +17,15 @@
 // Precision: each operand is scaled by a power of two into the fp16 range (a
 // row of M by its box's scale, a row of T_l by its output coefficient's scale,
 // shared by the 40 classes of the level) and split into an fp16 head and tail
-// (x = hi + lo, 11 significant bits each).  D accumulates all four products
-// lo*lo + hi*lo + lo*hi + hi*hi in FP32, smallest first, so the products carry
-// about 22 significant bits, as a 3xTF32 split does, with half the operand
-// bytes and twice the tensor rate.  The drain takes the box scale out of every
-// chunk and the coefficient scale out of the sum.
+// (x = hi + lo, 11 significant bits each).  D accumulates hi*lo + lo*hi and then
+// hi*hi in FP32 (small terms first), so the products carry about 22 significant
+// bits, as a 3xTF32 split does, with half the operand bytes and twice the tensor
+// rate.  The drain takes the box scale out of every chunk and the coefficient
+// scale out of the sum.
 //
 // Pipeline: the K dimension of each class is cut into 32-wide chunks (64-byte
 // rows, 64-byte swizzle); a chunk's A and T tiles form one shared-memory stage.
-// One thread issues the 8 MMAs of a chunk and commits them to the stage's
+// One thread issues the 6 MMAs of a chunk and commits them to the stage's
 // mbarrier, which releases the stage for reuse.  Every wait is bounded and
 // reports kErrWaitTimeout through the device error word.
 #include <algorithm>
@@ -152,7 +152,7 @@ __global__ void k_m2l_images(const float *__restrict__ ops, int64_t nblk, int K,
 //              lanes arrive on the stage's barrier through
 //              cp.async.mbarrier.arrive.noinc; its lane 0 also issues the bulk
 //              copy of the operator image;
-//   warp 12    lane 0 issues the 8 MMAs of each chunk into one of NA TMEM
+//   warp 12    lane 0 issues the 6 MMAs of each chunk into one of NA TMEM
 //              accumulators and commits them to the stage's "empty" barrier and
 //              the accumulator's "full" barrier.
 // Barriers: full[S] (33 arrivals + image bytes), empty[S] (MMA commit),
@@ -417,15 +417,14 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 const uint32_t sa = sbase + (uint32_t)st * stage_bytes;
                 const uint32_t bh = sa + 2 * kAStage, bl = bh + (uint32_t)Kn * 64u;
                 const uint32_t d = tmem + (uint32_t)(g % NA) * kAccCols;
-                // the small products first (lo*lo, hi*lo, lo*hi over both K halves), then hi*hi:
-                // the tensor core's FP32 sum then adds the large terms to a small partial sum
-                // instead of the small terms to a large one
+                // the small products first (hi*lo, lo*hi over both K halves), then hi*hi: the
+                // tensor core's FP32 sum then adds the large terms to a small partial sum instead
+                // of the small terms to a large one
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint64_t dah = umma_desc_sw64(sa + 32 * ks), dal = umma_desc_sw64(sa + kAStage + 32 * ks);
                     const uint64_t dbh = umma_desc_sw64(bh + 32 * ks), dbl = umma_desc_sw64(bl + 32 * ks);
-                    umma_f16(d, dal, dbl, idesc, ks > 0 ? 1u : 0u);
-                    umma_f16(d, dah, dbl, idesc, 1u);
+                    umma_f16(d, dah, dbl, idesc, ks > 0 ? 1u : 0u);
                     umma_f16(d, dal, dbh, idesc, 1u);
                 }
 #pragma unroll
