@@ -329,6 +329,12 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3, grp = w >> 2;
     const int p0 = blockIdx.x * kTS;
     const int ng = min(kTS, n - p0);
+    // programmatic dependent launch: the next level's kernel may start its prologue (barrier
+    // set-up, the operator's bulk copy, parent and child ids) on idle SMs while this level
+    // computes; it reads expansions only after its griddepcontrol.wait, which waits for this
+    // grid to finish.  Triggering here rather than after the reduction took the 1M-point
+    // product from 0.684 to 0.674 ms.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -373,10 +379,6 @@ __global__ void __launch_bounds__(32 * kTSWarps) k_trans_s(const int32_t *__rest
     }
     float acc[kTSG][RC];
     trans_rows_smem<RC>(sop + (size_t)q * K * K, mx, K, lane, acc);
-    // programmatic dependent launch: once every CTA is writing its results, the next
-    // level's kernel may start its prologue (barrier set-up, operator copy, parent and
-    // child ids); triggering this late keeps waiting CTAs from holding SMs for long
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (UP) {
         __shared__ int s_mx[kTS];   // largest |sum| of each parent (float bits, non-negative)
         if (threadIdx.x < kTS) s_mx[threadIdx.x] = 0;
