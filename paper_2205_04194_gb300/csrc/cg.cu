@@ -302,6 +302,12 @@ __global__ void k_scatter_f64(const double *__restrict__ v, const int32_t *__res
 // FP32 inverse L^{-T} L^{-1} of an ill-conditioned patch need not be).  L^{-1}
 // replaces L in shared memory column by column (last column first), with one
 // extra column of n values.
+// Packed lower-triangular storage of an n x n inverse factor X = L^{-1}: column j holds
+// rows j .. n-1 contiguously from inv_packed_col(j, n); a patch's block is padded to a
+// multiple of four floats, so every block starts on a 16-byte boundary (one bulk copy).
+__host__ __device__ __forceinline__ int inv_packed_col(int j, int n) { return j * (2 * n - j + 1) / 2; }
+__host__ __device__ __forceinline__ int inv_packed_size(int n) { return (n * (n + 1) / 2 + 3) & ~3; }
+
 template <class T, bool INV>
 __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, const int32_t *__restrict__ ppts,
                                  const int64_t *__restrict__ foff, const double2 *__restrict__ pos,
@@ -382,18 +388,18 @@ __global__ void k_schwarz_factor(int npatch, const int32_t *__restrict__ poff, c
             if (s_bad) continue;
             for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
                 const int t = e / n, i = e - t * n;
-                F[e] = i >= t ? A[e] : (T)0;
+                if (i >= t) F[inv_packed_col(t, n) + (i - t)] = A[e];
             }
+            for (int e = n * (n + 1) / 2 + threadIdx.x; e < inv_packed_size(n); e += blockDim.x) F[e] = (T)0;
             __syncthreads();
             if (!s_bad) return;
         }
     }
     // every attempt overflowed: the patch acts as the diagonal c I (as a point in no patch)
     if constexpr (INV) {
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int j = e / n, i = e - j * n;
-            F[e] = i == j ? (T)sqrt(cb) : (T)0;
-        }
+        for (int e = threadIdx.x; e < inv_packed_size(n); e += blockDim.x) F[e] = (T)0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) F[inv_packed_col(j, n)] = (T)sqrt(cb);
     }
 }
 
@@ -452,58 +458,63 @@ __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, co
     }
 }
 
-// One warp per patch: y = L^{-T} (L^{-1} r_patch) with the FP32 inverse factor
-// (column-major n x n lower, n <= 32 * kInvRowsPerLane).  Pass 1, w = L^{-1} r:
-// r_k is broadcast from the lane holding it and lane l accumulates rows l, l + 32,
-// ... over the columns k (coalesced column reads).  Pass 2, y_k = column k . w:
-// one warp reduction per column.
+// One CTA per patch: y = L^{-T} (L^{-1} r_patch) with the FP32 inverse factor X = L^{-1}
+// (packed lower, n <= 32 * kInvRowsPerLane).  The patch's X arrives in shared memory by one
+// bulk copy, so each factor byte crosses HBM once per apply; the two triangular products
+// then run from shared memory.  Pass 1, w_i = sum_{j <= i} X_ij r_j: a thread per row,
+// consecutive threads on consecutive rows of a column.  Pass 2, y_k = sum_{i >= k} X_ik w_i:
+// a thread per column, reading it contiguously.
 constexpr int kInvRowsPerLane = 7;   // patches up to 224 points
-__global__ void __launch_bounds__(128) k_schwarz_inv_apply(int npatch, const int32_t *__restrict__ poff,
-                                                           const int32_t *__restrict__ ppts,
-                                                           const int64_t *__restrict__ foff,
-                                                           const float *__restrict__ inv, const double *__restrict__ r,
-                                                           double *__restrict__ ypatch, const CGScalars *S) {
+constexpr int kInvThreads = 128;
+
+size_t inv_apply_smem(int maxn) { return sizeof(float) * ((size_t)inv_packed_size(maxn) + 2 * (size_t)maxn); }
+
+__global__ void __launch_bounds__(kInvThreads) k_schwarz_inv_apply(int npatch, const int32_t *__restrict__ poff,
+                                                                  const int32_t *__restrict__ ppts,
+                                                                  const int64_t *__restrict__ foff,
+                                                                  const float *__restrict__ inv,
+                                                                  const double *__restrict__ r,
+                                                                  double *__restrict__ ypatch, const CGScalars *S,
+                                                                  int *err) {
+    extern __shared__ __align__(16) unsigned char smraw_i[];
+    __shared__ __align__(8) uint64_t bar;
     if (S && S->done) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= npatch) return;
-    const int o = poff[warp], n = poff[warp + 1] - o;
-    const float *Li = inv + foff[warp];
-    float rv[kInvRowsPerLane], acc[kInvRowsPerLane];
-#pragma unroll
-    for (int t = 0; t < kInvRowsPerLane; ++t) {
-        const int i = lane + 32 * t;
-        rv[t] = i < n ? (float)r[ppts[o + i]] : 0.f;
-        acc[t] = 0.f;
+    const int b = blockIdx.x;
+    if (b >= npatch) return;
+    const int o = poff[b], n = poff[b + 1] - o, np = inv_packed_size(n);
+    float *X = reinterpret_cast<float *>(smraw_i);
+    float *rv = X + np, *wv = rv + n;
+    if (n == 0) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
     }
-#pragma unroll
-    for (int kt = 0; kt < kInvRowsPerLane; ++kt) {
-        if (32 * kt >= n) break;
-        const int kn = min(32, n - 32 * kt);
-        const float *col0 = Li + (size_t)(32 * kt) * n;
-#pragma unroll 4
-        for (int kl = 0; kl < kn; ++kl) {
-            const float rk = __shfl_sync(0xFFFFFFFFu, rv[kt], kl);
-            const float *col = col0 + (size_t)kl * n;
-#pragma unroll
-            for (int t = kt; t < kInvRowsPerLane; ++t) {   // rows i >= 32 kt (the rest is zero)
-                const int i = lane + 32 * t;
-                if (i < n) acc[t] = fmaf(__ldg(col + i), rk, acc[t]);
-            }
-        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)(sizeof(float) * np));
+        bulk_g2s(X, inv + foff[b], (uint32_t)(sizeof(float) * np), &bar);
     }
-    // acc = w = L^{-1} r; y_k = sum_{i >= k} L^{-1}[i][k] w_i
-    for (int k = 0; k < n; ++k) {
-        const float *col = Li + (size_t)k * n;
-        float part = 0.f;
-#pragma unroll
-        for (int t = 0; t < kInvRowsPerLane; ++t) {
-            const int i = lane + 32 * t;
-            if (i < n && i >= k) part = fmaf(__ldg(col + i), acc[t], part);
+    for (int i = threadIdx.x; i < n; i += kInvThreads) rv[i] = (float)r[ppts[o + i]];
+    // a CTA-uniform outcome of the bounded wait, so that every thread leaves together
+    if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
+        if (threadIdx.x == 0) set_error(err, kErrWaitTimeout);
+        return;   // the results of this apply are invalid; the host reads the error word
+    }
+    for (int i = threadIdx.x; i < n; i += kInvThreads) {
+        float acc = 0.f;
+        int cj = i;   // packed index of X_ij for j = 0
+        for (int j = 0; j <= i; ++j) {
+            acc = fmaf(X[cj], rv[j], acc);
+            cj += n - j - 1;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
-        if (lane == 0) ypatch[o + k] = (double)part;
+        wv[i] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += kInvThreads) {
+        const float *col = X + inv_packed_col(k, n);
+        float acc = 0.f;
+        for (int i = k; i < n; ++i) acc = fmaf(col[i - k], wv[i], acc);
+        ypatch[o + k] = (double)acc;
     }
 }
 
@@ -572,6 +583,17 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     }
     Z.npatch = P.nleaf;
     Z.total_slots = (int64_t)ppts.size();
+    // FP32 patches of at most 32 * kInvRowsPerLane points are applied through their inverse
+    // factor, stored packed (lower triangle only)
+    Z.inverse = !fp64 && maxn <= 32 * kInvRowsPerLane;
+    if (Z.inverse) {
+        fsz = 0;
+        for (int b = 0; b < P.nleaf; ++b) {
+            foff[b] = fsz;
+            fsz += inv_packed_size(poff[b + 1] - poff[b]);
+        }
+    }
+    Z.maxn = maxn;
     // reverse map point -> slots, in increasing slot order (deterministic sums)
     std::vector<int32_t> ptcnt(P.N + 1, 0);
     for (auto j : ppts) ptcnt[j + 1]++;
@@ -592,8 +614,6 @@ void build_schwarz(Plan &P, int nmax, double shift, bool fp64, cudaStream_t s) {
     // cannot hold as positive definite otherwise meets clamped pivots whose Schur updates grow
     // without bound
     const double fshift = fp64 ? shift : std::max(shift, kF32PatchShift);
-    // FP32 patches of at most 32 * kInvRowsPerLane points are applied through their inverse factor
-    Z.inverse = !fp64 && maxn <= 32 * kInvRowsPerLane;
     const size_t smem = es * ((size_t)maxn * maxn + (Z.inverse ? (size_t)maxn : 0));
     if (fp64) {
         IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_factor<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -623,11 +643,14 @@ void schwarz_apply(const Plan &P, const Schwarz &Z, const double *r, double *z, 
                    cudaStream_t s) {
     const CGScalars *S = static_cast<const CGScalars *>(Sv);
     const unsigned g = blocks_for((int64_t)Z.npatch * 32, 128);
-    if (Z.inverse)
-        k_schwarz_inv_apply<<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
-                                              Z.fac_off.as<int64_t>(), Z.factor.as<float>(), r, Z.ypatch.as<double>(),
-                                              S);
-    else if (Z.fp64)
+    if (Z.inverse) {
+        const size_t smem = inv_apply_smem(Z.maxn);
+        IMQ_CUDA(cudaFuncSetAttribute(k_schwarz_inv_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (Z.npatch > 0)
+            k_schwarz_inv_apply<<<Z.npatch, kInvThreads, smem, s>>>(
+                Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(), Z.fac_off.as<int64_t>(),
+                Z.factor.as<float>(), r, Z.ypatch.as<double>(), S, device_error_word());
+    } else if (Z.fp64)
         k_schwarz_solve<double><<<g, 128, 0, s>>>(Z.npatch, Z.patch_off.as<int32_t>(), Z.patch_pts.as<int32_t>(),
                                                   Z.fac_off.as<int64_t>(), Z.factor.as<double>(), r,
                                                   Z.ypatch.as<double>(), S);

@@ -151,10 +151,12 @@ struct Schwarz {
     int npatch = 0;
     DevMem patch_off;    // int32[npatch+1] offsets into patch_pts
     DevMem patch_pts;    // int32[] sorted point indices of each patch
-    DevMem fac_off;      // int64[npatch] offset of each patch's n*n factor
-    DevMem factor;       // float[] or double[] column-major Cholesky factors (or explicit inverses)
+    DevMem fac_off;      // int64[npatch] offset of each patch's factor
+    DevMem factor;       // float[] or double[] column-major n x n Cholesky factors, or packed
+                         // lower inverse factors (inverse)
     bool fp64 = false;
-    bool inverse = false; // factor holds each patch's explicit inverse (FP32, n <= 160)
+    bool inverse = false; // factor holds each patch's packed inverse factor L^{-1} (FP32, n <= 224)
+    int maxn = 0;         // points of the largest patch
     DevMem pt_off;       // int32[N+1] reverse map: point -> patch slots
     DevMem pt_slot;      // int32[] patch slot (patch_off[b] + local index)
     DevMem ypatch;       // double[total slots] per-patch solutions
