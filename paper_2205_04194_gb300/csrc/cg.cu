@@ -463,9 +463,11 @@ __global__ void k_schwarz_solve(int npatch, const int32_t *__restrict__ poff, co
 // bulk copy, so each factor byte crosses HBM once per apply; the two triangular products
 // then run from shared memory.  Pass 1, w_i = sum_{j <= i} X_ij r_j: a thread per row,
 // consecutive threads on consecutive rows of a column.  Pass 2, y_k = sum_{i >= k} X_ik w_i:
-// a thread per column, reading it contiguously.
+// a thread per column, reading it contiguously.  256 threads (every row of a 224-point patch
+// has its own thread) and about 100 KB of shared memory: two CTAs per SM, one computing while
+// the other's copy lands.
 constexpr int kInvRowsPerLane = 7;   // patches up to 224 points
-constexpr int kInvThreads = 128;
+constexpr int kInvThreads = 256;
 
 size_t inv_apply_smem(int maxn) { return sizeof(float) * ((size_t)inv_packed_size(maxn) + 2 * (size_t)maxn); }
 
