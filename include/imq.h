@@ -525,8 +525,9 @@ imq_status imq_autotune_v(const double *points, const int64_t *offsets, int npro
  * imq_sync_check -- synchronise `stream` and report a failed bounded wait.
  *
  *   The kernels that wait on shared-memory barriers (the tensor-core M2L
- *   pipeline, the P2P source staging, the M2M/L2L operator copy, the dense
- *   product's source tiles) give up after a bounded number of polls or 0.5 s
+ *   pipeline, the P2P source staging, the M2M/L2L operator copy, the Schwarz
+ *   patches' factor copy, the dense product's source tiles) give up after a
+ *   bounded number of polls or 0.5 s
  *   instead of hanging, and record that in a per-device error word (the
  *   allocation-free dense product in the word of its own scratch array).
  *   Calls that synchronise anyway (host output buffers, imq_matvec_timed,
