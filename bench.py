@@ -49,7 +49,7 @@ TRAFFIC = {
     # the V pairs (x 1,121,136 / 267,324) to the 1M launch
     "m2l": {"bytes": 22.574848e6 * 1121136 / 267324, "sources": {
         "paper_2205_04194_gb300/csrc/m2l_umma.cu": "2382ca23c6659b5973089438a6f5dd5615f3786aaa39f452af1da025d4a7d0f4",
-        "paper_2205_04194_gb300/csrc/umma.cuh": "ec6da3b3c75070f001a40973b94766e68b1db5c9604bc71cdac4d874440d5422",
+        "paper_2205_04194_gb300/csrc/umma.cuh": "389ed8c09540f0a3e24b70570e9738f6acff25805ba38fc440f7a8f9f2b6336e",
         "paper_2205_04194_gb300/csrc/ptx.cuh": "9f11aae585d997f977cfb9515e1a6d3900bf168e91c1a75824dfdb29176bb76c"}},
 }
 

@@ -134,7 +134,7 @@ typedef enum imq_translations { IMQ_TRANS_FP32 = 0, IMQ_TRANS_FP64 = 1, IMQ_TRAN
 typedef enum imq_m2l_kernel {
     IMQ_M2L_AUTO = 0,
     IMQ_M2L_CUDA_CORES = 1,    /* register-tiled FP32 FMA                          */
-    IMQ_M2L_TENSOR = 2         /* tcgen05 kind::tf32, 3xTF32 split, TMEM accumulator */
+    IMQ_M2L_TENSOR = 2         /* tcgen05 kind::f16, fp16 hi/lo split, TMEM accumulator */
 } imq_m2l_kernel;
 
 /* ------------------------------------------------------------------------- *

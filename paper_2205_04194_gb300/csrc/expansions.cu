@@ -850,7 +850,7 @@ void ensure_parents(Plan &P, cudaStream_t s) {
     IMQ_CUDA(cudaStreamSynchronize(s));
 }
 
-// Xpk (upward, shared-memory kernel only): also write the tf32 hi / lo rows of the parents
+// Xpk (upward, shared-memory kernel only): also write the scaled fp16 hi / lo rows of the parents
 template <class T, bool UP>
 void trans_launch(Plan &P, T *X, const T *op, int K, int lev_lo, int lev_hi, bool downward, cudaStream_t s,
                   int *launches, float *Xpk = nullptr, int KP = 0) {
@@ -972,7 +972,7 @@ int fmm_apply_f32_fixed(Plan &P, const float *us, float *bs, int nrhs, cudaStrea
     // solvers capture single right-hand-side products only)
     if (P.near.bytes < sizeof(float) * (size_t)P.N * nrhs) P.near.alloc(sizeof(float) * (size_t)P.N * nrhs);
     if (nrhs > 2 && !P.rec4b.ptr) P.rec4b.alloc(sizeof(float4) * (size_t)P.N);
-    // the tensor-core M2L's tf32 hi / lo rows are written by P2M and M2M themselves
+    // the tensor-core M2L's scaled fp16 hi / lo rows are written by P2M and M2M themselves
     // (both fixed-order / shared-memory kernels), so no packing pass sits on the chain
     // FP64 translations: the multipoles are widened after P2M, translated (M2M, M2L, L2L) in FP64
     // and narrowed for M2P and L2P; the FP32 M2L path and its packed rows are not used

@@ -1,13 +1,9 @@
 // Inline-PTX helpers for the 5th-generation tensor cores of sm_103a:
-// tcgen05.mma with operands in shared memory and the accumulator in tensor
-// memory (TMEM), plus the 16-byte cp.async used to stage gathered operands.
-//
-// Operand layout used throughout: K-major, 128-byte swizzle.  A tile of R rows
-// x 32 tf32 values occupies R x 128 bytes; row r sits at byte r * 128 of its
-// 1024-byte atom of 8 rows, and its 16-byte chunk j (values 4j .. 4j+3) at
-// chunk position j ^ (r & 7).  Atoms follow one another along the rows
-// (stride 1024 bytes).  A K-step of 8 tf32 values advances the descriptor's
-// start address by 32 bytes inside the atom.
+// tcgen05.mma (kind::f16) with operands in shared memory and the accumulator in
+// tensor memory (TMEM), tcgen05.ld for the drain, the 16-byte cp.async that
+// gathers operand rows, and the power-of-two scaled fp16 hi / lo split of the
+// M2L operands.  Operand layout: K-major, 64-byte swizzle (sw64_offset,
+// umma_desc_sw64).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -16,18 +12,6 @@
 #include "ptx.cuh"
 
 namespace imq {
-
-// round an fp32 value to tf32 (10 explicit mantissa bits), nearest, ties away
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// byte offset of (row r, 16-byte chunk j) in a 128B-swizzled K-major tile
-__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t j) {
-    return r * 128u + ((j ^ (r & 7u)) << 4);
-}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst_smem), "l"(src) : "memory");
@@ -41,15 +25,10 @@ __device__ __forceinline__ void cp_async16_zero(uint32_t dst_smem, const void *s
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ void st_shared_zero16(uint32_t dst_smem) {
-    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst_smem), "r"(0u) : "memory");
-}
-
 // generic-proxy writes to shared memory -> visible to tcgen05.mma (async proxy)
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -68,31 +47,19 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart.  Fields: start address >> 4 (bits 0-13), leading byte
-// offset >> 4 (16-29, unused by swizzled K-major layouts: 1), stride byte
-// offset >> 4 (32-45), descriptor version 1 (46-47), base offset 0 (49-51),
-// swizzle mode 2 = 128B (61-63).
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
-    return d;
-}
-
 // 64-byte swizzle (the fp16 M2L): a row of 32 fp16 values is 64 bytes, an atom
 // is 8 rows (512 bytes), and the 16-byte chunk j (values 8j .. 8j+7) of row r
 // sits at chunk position j ^ ((r >> 1) & 3): the XOR of address bits 4-5 with
-// bits 7-8, as for the 128-byte swizzle one bit narrower.
+// bits 7-8.
 __host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t r, uint32_t j) {
     return r * 64u + ((j ^ ((r >> 1) & 3u)) << 4);
 }
-// Descriptor of a K-major, 64-byte-swizzled operand: 8-row atoms 512 bytes
-// apart (stride byte offset), swizzle mode 4 = 64B (bits 61-63); a K-step of
-// 16 fp16 values advances the start address by 32 bytes inside the atom.
+// Shared-memory matrix descriptor of a K-major, 64-byte-swizzled operand.
+// Fields: start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29,
+// unused by swizzled K-major layouts: 1), stride byte offset >> 4 (32-45: the
+// 8-row atoms 512 bytes apart), descriptor version 1 (46-47), base offset 0
+// (49-51), swizzle mode 4 = 64B (61-63).  A K-step of 16 fp16 values advances
+// the start address by 32 bytes inside the atom.
 __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr) {
     uint64_t d = 0;
     d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
@@ -140,55 +107,10 @@ __device__ __forceinline__ void f16_split(float x, __half &hi, __half &lo) {
     lo = __float2half_rn(x - __half2float(hi));
 }
 
-// Instruction descriptor, kind::tf32: D f32 (bits 4-5 = 1), A and B tf32
-// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
-// M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t umma_idesc_tf32(uint32_t M, uint32_t N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// D[tmem] (+)= A * B^T for one K-step; issued by a single thread.
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 // arrive on an mbarrier once every tcgen05.mma issued so far by this thread completes
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-// 32 lanes x 32 consecutive 32-bit columns: thread t of the warp gets lane
-// (warp's lane quarter + t), columns [col, col + 32).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    // the registers are tied to the wait so no use of them is scheduled before it
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Issue (without waiting) a load of 32 lanes x 16 consecutive 32-bit columns:

@@ -77,6 +77,13 @@ def _torch_allocator():
 
 TRANSLATIONS = {"fp32": 0, "fp64": 1, "mixed": 2}
 
+# imq_cg_options fields by name (the values of include/imq.h's enums)
+PRECONDS = {"none": 0, None: 0, "schwarz": 1, "schwarz2": 2}
+RESIDUALS = {"plan": 0, "dense": 1}
+OPERATORS = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}
+KRYLOVS = {"cg": 0, "gmres": 1}
+COARSE_GRAMS = {"auto": 0, "fp64": 1, "fp32": 2}
+
 
 def _plan_options(domain=None, check_duplicates=False, m2l_kernel="auto", algorithm="fmm", levels=0,
                   allocator=None, translations="fp32", p2p_warps=0, p2p_chunk=0, m2l_stages=0, m2l_split=0):
@@ -171,20 +178,20 @@ class Plan:
         _lib.load().imq_cg_default_options(ctypes.byref(o))
         o.rtol = float(kw["rtol"])
         o.maxit = int(kw["maxit"])
-        o.precond = {"none": 0, None: 0, "schwarz": 1, "schwarz2": 2}[kw["precond"]]
+        o.precond = PRECONDS[kw["precond"]]
         o.coarse_points = int(kw.get("coarse_points", 0))
-        o.coarse_gram = {"auto": 0, "fp64": 1, "fp32": 2}[kw.get("coarse_gram", "auto")]
+        o.coarse_gram = COARSE_GRAMS[kw.get("coarse_gram", "auto")]
         o.schwarz_nmax = int(kw["schwarz_nmax"])
         o.schwarz_shift = float(kw["schwarz_shift"])
         o.refine_steps = int(kw["refine_steps"])
         o.inner_rtol = float(kw["inner_rtol"])
-        o.residual = {"plan": 0, "dense": 1}[kw["residual"]]
+        o.residual = RESIDUALS[kw["residual"]]
         o.x0_given = 1 if x0 is not None else 0
         rp = kw.get("residual_plan")
         o.residual_plan = rp._h if rp is not None else None
-        o.inner_operator = {"fast_f32": 0, "fast_f64": 1, "dense_f64": 2}[kw["operator"]]
+        o.inner_operator = OPERATORS[kw["operator"]]
         o.schwarz_fp64 = 1 if kw["schwarz_fp64"] else 0
-        o.krylov = {"cg": 0, "gmres": 1}[kw.get("krylov", "cg")]
+        o.krylov = KRYLOVS[kw.get("krylov", "cg")]
         o.gmres_m = int(kw.get("gmres_m", 0))
         info = CgInfo()
         fp, kf = _buf(f, torch.float64)
