@@ -153,3 +153,33 @@ def test_allocator_needs_both_functions(lib):
     opt.alloc = keep                                  # free missing
     assert L.imq_plan(pts, 2, 1.0, 8, 16, ctypes.byref(opt), None, ctypes.byref(h)) == 1
     assert b"together" in L.imq_last_error()
+
+
+def test_binding_names_match_the_header_enums(tmp_path):
+    """The Python names of every option value (dtype, algorithm, translations, M2L kernel,
+    preconditioner, inner operator, residual, Krylov method) map to the values include/imq.h
+    gives those enum constants (a C program compiled with gcc prints them)."""
+    import subprocess
+    from paper_2205_04194_gb300 import imq
+    pairs = {"IMQ_F32": imq.F32, "IMQ_F64": imq.F64,
+             "IMQ_ALG_FMM": imq.ALGORITHMS["fmm"], "IMQ_ALG_TREECODE": imq.ALGORITHMS["treecode"],
+             "IMQ_TRANS_FP32": imq.TRANSLATIONS["fp32"], "IMQ_TRANS_FP64": imq.TRANSLATIONS["fp64"],
+             "IMQ_TRANS_MIXED": imq.TRANSLATIONS["mixed"],
+             "IMQ_M2L_AUTO": imq.M2L_KERNELS["auto"], "IMQ_M2L_CUDA_CORES": imq.M2L_KERNELS["cuda_cores"],
+             "IMQ_M2L_TENSOR": imq.M2L_KERNELS["tensor"],
+             "IMQ_PRECOND_NONE": imq.PRECONDS["none"], "IMQ_PRECOND_SCHWARZ": imq.PRECONDS["schwarz"],
+             "IMQ_PRECOND_SCHWARZ_2L": imq.PRECONDS["schwarz2"],
+             "IMQ_OPERATOR_FAST_F32": imq.OPERATORS["fast_f32"], "IMQ_OPERATOR_FAST_F64": imq.OPERATORS["fast_f64"],
+             "IMQ_OPERATOR_DENSE_F64": imq.OPERATORS["dense_f64"],
+             "IMQ_RESIDUAL_PLAN_F64": imq.RESIDUALS["plan"], "IMQ_RESIDUAL_DENSE_F64": imq.RESIDUALS["dense"],
+             "IMQ_KRYLOV_CG": imq.KRYLOVS["cg"], "IMQ_KRYLOV_GMRES": imq.KRYLOVS["gmres"]}
+    lines = ["#include <stdio.h>", '#include "imq.h"', "int main(void) {"]
+    lines += [f'printf("{name} %d\\n", (int){name});' for name in pairs]
+    lines += ["return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    got = {out[k]: int(out[k + 1]) for k in range(0, len(out), 2)}
+    assert got == pairs
