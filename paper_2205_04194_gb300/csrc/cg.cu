@@ -1045,7 +1045,7 @@ void cg_solve(Plan &P, const double *f_dev, double *x_dev, int nrhs, const imq_c
                 // or met its target on the recursive residual is restarted from the true residual of
                 // its best iterate while iterations are left (the recursive residual of the FP32
                 // operator can drift below the true one, so only the true residual certifies);
-                // otherwise the next round only computes the final true residual
+                // otherwise the next outer pass only computes the final true residual
                 if (max_outer == 0) {
                     if ((hs.status == kBreakdown || hs.status == kConverged) && hs.rr_best < hs.rr0 &&
                         restarts < kMaxRestarts)

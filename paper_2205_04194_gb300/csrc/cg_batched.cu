@@ -611,7 +611,7 @@ void cg_solve_batched(Plan &P, const double *f_dev, double *x_dev, int nrhs, con
                 if (max_outer == 0) {
                     // restart the problems whose pass improved on its start and broke down or met
                     // its target on the recursive residual, from the true residual of their best
-                    // iterate (only the true residual certifies); otherwise the next round only
+                    // iterate (only the true residual certifies); otherwise the next outer pass only
                     // computes the final true residuals
                     bool restart = false;
                     for (int b = 0; b < B; ++b)
